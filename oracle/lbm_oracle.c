@@ -1,0 +1,798 @@
+/*
+ * FP64 CPU oracle of the coupled f+h thermal lattice Boltzmann step of
+ * Gruszczynski & Laniewski-Wollk, "A comparative study of 3D Cumulant and
+ * Central Moments lattice Boltzmann schemes with interpolated boundary
+ * conditions ..." (arXiv 2203.01316).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes.  Only the test suite, the
+ * package smoke check and the CPU-baseline leg of the benchmark may load it.
+ * It shares no code, table or header with the CUDA library.
+ *
+ * Everything is done the literal way:
+ *   - the D3Q27 velocity list is typed from Sec. 2.1 (Lattice Boltzmann
+ *     Method), the 27 moment indices in the order given there;
+ *   - the raw-moment matrix M and the central-moment matrix T(u) are built
+ *     row by row from Eqs. (M) and (T) of Appendix C, and T(u) is applied by
+ *     an explicit 27x27 product; its inverse is applied by solving T x = y
+ *     with Gaussian elimination (T = N M, so T^-1 = M^-1 N^-1);
+ *   - equilibria are T(u)^-1 applied to the central-moment equilibrium
+ *     vector of Sec. 2.1.1 (Appendix A route);
+ *   - cumulants are the coefficients of the logarithm of the normalised
+ *     central-moment generating function, evaluated in the polynomial ring
+ *     truncated to degree <= 2 per axis (closed on the 27 indices, so exact);
+ *   - the f collision is Eq. (hydro_cu_collision), the h collision
+ *     Eq. (H_cm_collision) with the CM-SRT / CM-1st / CM-TRT rate sets of
+ *     Sec. 2.1.1, the source term per Appendix D;
+ *   - streaming is the push form of the evolution equation of Sec. 2.1,
+ *     followed by Eq. (IBB) and Eq. (IABB) on every wall link.
+ *
+ * Readings of points the paper leaves open (each is listed in the design
+ * notes of the repository):
+ *   R1 f relaxation (the paper defers to Geier 2015): off-diagonal second
+ *      cumulants and the deviators c200-c020, c200-c002 relax with
+ *      omega1 = 1/(3 nu + 1/2); the trace with omega_bulk (default 1) toward
+ *      3 cs^2; cumulants of order 3, 4, 5, 6 relax with omega3..omega6
+ *      (default 1) toward 0.
+ *   R2 body force: the first-order cumulant (the mean velocity) gains F/rho
+ *      in collision; u = (sum e f + F/2)/rho is the velocity that shifts h.
+ *   R3 source for the CM kinds: source moments Q*E (equilibrium-shaped),
+ *      added as (1 - S/2) Q E; h stores the App. D shifted variable, so
+ *      H = sum h + Q/2.
+ *   R4 IABB wall equilibrium: u_w = 0, so h^eq_i(x_w) = w_i T_w.
+ *   R5 thin gap (x_f = x_b - e_a is solid or outside the domain): the q > 1/2
+ *      branch evaluated at q = 1/2 (plain BB / ABB).
+ *   R6 inlet plane x = 0: post-collision populations are the equilibria at
+ *      (rho = 1, u_in) and (T_in, u_in); outlet plane x = nx-1: an incoming
+ *      population with e_x < 0 is the post-collision value at
+ *      (nx-1, y-e_y, z-e_z) (zero normal gradient of the post-collision
+ *      field).  y and z are always periodic.
+ *   R7 D3Q7 = velocities {0,+x,+y,+z,-x,-y,-z} (indices 0,1,2,3,7,8,9 of the
+ *      D3Q27 list), moments {000,100,010,001,200,020,002}, cs^2 = 1/3.
+ *   R8 surface heat flux of one wall: sum over its IABB links of
+ *      h_abar(x_b, t+1) - h*_a(x_b, t).
+ *
+ * Parity unpinned: none of the functions below lacks a pin; the cumulant
+ * relaxation beyond second order is pinned only through R1's default rates.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define CS2 (1.0 / 3.0)
+
+/* ---- lattice: Sec. 2.1, velocity list e = [e_x, e_y, e_z] ---- */
+static const int EX[27] = {0, 1, 0, 0, 1, 1, 0, -1, 0, 0, 1, 1, -1, -1, 0, 0, 1, -1, -1, 0, -1, 1, 1, 1, -1, -1, -1};
+static const int EY[27] = {0, 0, 1, 0, 1, 0, 1, 0, -1, 0, -1, 0, 1, 0, 1, -1, 1, -1, 0, -1, 1, -1, 1, -1, 1, -1, -1};
+static const int EZ[27] = {0, 0, 0, 1, 0, 1, 1, 0, 0, -1, 0, -1, 0, 1, -1, 1, 1, 0, -1, -1, 1, 1, -1, -1, -1, 1, -1};
+
+/* moment indices mno in the order of Sec. 2.1 */
+static const int MOM27[27][3] = {
+    {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+    {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {2, 0, 1},
+    {0, 1, 2}, {0, 2, 1}, {1, 1, 1}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}, {2, 1, 1},
+    {1, 2, 1}, {1, 1, 2}, {1, 2, 2}, {2, 1, 2}, {2, 2, 1}, {2, 2, 2}};
+
+/* reading R7 */
+static const int D3Q7_DIRS[7] = {0, 1, 2, 3, 7, 8, 9};
+static const int MOM7[7][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}};
+
+typedef struct {
+    int Q;
+    int e[27][3];
+    int mom[27][3];
+    int dir27[27]; /* index of each velocity in the D3Q27 list */
+    int opp[27];
+    double w[27];  /* equilibrium at H = 1, u = 0 */
+} lattice_t;
+
+static double ipow(double b, int p) {
+    double r = 1.0;
+    for (int i = 0; i < p; ++i) r *= b;
+    return r;
+}
+
+/* Eq. (M): M_mno|a = e_ax^m e_ay^n e_az^o */
+static void build_M(const lattice_t* L, double* M) {
+    for (int r = 0; r < L->Q; ++r)
+        for (int a = 0; a < L->Q; ++a)
+            M[r * L->Q + a] = ipow(L->e[a][0], L->mom[r][0]) * ipow(L->e[a][1], L->mom[r][1]) *
+                              ipow(L->e[a][2], L->mom[r][2]);
+}
+
+/* Eq. (T): T_mno|a = (e_ax-ux)^m (e_ay-uy)^n (e_az-uz)^o */
+static void build_T(const lattice_t* L, const double u[3], double* T) {
+    for (int r = 0; r < L->Q; ++r)
+        for (int a = 0; a < L->Q; ++a)
+            T[r * L->Q + a] = ipow(L->e[a][0] - u[0], L->mom[r][0]) *
+                              ipow(L->e[a][1] - u[1], L->mom[r][1]) *
+                              ipow(L->e[a][2] - u[2], L->mom[r][2]);
+}
+
+static void matvec(int n, const double* A, const double* x, double* y) {
+    for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) s += A[r * n + c] * x[c];
+        y[r] = s;
+    }
+}
+
+/* Solve A x = b by Gaussian elimination with partial pivoting.  Returns 0, or
+ * -1 if A is singular. */
+static int solve(int n, const double* A, const double* b, double* x) {
+    double a[27 * 28];
+    for (int r = 0; r < n; ++r) {
+        for (int c = 0; c < n; ++c) a[r * (n + 1) + c] = A[r * n + c];
+        a[r * (n + 1) + n] = b[r];
+    }
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(a[r * (n + 1) + k]) > fabs(a[piv * (n + 1) + k])) piv = r;
+        if (a[piv * (n + 1) + k] == 0.0) return -1;
+        if (piv != k)
+            for (int c = 0; c <= n; ++c) {
+                double t = a[k * (n + 1) + c];
+                a[k * (n + 1) + c] = a[piv * (n + 1) + c];
+                a[piv * (n + 1) + c] = t;
+            }
+        for (int r = k + 1; r < n; ++r) {
+            double f = a[r * (n + 1) + k] / a[k * (n + 1) + k];
+            for (int c = k; c <= n; ++c) a[r * (n + 1) + c] -= f * a[k * (n + 1) + c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = a[r * (n + 1) + n];
+        for (int c = r + 1; c < n; ++c) s -= a[r * (n + 1) + c] * x[c];
+        x[r] = s / a[r * (n + 1) + r];
+    }
+    return 0;
+}
+
+/* central-moment equilibrium vector of Sec. 2.1.1 for psi = 1: non-zero at
+ * 000 (1), 200/020/002 (cs^2), 220/202/022 (cs^4), 222 (cs^6) */
+static double eq_central(const int m[3]) {
+    double v = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (m[d] == 1) return 0.0;
+        if (m[d] == 2) v *= CS2;
+    }
+    return v;
+}
+
+/* g^eq = M^-1 N^-1 Y^eq = T(u)^-1 Y^eq (Appendix A) */
+static void equilibrium(const lattice_t* L, double psi, const double u[3], double* g) {
+    double T[27 * 27], y[27];
+    build_T(L, u, T);
+    for (int r = 0; r < L->Q; ++r) y[r] = psi * eq_central(L->mom[r]);
+    solve(L->Q, T, y, g);
+}
+
+static void lattice_init(lattice_t* L, int Q) {
+    L->Q = Q;
+    for (int a = 0; a < Q; ++a) {
+        int d = (Q == 27) ? a : D3Q7_DIRS[a];
+        L->dir27[a] = d;
+        L->e[a][0] = EX[d];
+        L->e[a][1] = EY[d];
+        L->e[a][2] = EZ[d];
+        for (int k = 0; k < 3; ++k) L->mom[a][k] = (Q == 27) ? MOM27[a][k] : MOM7[a][k];
+    }
+    for (int a = 0; a < Q; ++a) {
+        L->opp[a] = -1;
+        for (int b = 0; b < Q; ++b)
+            if (L->e[b][0] == -L->e[a][0] && L->e[b][1] == -L->e[a][1] && L->e[b][2] == -L->e[a][2])
+                L->opp[a] = b;
+    }
+    const double u0[3] = {0.0, 0.0, 0.0};
+    equilibrium(L, 1.0, u0, L->w);
+}
+
+static lattice_t LAT27, LAT7;
+static int lattices_ready = 0;
+static void ensure_lattices(void) {
+    if (!lattices_ready) {
+        lattice_init(&LAT27, 27);
+        lattice_init(&LAT7, 7);
+        lattices_ready = 1;
+    }
+}
+static const lattice_t* lattice(int Q) {
+    ensure_lattices();
+    return Q == 7 ? &LAT7 : &LAT27;
+}
+
+/* ---- cumulants: truncated polynomial ring, coefficient [i][j][k] at
+ * index 9 i + 3 j + k, s_x^3 = s_y^3 = s_z^3 = 0 ---- */
+static void poly_mul(const double* a, const double* b, double* r) {
+    for (int n = 0; n < 27; ++n) r[n] = 0.0;
+    for (int i1 = 0; i1 < 3; ++i1)
+        for (int j1 = 0; j1 < 3; ++j1)
+            for (int k1 = 0; k1 < 3; ++k1) {
+                double av = a[9 * i1 + 3 * j1 + k1];
+                if (av == 0.0) continue;
+                for (int i2 = 0; i1 + i2 < 3; ++i2)
+                    for (int j2 = 0; j1 + j2 < 3; ++j2)
+                        for (int k2 = 0; k1 + k2 < 3; ++k2)
+                            r[9 * (i1 + i2) + 3 * (j1 + j2) + (k1 + k2)] += av * b[9 * i2 + 3 * j2 + k2];
+            }
+}
+
+static const double FACT[3] = {1.0, 1.0, 2.0};
+
+/* ln(P) for P with P[0] = 1: ln(1+x) = sum_n (-1)^(n+1) x^n / n, x^7 = 0 */
+static void poly_log(const double* P, double* Lg) {
+    double x[27], xn[27], t[27];
+    for (int n = 0; n < 27; ++n) x[n] = P[n];
+    x[0] -= 1.0;
+    for (int n = 0; n < 27; ++n) { xn[n] = x[n]; Lg[n] = 0.0; }
+    for (int p = 1; p <= 6; ++p) {
+        double c = ((p % 2) ? 1.0 : -1.0) / (double)p;
+        for (int n = 0; n < 27; ++n) Lg[n] += c * xn[n];
+        poly_mul(xn, x, t);
+        for (int n = 0; n < 27; ++n) xn[n] = t[n];
+    }
+}
+
+/* exp(Lg) for Lg[0] = 0: sum_n Lg^n / n!, Lg^7 = 0 */
+static void poly_exp(const double* Lg, double* P) {
+    double xn[27], t[27];
+    double fact = 1.0;
+    for (int n = 0; n < 27; ++n) { P[n] = 0.0; xn[n] = 0.0; }
+    xn[0] = 1.0;
+    for (int p = 0; p <= 6; ++p) {
+        if (p > 0) fact *= (double)p;
+        for (int n = 0; n < 27; ++n) P[n] += xn[n] / fact;
+        poly_mul(xn, Lg, t);
+        for (int n = 0; n < 27; ++n) xn[n] = t[n];
+    }
+}
+
+/* Cumulant transform (Sec. 2.1, following Geier 2015): C[000] = rho,
+ * C[100], C[010], C[001] = the mean velocity (first-order cumulants), and
+ * for order >= 2 the cumulants of the normalised distribution, computed as
+ * i! j! k! [s^ijk] ln( sum kappa_ijk / rho s^ijk / (i! j! k!) ) from the
+ * central moments kappa about the mean. */
+static void cumulants(const double* g, double* C) {
+    const lattice_t* L = lattice(27);
+    double rho = 0.0, mean[3] = {0, 0, 0};
+    for (int a = 0; a < 27; ++a) {
+        rho += g[a];
+        for (int d = 0; d < 3; ++d) mean[d] += L->e[a][d] * g[a];
+    }
+    for (int d = 0; d < 3; ++d) mean[d] /= rho;
+    double T[27 * 27], kap[27], P[27], Lg[27];
+    build_T(L, mean, T);
+    matvec(27, T, g, kap);
+    for (int r = 0; r < 27; ++r) {
+        const int* m = L->mom[r];
+        P[9 * m[0] + 3 * m[1] + m[2]] = kap[r] / rho / (FACT[m[0]] * FACT[m[1]] * FACT[m[2]]);
+    }
+    poly_log(P, Lg);
+    for (int r = 0; r < 27; ++r) {
+        const int* m = L->mom[r];
+        C[r] = FACT[m[0]] * FACT[m[1]] * FACT[m[2]] * Lg[9 * m[0] + 3 * m[1] + m[2]];
+    }
+    C[0] = rho;
+    C[1] = mean[0];
+    C[2] = mean[1];
+    C[3] = mean[2];
+}
+
+/* inverse of cumulants(): exponentiate, scale by rho, and solve T(mean). */
+static void cumulants_inverse(const double* C, double* g) {
+    const lattice_t* L = lattice(27);
+    double rho = C[0], mean[3] = {C[1], C[2], C[3]};
+    double Lg[27], P[27], kap[27], T[27 * 27];
+    for (int r = 0; r < 27; ++r) {
+        const int* m = L->mom[r];
+        int order = m[0] + m[1] + m[2];
+        Lg[9 * m[0] + 3 * m[1] + m[2]] =
+            (order >= 2) ? C[r] / (FACT[m[0]] * FACT[m[1]] * FACT[m[2]]) : 0.0;
+    }
+    poly_exp(Lg, P);
+    for (int r = 0; r < 27; ++r) {
+        const int* m = L->mom[r];
+        kap[r] = rho * FACT[m[0]] * FACT[m[1]] * FACT[m[2]] * P[9 * m[0] + 3 * m[1] + m[2]];
+    }
+    build_T(L, mean, T);
+    solve(27, T, kap, g);
+}
+
+/* ---- parameters ---- */
+typedef struct {
+    int nx, ny, nz;
+    int qh;          /* 27 or 7 */
+    int hkind;       /* 0 CM-TRT, 1 CM-SRT, 2 CM-1st */
+    int periodic_x;  /* 1: periodic in x; 0: inlet plane x=0, outlet x=nx-1 */
+    double nu, k;
+    double omega_bulk, omega3, omega4, omega5, omega6;
+    double F[3];
+    double u_in[3], T_in;
+} orc_params;
+
+enum { KIND_TRT = 0, KIND_SRT = 1, KIND_1ST = 2 };
+
+/* Eq. (hydro_cu_collision) with reading R1 (rates) and R2 (force).  Writes
+ * the post-collision populations and the velocity u that shifts h. */
+static void collide_f(const orc_params* p, const double* f, double* fs, double* u) {
+    double C[27], Cs[27];
+    cumulants(f, C);
+    const double rho = C[0];
+    const double w1 = 1.0 / (3.0 * p->nu + 0.5);
+    const double wb = p->omega_bulk;
+    for (int r = 0; r < 27; ++r) Cs[r] = C[r];
+    for (int d = 0; d < 3; ++d) {
+        Cs[1 + d] = C[1 + d] + p->F[d] / rho;
+        u[d] = C[1 + d] + 0.5 * p->F[d] / rho;
+    }
+    /* second order: off-diagonal 110 (4), 101 (5), 011 (6) */
+    for (int r = 4; r <= 6; ++r) Cs[r] = C[r] + w1 * (0.0 - C[r]);
+    /* diagonal 200 (7), 020 (8), 002 (9): deviators with omega1, trace with
+     * omega_bulk toward 3 cs^2 */
+    double dxy = C[7] - C[8], dxz = C[7] - C[9], tr = C[7] + C[8] + C[9];
+    dxy = dxy + w1 * (0.0 - dxy);
+    dxz = dxz + w1 * (0.0 - dxz);
+    tr = tr + wb * (3.0 * CS2 - tr);
+    Cs[7] = (tr + dxy + dxz) / 3.0;
+    Cs[8] = Cs[7] - dxy;
+    Cs[9] = Cs[7] - dxz;
+    const double wn[7] = {0, 0, 0, p->omega3, p->omega4, p->omega5, p->omega6};
+    const lattice_t* L = lattice(27);
+    for (int r = 10; r < 27; ++r) {
+        int order = L->mom[r][0] + L->mom[r][1] + L->mom[r][2];
+        Cs[r] = C[r] + wn[order] * (0.0 - C[r]);
+    }
+    cumulants_inverse(Cs, fs);
+}
+
+/* relaxation rate of moment r for the CM kinds of Sec. 2.1.1 */
+static double rate_h(int kind, int order, double sH) {
+    switch (kind) {
+        case KIND_SRT: return sH;
+        case KIND_1ST: return (order == 1) ? sH : 1.0;
+        default: return (order % 2 == 1) ? sH : 1.0; /* CM-TRT */
+    }
+}
+
+/* Eq. (H_cm_collision) with the Appendix D source (reading R3).  h holds the
+ * shifted variable h - q/2; Q is the source (zeroth moment) of this node. */
+static void collide_h(const orc_params* p, const double* h, const double u[3], double Q, double* hs) {
+    const lattice_t* L = lattice(p->qh);
+    const int n = L->Q;
+    const double sH = 1.0 / (p->k / CS2 + 0.5);
+    double T[27 * 27], Y[27], Ys[27];
+    build_T(L, u, T);
+    matvec(n, T, h, Y);
+    double H = 0.0;
+    for (int a = 0; a < n; ++a) H += h[a];
+    H += 0.5 * Q;
+    for (int r = 0; r < n; ++r) {
+        const int* m = L->mom[r];
+        double s = rate_h(p->hkind, m[0] + m[1] + m[2], sH);
+        double E = eq_central(m);
+        Ys[r] = Y[r] + s * (H * E - Y[r]) + (1.0 - 0.5 * s) * Q * E;
+    }
+    solve(n, T, Ys, hs);
+}
+
+/* ---- simulation state ---- */
+enum { FL_FLUID = 0, FL_SOLID = 1, FL_INLET = 2, FL_OUTLET = 3 };
+
+typedef struct {
+    orc_params p;
+    int N;
+    double* f;      /* pre-collision, [27][N] */
+    double* h;      /* pre-collision, [qh][N] */
+    double* fs;     /* post-collision scratch */
+    double* hs;
+    double* fn;     /* streaming target */
+    double* hn;
+    uint8_t* flags;
+    float* qtab;    /* [N*27], -1 where no wall link */
+    int* wtab;      /* [N*27], wall id of the link */
+    double* Twall;  /* per wall id */
+    int nwalls;
+    double* theta;  /* per node source Q, or NULL */
+} orc_sim;
+
+static int node_of(const orc_sim* s, int x, int y, int z) { return x + s->p.nx * (y + s->p.ny * z); }
+
+/* neighbour x + e (y, z periodic; x periodic or bounded).  Returns -1 when it
+ * leaves the domain through a non-periodic x face. */
+static int neighbour(const orc_sim* s, int n, int ex, int ey, int ez) {
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    x += ex;
+    y = ((y + ey) % ny + ny) % ny;
+    z = ((z + ez) % nz + nz) % nz;
+    if (s->p.periodic_x) x = ((x % nx) + nx) % nx;
+    else if (x < 0 || x >= nx) return -1;
+    return node_of(s, x, y, z);
+}
+
+orc_sim* orc_create(const orc_params* p) {
+    ensure_lattices();
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    s->p = *p;
+    s->N = p->nx * p->ny * p->nz;
+    size_t N = (size_t)s->N;
+    s->f = (double*)calloc(27 * N, sizeof(double));
+    s->fs = (double*)calloc(27 * N, sizeof(double));
+    s->fn = (double*)calloc(27 * N, sizeof(double));
+    s->h = (double*)calloc((size_t)p->qh * N, sizeof(double));
+    s->hs = (double*)calloc((size_t)p->qh * N, sizeof(double));
+    s->hn = (double*)calloc((size_t)p->qh * N, sizeof(double));
+    s->flags = (uint8_t*)calloc(N, 1);
+    s->qtab = (float*)malloc(27 * N * sizeof(float));
+    s->wtab = (int*)calloc(27 * N, sizeof(int));
+    for (size_t i = 0; i < 27 * N; ++i) s->qtab[i] = -1.0f;
+    s->nwalls = 1;
+    s->Twall = (double*)calloc(1, sizeof(double));
+    return s;
+}
+
+void orc_destroy(orc_sim* s) {
+    if (!s) return;
+    free(s->f); free(s->fs); free(s->fn); free(s->h); free(s->hs); free(s->hn);
+    free(s->flags); free(s->qtab); free(s->wtab); free(s->Twall); free(s->theta);
+    free(s);
+}
+
+/* Geometry: flags (0 fluid, 1 solid, 2 inlet, 3 outlet) and the wall links
+ * (node x_b, direction a with x_b + e_a solid, q in (0,1], wall id).
+ * Returns 0, or a negative code naming the first rule broken:
+ *  -1 flag out of range, -2 inlet/outlet planes wrong, -3 link node not
+ *  fluid, -4 link target not solid, -5 q outside (0,1], -6 duplicate link,
+ *  -7 fluid->solid link missing, -8 solid adjacent to the outlet plane,
+ *  -9 wall id out of range. */
+int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* lnode,
+                     const int* ldir, const float* lq, const int* lwall, int nwalls) {
+    const int N = s->N, nx = s->p.nx;
+    for (int n = 0; n < N; ++n) {
+        if (flags[n] > 3) return -1;
+        int x = n % nx;
+        if (s->p.periodic_x) {
+            if (flags[n] == FL_INLET || flags[n] == FL_OUTLET) return -2;
+        } else {
+            if ((x == 0) != (flags[n] == FL_INLET)) return -2;
+            if ((x == nx - 1) != (flags[n] == FL_OUTLET)) return -2;
+            if (x == nx - 2 && flags[n] == FL_SOLID) return -8;
+        }
+    }
+    memcpy(s->flags, flags, (size_t)N);
+    for (size_t i = 0; i < 27 * (size_t)N; ++i) { s->qtab[i] = -1.0f; s->wtab[i] = 0; }
+    const lattice_t* L = lattice(27);
+    for (int l = 0; l < nlinks; ++l) {
+        int n = lnode[l], a = ldir[l];
+        if (n < 0 || n >= N || a < 0 || a >= 27) return -3;
+        if (flags[n] != FL_FLUID) return -3;
+        int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
+        if (t < 0 || flags[t] != FL_SOLID) return -4;
+        if (!(lq[l] > 0.0f && lq[l] <= 1.0f)) return -5;
+        if (s->qtab[(size_t)n * 27 + a] >= 0.0f) return -6;
+        if (lwall[l] < 0 || lwall[l] >= nwalls) return -9;
+        s->qtab[(size_t)n * 27 + a] = lq[l];
+        s->wtab[(size_t)n * 27 + a] = lwall[l];
+    }
+    for (int n = 0; n < N; ++n) {
+        if (flags[n] == FL_SOLID) continue;
+        for (int a = 1; a < 27; ++a) {
+            int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
+            if (t >= 0 && flags[t] == FL_SOLID) {
+                if (flags[n] != FL_FLUID) {
+                    if (flags[n] == FL_OUTLET) return -8;
+                    continue; /* inlet populations into a solid are dropped */
+                }
+                if (s->qtab[(size_t)n * 27 + a] < 0.0f) return -7;
+            }
+        }
+    }
+    free(s->Twall);
+    s->nwalls = nwalls;
+    s->Twall = (double*)calloc((size_t)nwalls, sizeof(double));
+    return 0;
+}
+
+void orc_set_wall_temperature(orc_sim* s, int wall, double T) {
+    if (wall >= 0 && wall < s->nwalls) s->Twall[wall] = T;
+}
+
+void orc_set_theta(orc_sim* s, const double* theta) {
+    if (!s->theta) s->theta = (double*)calloc((size_t)s->N, sizeof(double));
+    memcpy(s->theta, theta, (size_t)s->N * sizeof(double));
+}
+
+static double theta_at(const orc_sim* s, int n) { return s->theta ? s->theta[n] : 0.0; }
+
+/* Initial state: equilibria at (rho, u) for f and (H = rho T, u) for h, then
+ * the App. D shift h - q/2 (q = Q h^eq(1, u)).  Inlet nodes take the inlet
+ * state, solid nodes zero. */
+void orc_init_fields(orc_sim* s, const double* rho, const double* u, const double* T) {
+    const int N = s->N, qh = s->p.qh;
+    const lattice_t* Lh = lattice(qh);
+    for (int n = 0; n < N; ++n) {
+        double fe[27], he[27], qe[27];
+        if (s->flags[n] == FL_SOLID) {
+            for (int a = 0; a < 27; ++a) s->f[(size_t)a * N + n] = 0.0;
+            for (int a = 0; a < qh; ++a) s->h[(size_t)a * N + n] = 0.0;
+            continue;
+        }
+        double r = rho[n], uu[3] = {u[n], u[N + n], u[2 * N + n]}, TT = T[n];
+        if (s->flags[n] == FL_INLET) {
+            r = 1.0;
+            for (int d = 0; d < 3; ++d) uu[d] = s->p.u_in[d];
+            TT = s->p.T_in;
+        }
+        equilibrium(lattice(27), r, uu, fe);
+        equilibrium(Lh, r * TT, uu, he);
+        double Q = theta_at(s, n);
+        equilibrium(Lh, Q, uu, qe);
+        for (int a = 0; a < 27; ++a) s->f[(size_t)a * N + n] = fe[a];
+        for (int a = 0; a < qh; ++a) s->h[(size_t)a * N + n] = he[a] - 0.5 * qe[a];
+    }
+}
+
+void orc_set_state(orc_sim* s, const double* f, const double* h) {
+    memcpy(s->f, f, 27 * (size_t)s->N * sizeof(double));
+    memcpy(s->h, h, (size_t)s->p.qh * s->N * sizeof(double));
+}
+
+void orc_get_state(const orc_sim* s, double* f, double* h) {
+    memcpy(f, s->f, 27 * (size_t)s->N * sizeof(double));
+    memcpy(h, s->h, (size_t)s->p.qh * s->N * sizeof(double));
+}
+
+/* Collision of every node: pre-collision state -> fs, hs. */
+void orc_collide(orc_sim* s) {
+    const int N = s->N, qh = s->p.qh;
+    const lattice_t* Lh = lattice(qh);
+    double feq_in[27], heq_in[27];
+    equilibrium(lattice(27), 1.0, s->p.u_in, feq_in);
+    equilibrium(Lh, s->p.T_in, s->p.u_in, heq_in);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int n = 0; n < N; ++n) {
+        double f[27], h[27], fs[27], hs[27], u[3];
+        uint8_t fl = s->flags[n];
+        if (fl == FL_SOLID) {
+            for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = 0.0;
+            for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = 0.0;
+            continue;
+        }
+        if (fl == FL_INLET) { /* reading R6 */
+            for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = feq_in[a];
+            for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = heq_in[a];
+            continue;
+        }
+        for (int a = 0; a < 27; ++a) f[a] = s->f[(size_t)a * N + n];
+        for (int a = 0; a < qh; ++a) h[a] = s->h[(size_t)a * N + n];
+        collide_f(&s->p, f, fs, u);
+        collide_h(&s->p, h, u, theta_at(s, n), hs);
+        for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = fs[a];
+        for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = hs[a];
+    }
+}
+
+void orc_set_post(orc_sim* s, const double* fs, const double* hs) {
+    memcpy(s->fs, fs, 27 * (size_t)s->N * sizeof(double));
+    memcpy(s->hs, hs, (size_t)s->p.qh * s->N * sizeof(double));
+}
+
+void orc_get_post(const orc_sim* s, double* fs, double* hs) {
+    memcpy(fs, s->fs, 27 * (size_t)s->N * sizeof(double));
+    memcpy(hs, s->hs, (size_t)s->p.qh * s->N * sizeof(double));
+}
+
+/* Eq. (IBB) for one link: the population arriving at x_b in direction abar.
+ * fa_b = f*_a(x_b), fab_b = f*_abar(x_b), fa_f = f*_a(x_f), thin = x_f not
+ * usable (reading R5). */
+static double ibb(double q, double fa_b, double fab_b, double fa_f, int thin) {
+    if (q <= 0.5 && !thin) return 2.0 * q * fa_b + (1.0 - 2.0 * q) * fa_f;
+    if (q <= 0.5) q = 0.5;
+    return (fa_b + (2.0 * q - 1.0) * fab_b) / (2.0 * q);
+}
+
+/* Eq. (IABB) for one link; heq_w = h^eq_i(x_w) = w_i T_w (reading R4). */
+static double iabb(double q, double ha_b, double hab_b, double ha_f, int thin, double heq_w) {
+    if (q <= 0.5 && !thin) return -(2.0 * q * ha_b + (1.0 - 2.0 * q) * ha_f) + 2.0 * heq_w;
+    if (q <= 0.5) q = 0.5;
+    return (-ha_b + (2.0 * q - 1.0) * hab_b + 2.0 * heq_w) / (2.0 * q);
+}
+
+/* Streaming of fs, hs (push, Sec. 2.1 evolution equation) with Eq. (IBB),
+ * Eq. (IABB) and the planes of reading R6.  Result becomes the pre-collision
+ * state.  Returns the number of non-solid populations left unset (0 when the
+ * geometry is complete). */
+int orc_stream(orc_sim* s) {
+    const int N = s->N, qh = s->p.qh, nx = s->p.nx;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    for (size_t i = 0; i < 27 * (size_t)N; ++i) s->fn[i] = NAN;
+    for (size_t i = 0; i < (size_t)qh * N; ++i) s->hn[i] = NAN;
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) continue;
+        for (int a = 0; a < 27; ++a) {
+            int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
+            if (t < 0 || s->flags[t] == FL_SOLID) continue;
+            s->fn[(size_t)a * N + t] = s->fs[(size_t)a * N + n];
+        }
+        for (int a = 0; a < qh; ++a) {
+            int t = neighbour(s, n, Lh->e[a][0], Lh->e[a][1], Lh->e[a][2]);
+            if (t < 0 || s->flags[t] == FL_SOLID) continue;
+            s->hn[(size_t)a * N + t] = s->hs[(size_t)a * N + n];
+        }
+    }
+    /* wall links */
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int a = 1; a < 27; ++a) {
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f) continue;
+            int ab = L->opp[a];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double fa_f = thin ? 0.0 : s->fs[(size_t)a * N + xf];
+            s->fn[(size_t)ab * N + n] =
+                ibb(q, s->fs[(size_t)a * N + n], s->fs[(size_t)ab * N + n], fa_f, thin);
+            /* the same link for h, when the direction belongs to h's lattice */
+            for (int i = 0; i < qh; ++i) {
+                if (Lh->dir27[i] != a) continue;
+                int ib = Lh->opp[i];
+                double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
+                double heq = Lh->w[i] * s->Twall[s->wtab[(size_t)n * 27 + a]];
+                s->hn[(size_t)ib * N + n] = iabb(q, s->hs[(size_t)i * N + n],
+                                                 s->hs[(size_t)ib * N + n], ha_f, thin, heq);
+            }
+        }
+    }
+    /* planes (reading R6) */
+    if (!s->p.periodic_x) {
+        double feq_in[27], heq_in[27];
+        equilibrium(L, 1.0, s->p.u_in, feq_in);
+        equilibrium(Lh, s->p.T_in, s->p.u_in, heq_in);
+        for (int n = 0; n < N; ++n) {
+            int x = n % nx;
+            if (s->flags[n] == FL_INLET) {
+                for (int a = 0; a < 27; ++a) s->fn[(size_t)a * N + n] = feq_in[a];
+                for (int a = 0; a < qh; ++a) s->hn[(size_t)a * N + n] = heq_in[a];
+            } else if (s->flags[n] == FL_OUTLET && x == nx - 1) {
+                for (int a = 0; a < 27; ++a) {
+                    if (L->e[a][0] >= 0) continue;
+                    int src = neighbour(s, n, 0, -L->e[a][1], -L->e[a][2]);
+                    s->fn[(size_t)a * N + n] = s->fs[(size_t)a * N + src];
+                }
+                for (int a = 0; a < qh; ++a) {
+                    if (Lh->e[a][0] >= 0) continue;
+                    int src = neighbour(s, n, 0, -Lh->e[a][1], -Lh->e[a][2]);
+                    s->hn[(size_t)a * N + n] = s->hs[(size_t)a * N + src];
+                }
+            }
+        }
+    }
+    int missing = 0;
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) {
+            for (int a = 0; a < 27; ++a) s->fn[(size_t)a * N + n] = 0.0;
+            for (int a = 0; a < qh; ++a) s->hn[(size_t)a * N + n] = 0.0;
+            continue;
+        }
+        for (int a = 0; a < 27; ++a) missing += isnan(s->fn[(size_t)a * N + n]) ? 1 : 0;
+        for (int a = 0; a < qh; ++a) missing += isnan(s->hn[(size_t)a * N + n]) ? 1 : 0;
+    }
+    double* t;
+    t = s->f; s->f = s->fn; s->fn = t;
+    t = s->h; s->h = s->hn; s->hn = t;
+    return missing;
+}
+
+int orc_step(orc_sim* s, int nsteps) {
+    for (int i = 0; i < nsteps; ++i) {
+        orc_collide(s);
+        int m = orc_stream(s);
+        if (m) return m;
+    }
+    return 0;
+}
+
+/* Macroscopic fields of the pre-collision state (Sec. 2.1): rho = sum f,
+ * u = (sum e f + F/2)/rho, H = sum h + Q/2, T = H/rho (c_v = 1).  Solid
+ * nodes report 0; inlet nodes the inlet state. */
+void orc_macros(const orc_sim* s, double* rho, double* u, double* T) {
+    const int N = s->N, qh = s->p.qh;
+    const lattice_t* L = lattice(27);
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) {
+            rho[n] = 0.0; u[n] = u[N + n] = u[2 * N + n] = 0.0; T[n] = 0.0;
+            continue;
+        }
+        if (s->flags[n] == FL_INLET) {
+            rho[n] = 1.0;
+            for (int d = 0; d < 3; ++d) u[d * N + n] = s->p.u_in[d];
+            T[n] = s->p.T_in;
+            continue;
+        }
+        double r = 0.0, j[3] = {0, 0, 0}, H = 0.0;
+        for (int a = 0; a < 27; ++a) {
+            double v = s->f[(size_t)a * N + n];
+            r += v;
+            for (int d = 0; d < 3; ++d) j[d] += L->e[a][d] * v;
+        }
+        for (int a = 0; a < qh; ++a) H += s->h[(size_t)a * N + n];
+        H += 0.5 * theta_at(s, n);
+        rho[n] = r;
+        for (int d = 0; d < 3; ++d) u[d * N + n] = (j[d] + 0.5 * s->p.F[d]) / r;
+        T[n] = H / r;
+    }
+}
+
+/* Totals over non-solid nodes of rho and H (pre-collision definitions). */
+void orc_balances(const orc_sim* s, double* mass, double* energy) {
+    const int N = s->N, qh = s->p.qh;
+    double m = 0.0, e = 0.0;
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) continue;
+        for (int a = 0; a < 27; ++a) m += s->f[(size_t)a * N + n];
+        for (int a = 0; a < qh; ++a) e += s->h[(size_t)a * N + n];
+        e += 0.5 * theta_at(s, n);
+    }
+    *mass = m;
+    *energy = e;
+}
+
+/* Surface heat flux of wall `wall` for the transition t -> t+1 from the
+ * current state (reading R8; Sec. 4.4 surface-flux equation): collide, then
+ * sum h_ibar(x_b,t+1) - h*_i(x_b,t) over the IABB links of that wall. */
+double orc_surface_flux(orc_sim* s, int wall) {
+    orc_collide(s);
+    const int N = s->N, qh = s->p.qh;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    double flux = 0.0;
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int i = 0; i < qh; ++i) {
+            int a = Lh->dir27[i];
+            if (a == 0) continue;
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f || s->wtab[(size_t)n * 27 + a] != wall) continue;
+            int ib = Lh->opp[i];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
+            double heq = Lh->w[i] * s->Twall[wall];
+            double hin = iabb(q, s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n], ha_f, thin, heq);
+            flux += hin - s->hs[(size_t)i * N + n];
+        }
+    }
+    return flux;
+}
+
+/* ---- single-node entry points (used by the pin tests) ---- */
+void orc_lattice(int Q, int* e, double* w, int* opp, int* mom) {
+    const lattice_t* L = lattice(Q);
+    for (int a = 0; a < Q; ++a) {
+        for (int d = 0; d < 3; ++d) { e[3 * a + d] = L->e[a][d]; mom[3 * a + d] = L->mom[a][d]; }
+        w[a] = L->w[a];
+        opp[a] = L->opp[a];
+    }
+}
+void orc_matrix_M(int Q, double* M) { build_M(lattice(Q), M); }
+void orc_matrix_T(int Q, const double* u, double* T) { build_T(lattice(Q), u, T); }
+void orc_equilibrium(int Q, double psi, const double* u, double* g) { equilibrium(lattice(Q), psi, u, g); }
+void orc_cumulants(const double* g, double* C) { cumulants(g, C); }
+void orc_cumulants_inverse(const double* C, double* g) { cumulants_inverse(C, g); }
+void orc_collide_f(const orc_params* p, const double* f, double* fs, double* u) { collide_f(p, f, fs, u); }
+void orc_collide_h(const orc_params* p, const double* h, const double* u, double Q, double* hs) {
+    collide_h(p, h, u, Q, hs);
+}
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

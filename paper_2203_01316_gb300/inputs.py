@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs: geometries (node flags + wall links with their
+wall-distance fractions q) and initial macroscopic fields.
+
+This module holds no lattice Boltzmann arithmetic; it only builds what the
+method consumes.  Both the GPU library and the CPU oracle are fed from it.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014): output i of
+seed s is mix(s + i * 0x9E3779B97F4A7C15), with the published mixing
+constants; a double in [0,1) is the top 53 bits times 2^-53.
+
+Conventions shared with the library:
+  node index n = x + nx*(y + ny*z); flags 0 fluid, 1 solid, 2 inlet, 3 outlet;
+  a wall link (n, a) means node n is fluid and n + e_a is solid, with q the
+  fraction of the link at which the wall is crossed (Sec. 3 of the paper:
+  "distance along the link between boundary node and wall").
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# D3Q27 velocity list in the paper's order (Sec. 2.1); geometry needs it to
+# know which neighbour each link points at.
+E27 = np.array([
+    [0, 1, 0, 0, 1, 1, 0, -1, 0, 0, 1, 1, -1, -1, 0, 0, 1, -1, -1, 0, -1, 1, 1, 1, -1, -1, -1],
+    [0, 0, 1, 0, 1, 0, 1, 0, -1, 0, -1, 0, 1, 0, 1, -1, 1, -1, 0, -1, 1, -1, 1, -1, 1, -1, -1],
+    [0, 0, 0, 1, 0, 1, 1, 0, 0, -1, 0, -1, 0, 1, -1, 1, 1, 0, -1, -1, 1, 1, -1, -1, -1, 1, -1],
+], dtype=np.int64).T
+
+FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset+1 .. offset+n of splitmix64 seeded with `seed` (uint64)."""
+    i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, lo=0.0, hi=1.0, offset: int = 0) -> np.ndarray:
+    u = (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def node_index(x, y, z, nx, ny):
+    return x + nx * (y + ny * z)
+
+
+def _empty_links():
+    return {"node": np.zeros(0, np.int32), "dir": np.zeros(0, np.int32),
+            "q": np.zeros(0, np.float32), "wall": np.zeros(0, np.int32)}
+
+
+def _sort_links(node, dr, q, wall):
+    node = np.asarray(node, np.int64)
+    dr = np.asarray(dr, np.int64)
+    order = np.lexsort((dr, node))
+    return {"node": node[order].astype(np.int32), "dir": dr[order].astype(np.int32),
+            "q": np.asarray(q, np.float32)[order], "wall": np.asarray(wall, np.int32)[order]}
+
+
+def channel_flags(nx, ny, nz, periodic_x=False):
+    """All-fluid box; with periodic_x False the x=0 plane is the inlet and
+    x=nx-1 the outlet."""
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    if not periodic_x:
+        flags[:, :, 0] = INLET
+        flags[:, :, nx - 1] = OUTLET
+    return flags
+
+
+def add_spheres(flags, centres, radii, wall_ids=None):
+    """Mark closed balls |x-c|^2 <= R^2 solid (periodic images in y and z)
+    and return the wall links of every fluid node next to them.  q is the
+    smallest t in (0,1] with |x_b + t e_a - c| = R, computed in float64 and
+    stored as float32.  Spheres must not touch one another."""
+    nz, ny, nx = flags.shape
+    centres = np.asarray(centres, np.float64).reshape(-1, 3)
+    radii = np.asarray(radii, np.float64).reshape(-1)
+    if wall_ids is None:
+        wall_ids = np.zeros(len(radii), np.int32)
+    boxes = []
+    for c, R in zip(centres, radii):
+        x0 = max(int(math.floor(c[0] - R)) - 1, 0)
+        x1 = min(int(math.ceil(c[0] + R)) + 1, nx - 1)
+        xs = np.arange(x0, x1 + 1)
+        ys = np.arange(int(math.floor(c[1] - R)) - 1, int(math.ceil(c[1] + R)) + 2)
+        zs = np.arange(int(math.floor(c[2] - R)) - 1, int(math.ceil(c[2] + R)) + 2)
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        d2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2
+        inside = d2 <= R * R
+        flags[Z[inside] % nz, Y[inside] % ny, X[inside]] = SOLID
+        boxes.append((X, Y, Z))
+    nodes, dirs, qs, walls = [], [], [], []
+    for (X, Y, Z), c, R, wid in zip(boxes, centres, radii, wall_ids):
+        fluid = flags[Z % nz, Y % ny, X] == FLUID
+        Xb, Yb, Zb = X[fluid], Y[fluid], Z[fluid]
+        for a in range(1, 27):
+            ex, ey, ez = E27[a]
+            Xt = Xb + ex
+            ok = (Xt >= 0) & (Xt < nx)
+            Yt, Zt = Yb + ey, Zb + ez
+            tgt_in = ((Xt - c[0]) ** 2 + (Yt - c[1]) ** 2 + (Zt - c[2]) ** 2) <= R * R
+            hit = ok & tgt_in
+            if not hit.any():
+                continue
+            dx, dy, dz = Xb[hit] - c[0], Yb[hit] - c[1], Zb[hit] - c[2]
+            ee = float(ex * ex + ey * ey + ez * ez)
+            de = dx * ex + dy * ey + dz * ez
+            dd = dx * dx + dy * dy + dz * dz
+            disc = np.maximum(de * de - ee * (dd - R * R), 0.0)
+            t = (-de - np.sqrt(disc)) / ee
+            t = np.clip(t, np.nextafter(0.0, 1.0), 1.0)
+            q32 = t.astype(np.float32)
+            q32 = np.where(q32 <= 0.0, np.float32(np.finfo(np.float32).tiny), q32)
+            nodes.append(node_index(Xb[hit], Yb[hit] % ny, Zb[hit] % nz, nx, ny))
+            dirs.append(np.full(hit.sum(), a))
+            qs.append(q32)
+            walls.append(np.full(hit.sum(), wid))
+    if not nodes:
+        return _empty_links()
+    return _sort_links(np.concatenate(nodes), np.concatenate(dirs), np.concatenate(qs),
+                       np.concatenate(walls))
+
+
+def merge_links(*lists):
+    return _sort_links(np.concatenate([l["node"] for l in lists]),
+                       np.concatenate([l["dir"] for l in lists]),
+                       np.concatenate([l["q"] for l in lists]),
+                       np.concatenate([l["wall"] for l in lists]))
+
+
+def plate_walls(flags, q_bottom=0.5, q_top=0.5, wall_bottom=0, wall_top=1):
+    """Solid layers y=0 and y=ny-1; links of the fluid layers y=1 and y=ny-2
+    crossing them, with the walls at y = 1 - q_bottom and y = ny-2 + q_top."""
+    nz, ny, nx = flags.shape
+    flags[:, 0, :] = SOLID
+    flags[:, ny - 1, :] = SOLID
+    nodes, dirs, qs, walls = [], [], [], []
+    zz, xx = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    for a in range(1, 27):
+        ex, ey, ez = E27[a]
+        if ey == 0:
+            continue
+        yb = 1 if ey < 0 else ny - 2
+        sel = flags[zz, yb, xx] == FLUID
+        if not sel.any():
+            continue
+        # a link whose target x leaves a non-periodic box hits the plane, not the wall
+        n = node_index(xx[sel], yb, zz[sel], nx, ny)
+        nodes.append(n)
+        dirs.append(np.full(n.size, a))
+        qs.append(np.full(n.size, q_bottom if ey < 0 else q_top, np.float32))
+        walls.append(np.full(n.size, wall_bottom if ey < 0 else wall_top))
+    return _sort_links(np.concatenate(nodes), np.concatenate(dirs), np.concatenate(qs),
+                       np.concatenate(walls))
+
+
+# ---- workloads -------------------------------------------------------------
+def periodic_tgv(n=32, u0=(0.05, 0.03, 0.01), A=0.01, dT=0.1):
+    """Fully periodic n^3 box: uniform velocity u0 plus a Taylor-Green vortex
+    of amplitude A and wavenumber 2 pi/n, T = 1 + dT sin sin sin."""
+    k = 2.0 * math.pi / n
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ux = u0[0] + A * np.sin(k * x) * np.cos(k * y) * np.cos(k * z)
+    uy = u0[1] - A * np.cos(k * x) * np.sin(k * y) * np.cos(k * z)
+    uz = np.full_like(ux, u0[2], dtype=np.float64)
+    T = 1.0 + dT * np.sin(k * x) * np.sin(k * y) * np.sin(k * z)
+    rho = np.ones_like(T)
+    return {"dims": (n, n, n), "flags": np.zeros((n, n, n), np.uint8), "links": _empty_links(),
+            "rho": rho.reshape(-1), "u": np.stack([ux, uy, uz]).reshape(3, -1),
+            "T": T.reshape(-1), "periodic_x": True, "nwalls": 1}
+
+
+def heated_sphere(nx=192, ny=64, nz=64, D=16.0, cx=48.0, seed=1234, u_in=0.02, T_in=0.0):
+    """Channel with a sphere of diameter D centred at (cx, ny/2, nz/2) plus a
+    seeded offset drawn uniformly in [0,1)^3; inlet at x=0, outlet at
+    x=nx-1, periodic y and z; fluid starts at (rho=1, u_in, T_in)."""
+    off = uniform(seed, 3)
+    c = np.array([cx, ny / 2.0, nz / 2.0]) + off
+    flags = channel_flags(nx, ny, nz, periodic_x=False)
+    links = add_spheres(flags, [c], [D / 2.0])
+    N = nx * ny * nz
+    u = np.zeros((3, N))
+    u[0] = u_in
+    return {"dims": (nx, ny, nz), "flags": flags.reshape(-1), "links": links,
+            "rho": np.ones(N), "u": u, "T": np.full(N, T_in), "periodic_x": False,
+            "nwalls": 1, "centre": c, "D": D, "u_in": (u_in, 0.0, 0.0), "T_in": T_in}
+
+
+def plate_channel(nx=128, ny=64, nz=64, q_bottom=0.5, q_top=0.5, seed=1234, theta_max=1e-5,
+                  T0=0.5):
+    """Periodic-x channel between a bottom wall (wall 0) and a top wall
+    (wall 1); per-node heat source theta drawn uniformly in [0, theta_max]."""
+    flags = channel_flags(nx, ny, nz, periodic_x=True)
+    links = plate_walls(flags, q_bottom, q_top)
+    N = nx * ny * nz
+    theta = uniform(seed, N, 0.0, theta_max)
+    theta[flags.reshape(-1) == SOLID] = 0.0
+    return {"dims": (nx, ny, nz), "flags": flags.reshape(-1), "links": links,
+            "rho": np.ones(N), "u": np.zeros((3, N)), "T": np.full(N, T0), "periodic_x": True,
+            "nwalls": 2, "theta": theta, "H_c": (ny - 3) + q_bottom + q_top}
+
+
+def porous_bed(nx=512, ny=256, nz=256, n_spheres=200, dmin=12.0, dmax=24.0, gap=2.0,
+               seed=1234, u_in=0.01, T_in=0.0, max_tries=200000):
+    """Channel with n_spheres non-overlapping spheres (diameters uniform in
+    [dmin, dmax], surface gap >= gap with periodic minimum image in y and z,
+    at least R + gap from the inlet and outlet planes), placed by rejection
+    sampling from splitmix64."""
+    centres, radii = [], []
+    ctr = 0
+    tries = 0
+    while len(radii) < n_spheres and tries < max_tries:
+        r = uniform(seed, 4, offset=ctr)
+        ctr += 4
+        tries += 1
+        R = 0.5 * (dmin + (dmax - dmin) * r[0])
+        c = np.array([R + gap + 1.0 + r[1] * (nx - 2 * (R + gap + 1.0) - 1.0), r[2] * ny, r[3] * nz])
+        ok = True
+        for c2, R2 in zip(centres, radii):
+            d = c - c2
+            d[1] -= ny * round(d[1] / ny)
+            d[2] -= nz * round(d[2] / nz)
+            if math.sqrt(float(d @ d)) < R + R2 + gap:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+            radii.append(R)
+    flags = channel_flags(nx, ny, nz, periodic_x=False)
+    links = add_spheres(flags, centres, radii)
+    N = nx * ny * nz
+    u = np.zeros((3, N))
+    u[0] = u_in
+    return {"dims": (nx, ny, nz), "flags": flags.reshape(-1), "links": links,
+            "rho": np.ones(N), "u": u, "T": np.full(N, T_in), "periodic_x": False,
+            "nwalls": 1, "centres": np.array(centres), "radii": np.array(radii),
+            "u_in": (u_in, 0.0, 0.0), "T_in": T_in}
