@@ -1,0 +1,369 @@
+"""Benchmark of the coupled f+h stream+collide step (MLUPS and fraction of the
+HBM roofline) on synthetic inputs.
+
+Workload (default): heated sphere in a channel, 384 x 128 x 128 nodes, sphere
+diameter 32 at x = 96 (seeded sub-lattice offset), inlet u = 0.02 / T = 0,
+sphere wall T = 1, zero-gradient outlet, periodic y/z; D3Q27 cumulant f and
+D3Q27 CM-TRT h; nu = 0.032, Pr = 1000; populations stored in FP32 (FP16 and
+BF16 storage are timed beside it).  One bench step = one lattice time step
+over the whole grid (one kernel launch).  The population arrays (2 x 1.36 GB
+read+written per step) are far larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank advances its own replica:
+the method has no data-parallel exchange on one grid here ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS of coupled f+h step and % of HBM roofline; adjoint/forward time ratio"
+WORKLOAD = dict(nx=384, ny=128, nz=128, D=32.0, cx=96.0, seed=1234, u_in=0.02, T_in=0.0, T_wall=1.0,
+                nu=0.032, Pr=1000.0)
+BYTES_PER_VALUE = {"f32": 4, "f64": 8, "f16": 2, "bf16": 2}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh", "lbm_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_01316_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel_key)
+    if not d or d.get("src_hash") != kernel_source_hash():
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+def make_workload(scale=1.0):
+    from paper_2203_01316_gb300 import inputs as I
+    W = WORKLOAD
+    nx, ny, nz = (max(8, int(round(W[k] * scale))) for k in ("nx", "ny", "nz"))
+    w = I.heated_sphere(nx, ny, nz, D=W["D"] * scale, cx=W["cx"] * scale, seed=W["seed"], u_in=W["u_in"],
+                        T_in=W["T_in"])
+    return w
+
+
+def make_solver(w, storage, stream=None):
+    from paper_2203_01316_gb300 import Solver
+    nx, ny, nz = w["dims"]
+    W = WORKLOAD
+    s = Solver(nx, ny, nz, nu=W["nu"], Pr=W["Pr"], lat_h=27, hkind="trt", storage=storage, periodic_x=False,
+               rho0=1.0, T_ref=0.5, stream=stream)
+    s.set_geometry(w["flags"], w["links"], n_walls=1)
+    s.set_bc(0, W["T_wall"])
+    s.set_inlet(w["u_in"], w["T_in"])
+    return s
+
+
+def time_steps(s, steps, warmup, stream):
+    import torch
+    s.step(warmup)
+    torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def oracle_rate(budget_s, max_steps=None):
+    """FP64 oracle on a scaled copy of the workload (same shape, fewer
+    nodes); returns (MLUPS, cores, sample description, steps run)."""
+    from oracle import oracle as O
+    probe = make_workload(scale=1 / 16)
+    nx, ny, nz = probe["dims"]
+    W = WORKLOAD
+    def run(w, steps):
+        nx, ny, nz = w["dims"]
+        p = O.make_params(nx=nx, ny=ny, nz=nz, qh=27, hkind="trt", periodic_x=False, nu=W["nu"],
+                          k=W["nu"] / W["Pr"], u_in=w["u_in"], T_in=w["T_in"])
+        o = O.Oracle(p)
+        o.set_geometry(w["flags"], w["links"], nwalls=1)
+        o.set_wall_temperature(0, W["T_wall"])
+        o.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        t = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t
+        o.close()
+        return dt
+    dt = run(probe, 1)
+    rate = nx * ny * nz / dt
+    # largest scaled workload whose steps fit the budget
+    scale = 1 / 16
+    for sc in (1 / 2, 1 / 3, 1 / 4, 1 / 6, 1 / 8, 1 / 12, 1 / 16):
+        n = (WORKLOAD["nx"] * sc) * (WORKLOAD["ny"] * sc) * (WORKLOAD["nz"] * sc)
+        if n * (max_steps or 2) / rate <= budget_s:
+            scale = sc
+            break
+    w = make_workload(scale)
+    nx, ny, nz = w["dims"]
+    steps = max_steps or max(1, int(budget_s * rate / (nx * ny * nz)))
+    dt = run(w, steps)
+    sample = (f"heated-sphere channel scaled by {scale:.4g}: {nx}x{ny}x{nz} nodes, sphere D="
+              f"{WORKLOAD['D'] * scale:.3g}, {steps} oracle steps (FP64, OpenMP)")
+    return nx * ny * nz * steps / dt / 1e6, O.num_threads(), sample, steps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    # each reference step is one oracle step on a scaled copy of the workload,
+    # sized so W + K steps take about a minute of host time
+    from oracle import oracle as O  # noqa: F811
+    budget = 60.0
+    probe = make_workload(scale=1 / 16)
+    nx, ny, nz = probe["dims"]
+    p = O.make_params(nx=nx, ny=ny, nz=nz, periodic_x=False, nu=WORKLOAD["nu"], k=WORKLOAD["nu"] / WORKLOAD["Pr"],
+                      u_in=probe["u_in"], T_in=probe["T_in"])
+    o = O.Oracle(p)
+    o.set_geometry(probe["flags"], probe["links"], nwalls=1)
+    o.init_fields(probe["rho"], probe["u"].reshape(-1), probe["T"])
+    t = time.perf_counter(); o.step(1); rate = nx * ny * nz / (time.perf_counter() - t)
+    o.close()
+    per_step = budget * rate / max(1, args.steps + args.warmup)
+    scale = 1 / 16
+    for sc in (1 / 2, 1 / 3, 1 / 4, 1 / 6, 1 / 8, 1 / 12, 1 / 16, 1 / 24, 1 / 32):
+        if (WORKLOAD["nx"] * sc) * (WORKLOAD["ny"] * sc) * (WORKLOAD["nz"] * sc) <= per_step:
+            scale = sc
+            break
+    w = make_workload(scale)
+    nx, ny, nz = w["dims"]
+    p = O.make_params(nx=nx, ny=ny, nz=nz, periodic_x=False, nu=WORKLOAD["nu"], k=WORKLOAD["nu"] / WORKLOAD["Pr"],
+                      u_in=w["u_in"], T_in=w["T_in"])
+    o = O.Oracle(p)
+    o.set_geometry(w["flags"], w["links"], nwalls=1)
+    o.set_wall_temperature(0, WORKLOAD["T_wall"])
+    o.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    value = nx * ny * nz * args.steps / dt / 1e6
+    sample = f"heated-sphere channel scaled by {scale:.4g}: {nx}x{ny}x{nz} nodes per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config():
+    W = WORKLOAD
+    return {"workload": f"heated sphere channel {W['nx']}x{W['ny']}x{W['nz']}, D={W['D']:g}, "
+                        f"D3Q27 cumulant f + D3Q27 CM-TRT h, IBB/IABB, Pr={W['Pr']:g}",
+            "grid": [W["nx"], W["ny"], W["nz"]], "storage": "f32", "lattice": "D3Q27/D3Q27",
+            "parallelism": "replicas", "l2": "inputs larger than L2 (2.7 GB population traffic per step)"}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2203_01316_gb300 import build
+    build.build()
+    # a dedicated stream: the library launches on it and the events bracket it
+    stream = torch.cuda.Stream()
+    w = make_workload()
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    flags = np.asarray(w["flags"])
+    n_active = int(np.count_nonzero(flags != 1))
+    s = make_solver(w, "f32", stream=stream.cuda_stream)
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    with ClockSampler(local) as clk:
+        dt = time_steps(s, args.steps, args.warmup, stream)
+    if ws > 1:
+        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    mass, energy = s.balances()  # also checks that nothing diverged
+    value = ws * N * args.steps / dt / 1e6
+    ms = dt / args.steps * 1e3
+    bpv = BYTES_PER_VALUE["f32"]
+    alg_bytes = n_active * 2 * (27 + 27) * bpv
+    hbm, src = peaks()
+    achieved = alg_bytes / (dt / args.steps) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "peak_source": src, "kernel": "k_step<float,27>",
+            "traffic": recorded_traffic("k_step_f32_q27_heated_sphere_384"),
+            "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the public API with host buffers: fields from pinned
+    # host memory -> K steps -> macroscopic fields back to pinned host memory
+    rho_h = torch.from_numpy(w["rho"]).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(w["u"].reshape(-1))).pin_memory()
+    T_h = torch.from_numpy(w["T"]).pin_memory()
+    out = [torch.empty(N, dtype=torch.float64).pin_memory(), torch.empty(3 * N, dtype=torch.float64).pin_memory(),
+           torch.empty(N, dtype=torch.float64).pin_memory()]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init_fields(rho_h.numpy(), u_h.numpy(), T_h.numpy())
+    s.step(args.steps)
+    r = s.L.lbm_macros(s._h, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), 0)
+    t1 = time.perf_counter()
+    if r != 0:
+        raise RuntimeError("lbm_macros failed in the end-to-end run")
+    e2e = {"value": N * args.steps / (t1 - t0) / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 5 * N * 8 / args.steps, "d2h_bytes_per_step": 5 * N * 8 / args.steps,
+           "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_macros(host)"}
+    s.close()
+    del s
+
+    variants = {}
+    vsteps = max(10, args.steps // 3)
+    for storage in ("f16", "bf16"):
+        sv = make_solver(w, storage, stream=stream.cuda_stream)
+        sv.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        dtv = time_steps(sv, vsteps, max(3, args.warmup // 3), stream)
+        bv = n_active * 2 * 54 * BYTES_PER_VALUE[storage]
+        variants[storage] = {"value": N * vsteps / dtv / 1e6, "unit": "MLUPS", "steps": vsteps,
+                             "achieved_GBs": bv / (dtv / vsteps) / 1e9,
+                             "frac": bv / (dtv / vsteps) / 1e9 / hbm}
+        sv.close()
+
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+            "fluid_mlups": ws * n_active * args.steps / dt / 1e6,
+            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk.summary(), "storage_variants": variants,
+            "balances": {"mass": mass, "energy": energy}}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        v, cores, sample, steps, odt = oracle_rate(budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) thermal lattice Boltzmann library.
+ *
+ * The library advances the double-distribution thermal LBM of
+ * Gruszczynski & Laniewski-Wollk (arXiv 2203.01316) on one GPU: flow
+ * populations f (D3Q27, cumulant collision, Sec. 2.1.1 Eq. hydro_cu_collision)
+ * and internal-energy populations h (D3Q27 or D3Q7, central-moment collision,
+ * Eq. H_cm_collision, kinds CM-TRT / CM-SRT / CM-1st), streamed with
+ * interpolated bounce-back for f (Sec. 3, Eq. IBB) and interpolated
+ * anti-bounce-back Dirichlet walls for h (Sec. 3, Eq. IABB) on every wall link
+ * with its wall-distance fraction q.
+ *
+ * Conventions used by every call:
+ *  - Grid nx x ny x nz, node index n = x + nx*(y + ny*z).  y and z are
+ *    periodic.  x is periodic, or bounded by an inlet plane (x = 0) and an
+ *    outlet plane (x = nx-1).
+ *  - Velocity a is the a-th vector of the paper's D3Q27 list (Sec. 2.1); D3Q7
+ *    uses the vectors {0,+x,+y,+z,-x,-y,-z} = D3Q27 indices {0,1,2,3,7,8,9}.
+ *  - Population arrays are structure-of-arrays [Q][N] (all N values of
+ *    velocity 0, then velocity 1, ...).
+ *  - `is_device` = 1 means the pointer is CUDA device memory (for example a
+ *    torch tensor's data_ptr()), 0 means host memory.  The library copies what
+ *    it needs; the caller keeps ownership of every buffer it passes.
+ *  - The library owns all the device memory of a context.  Calls are
+ *    asynchronous on the context's stream unless stated otherwise.
+ *  - Every call returns an lbm_status; none aborts or prints.  On failure
+ *    lbm_last_error() gives a message.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = 1,  /* bad argument or geometry; nothing changed */
+    LBM_ERR_NOMEM = 2,    /* device or host allocation failed */
+    LBM_ERR_CUDA = 3,     /* a CUDA call failed; message holds its text */
+    LBM_ERR_DIVERGED = 4, /* a non-finite population was found */
+    LBM_ERR_STATE = 5     /* call out of order (e.g. step before geometry) */
+} lbm_status;
+
+typedef enum { LBM_D3Q27 = 27, LBM_D3Q7 = 7 } lbm_lattice;
+
+/* Sec. 2.1.1: rates of the h central moments (s^H = 1/(3k + 1/2)).
+ * TRT: odd orders s^H, even orders 1.  SRT: all s^H.  1ST: order 1 s^H,
+ * higher orders 1. */
+typedef enum { LBM_H_CM_TRT = 0, LBM_H_CM_SRT = 1, LBM_H_CM_1ST = 2 } lbm_hkind;
+
+/* Storage of populations in HBM.  Every type stores the shifted values
+ * f - w*rho0 and h - w*T_ref; arithmetic is FP32 (FP64 for LBM_F64). */
+typedef enum { LBM_F32 = 0, LBM_F64 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_storage;
+
+typedef struct {
+    int nx, ny, nz;      /* grid; nx*ny*nz*27 must stay below 2^31 */
+    int lat_h;           /* lbm_lattice of h */
+    int hkind;           /* lbm_hkind */
+    int storage;         /* lbm_storage */
+    int periodic_x;      /* 1: periodic x; 0: inlet plane x=0, outlet x=nx-1 */
+    double nu;           /* kinematic viscosity (lattice units), > 0 */
+    double k;            /* thermal diffusivity k (rho c_v = 1), > 0, or 0 to derive from Pr */
+    double Pr;           /* Prandtl number nu/k, or 0 to derive from k; if both are
+                            given they must agree to 1e-12 relative */
+    double omega_bulk;   /* relaxation rate of the trace of the second-order
+                            cumulants (0 < omega_bulk < 2); 1 sets it to equilibrium */
+    double rho0, T_ref;  /* shift references of the stored populations */
+    void* cuda_stream;   /* cudaStream_t to run on; NULL = the library creates one */
+} lbm_params;
+
+/* Create a context and allocate its device state.  The populations are zero
+ * until lbm_init_fields.  Errors: LBM_ERR_INVALID (parameters), NOMEM, CUDA. */
+lbm_status lbm_create(const lbm_params* params, lbm_ctx** out);
+
+/* Free every resource of the context (synchronises its stream). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Geometry (Sec. 3).  flags: uint8[N], 0 fluid, 1 solid, 2 inlet, 3 outlet.
+ * Wall links: n_links entries (link_node[l], link_dir[l]) meaning node
+ * link_node is fluid and link_node + e_{link_dir} is solid; link_q in (0,1]
+ * is the fraction of the link at which the wall lies (Eq. IBB's q);
+ * link_wall in [0, n_walls) names the wall, whose temperature lbm_set_bc
+ * sets.  Rules checked (LBM_ERR_INVALID otherwise): with periodic_x = 0 the
+ * x = 0 plane is all inlet, x = nx-1 all outlet, and x = nx-2 holds no solid;
+ * inlet/outlet flags appear nowhere else; every fluid->solid link is listed
+ * exactly once.  Links may come in any order.  Replaces any earlier geometry;
+ * the populations must be (re)initialised afterwards. */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, int64_t n_links,
+                            const int32_t* link_node, const int32_t* link_dir,
+                            const float* link_q, const int32_t* link_wall, int n_walls,
+                            int is_device);
+
+/* Dirichlet temperature of wall `wall_id` for Eq. IABB (h^eq_i(x_w) = w_i T_w,
+ * wall velocity zero).  Takes effect at the next step. */
+lbm_status lbm_set_bc(lbm_ctx* ctx, int wall_id, double T_wall);
+
+/* Inlet plane state: post-collision populations there are the equilibria at
+ * (rho = 1, u_in) and (T_in, u_in). */
+lbm_status lbm_set_inlet(lbm_ctx* ctx, double ux, double uy, double uz, double T_in);
+
+/* Uniform body force on f: collision adds F to the momentum, and
+ * u = (sum e f + F/2)/rho is the velocity used for h. */
+lbm_status lbm_set_force(lbm_ctx* ctx, double Fx, double Fy, double Fz);
+
+/* Per-node heat source Q (float[N]) of Appendix D; NULL clears it.  The
+ * library keeps the App. D shifted variable h - q/2 internally. */
+lbm_status lbm_set_source(lbm_ctx* ctx, const float* theta, int is_device);
+
+/* Initialise every node at equilibrium: f^eq(rho, u), h^eq(rho*T, u) (then
+ * the App. D shift), and apply one collision so the stored state is
+ * post-collision.  rho[N], u[3*N] (all x, then all y, then all z), T[N],
+ * double.  Solid nodes are ignored; inlet nodes take the inlet state. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* T,
+                           int is_device);
+
+/* Advance n time steps (pull streaming + walls + planes + collision of f
+ * and h), asynchronously on the context's stream.  n >= 0. */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of the current time level (Sec. 2.1): rho, u (3*N,
+ * SoA), T = H/rho with H = sum h + Q/2; double.  Solid nodes give 0, inlet
+ * nodes the inlet state.  Synchronises; LBM_ERR_DIVERGED if a value is
+ * non-finite. */
+lbm_status lbm_macros(lbm_ctx* ctx, double* rho, double* u, double* T, int is_device);
+
+/* Post-collision populations of the current time level, unshifted, double:
+ * f[27*N], h[Q_h*N].  Either pointer may be NULL.  Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* h, int is_device);
+
+/* FP64 totals over non-solid nodes of rho and H.  Synchronises;
+ * LBM_ERR_DIVERGED if any population is non-finite. */
+lbm_status lbm_balances(lbm_ctx* ctx, double* mass, double* energy);
+
+/* Surface heat flux of wall `wall_id` for the transition from the current
+ * time level to the next (Sec. 4.4): the sum over that wall's IABB links of
+ * h_ibar(x_b, t+1) - h*_i(x_b, t), FP64.  Synchronises. */
+lbm_status lbm_surface_flux(lbm_ctx* ctx, int wall_id, double* flux);
+
+/* Nusselt number Nu = flux * length / (k * area * dT) (Sec. 4.4), with the
+ * flux of lbm_surface_flux.  Synchronises. */
+lbm_status lbm_nusselt(lbm_ctx* ctx, int wall_id, double length, double area, double dT,
+                       double* nu_out);
+
+/* Bytes needed by lbm_save_state. */
+lbm_status lbm_state_size(lbm_ctx* ctx, size_t* bytes);
+
+/* Copy the stored populations (with a header naming the grid, lattice and
+ * storage) to host memory of *bytes bytes; *bytes is set to the size used.
+ * Synchronises. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t* bytes);
+
+/* Restore a state written by lbm_save_state of a context with the same grid,
+ * lattice and storage (LBM_ERR_INVALID otherwise). */
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Streaming map used by the step: src[a*N + n] = node whose post-collision
+ * population a arrives at node n, -1 where a wall link replaces it, -2 for
+ * nodes that do not pull (solid, inlet).  int32[27*N]; is_device as above.
+ * Synchronises. */
+lbm_status lbm_stream_map(lbm_ctx* ctx, int32_t* src, int is_device);
+
+/* The wall links as stored by the library, sorted by (node, dir): up to
+ * *n_links entries are written; *n_links is set to the total.  Host memory.
+ * Synchronises. */
+lbm_status lbm_get_links(lbm_ctx* ctx, int64_t* n_links, int32_t* node, int32_t* dir,
+                         float* q, int32_t* wall);
+
+/* Wait for the context's stream; reports an asynchronous CUDA error. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Message of the last failed call on this context (or of lbm_create when
+ * ctx is NULL).  Valid until the next call. */
+const char* lbm_last_error(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

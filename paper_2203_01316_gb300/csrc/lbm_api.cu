@@ -1,0 +1,772 @@
+// Host implementation of the C ABI declared in include/lbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+using lbmd::Acc;
+using lbmd::Buffers;
+using lbmd::DevParams;
+
+struct lbm_ctx {
+    lbm_params p{};
+    int N = 0, qh = 27;
+    size_t ssize = 4;  // bytes per stored value
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    void* f[2] = {nullptr, nullptr};
+    void* h[2] = {nullptr, nullptr};
+    int cur = 0;  // f[cur], h[cur] hold the post-collision state of the current time level
+    uint8_t* d_flags = nullptr;
+    int nw = 0;
+    int32_t* d_wnode = nullptr;
+    int32_t* d_segbase = nullptr;
+    uint32_t* d_wmask = nullptr;
+    int32_t* d_woff = nullptr;
+    int64_t nl = 0;
+    float* d_lq = nullptr;
+    int32_t* d_lwall = nullptr;
+    int n_walls = 1;
+    float* d_Twall = nullptr;
+    std::vector<float> Twall{0.0f};
+    float* d_theta = nullptr;
+    void* d_inlet = nullptr;  // R[27 + qh]
+    double* d_scratch = nullptr;  // 3 * kRedBlocks partials + 4 results
+    double* d_stage = nullptr;    // 5 * N doubles for host-side outputs
+    int64_t n_fluid_like = 0;     // non-solid node count
+    bool geometry = false, initialised = false;
+    std::vector<int32_t> h_lnode, h_ldir, h_lwall;
+    std::vector<float> h_lq;
+    DevParams dp{};
+    std::string err;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+template <typename S_, int Q_> struct Tag {
+    using S = S_;
+    static constexpr int Q = Q_;
+};
+
+template <typename Fn> cudaError_t dispatch(const lbm_ctx* c, Fn&& fn) {
+    const bool q27 = c->qh == 27;
+    switch (c->p.storage) {
+        case LBM_F32: return q27 ? fn(Tag<float, 27>{}) : fn(Tag<float, 7>{});
+        case LBM_F64: return q27 ? fn(Tag<double, 27>{}) : fn(Tag<double, 7>{});
+        case LBM_F16_SHIFTED: return q27 ? fn(Tag<__half, 27>{}) : fn(Tag<__half, 7>{});
+        default: return q27 ? fn(Tag<__nv_bfloat16, 27>{}) : fn(Tag<__nv_bfloat16, 7>{});
+    }
+}
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+Buffers buffers(const lbm_ctx* c) {
+    Buffers b{};
+    b.fA = c->f[c->cur];
+    b.fB = c->f[1 - c->cur];
+    b.hA = c->h[c->cur];
+    b.hB = c->h[1 - c->cur];
+    b.flags = c->d_flags;
+    b.theta = c->d_theta;
+    b.inlet_post = c->d_inlet;
+    b.wnode = c->d_wnode;
+    b.seg_base = c->d_segbase;
+    b.wmask = c->d_wmask;
+    b.woff = c->d_woff;
+    b.lq = c->d_lq;
+    b.lwall = c->d_lwall;
+    b.Twall = c->d_Twall;
+    b.nw = c->nw;
+    return b;
+}
+
+// 1-D equilibrium weight of velocity e at velocity u (product form of the
+// discrete Maxwellian of Appendix A)
+double w1eq(int e, double u) {
+    const double cs2 = 1.0 / 3.0;
+    return e == 0 ? 1.0 - u * u - cs2 : 0.5 * (u * u + e * u + cs2);
+}
+
+// inlet post-collision deviations (f^eq(1, u_in) - w rho0, h^eq(T_in, u_in) - w Tref)
+lbm_status upload_inlet(lbm_ctx* c) {
+    std::vector<double> v(27 + c->qh);
+    const double* u = c->dp.uin;
+    for (int a = 0; a < 27; ++a) {
+        const int ex = lbmd::EX(a), ey = lbmd::EY(a), ez = lbmd::EZ(a);
+        v[a] = w1eq(ex, u[0]) * w1eq(ey, u[1]) * w1eq(ez, u[2]) - lbmd::W27(a) * c->dp.rho0;
+    }
+    const double T = c->dp.Tin, cs2 = 1.0 / 3.0;
+    if (c->qh == 27) {
+        for (int a = 0; a < 27; ++a)
+            v[27 + a] = T * w1eq(lbmd::EX(a), u[0]) * w1eq(lbmd::EY(a), u[1]) * w1eq(lbmd::EZ(a), u[2]) -
+                        lbmd::W27(a) * c->dp.Tref;
+    } else {
+        double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        v[27] = T * (1.0 - 3.0 * cs2 - u2);
+        for (int d = 0; d < 3; ++d) {
+            v[28 + d] = 0.5 * T * (cs2 + u[d] * u[d] + u[d]) - c->dp.Tref / 6.0;
+            v[31 + d] = 0.5 * T * (cs2 + u[d] * u[d] - u[d]) - c->dp.Tref / 6.0;
+        }
+    }
+    if (c->p.storage == LBM_F64) {
+        CK(cudaMemcpyAsync(c->d_inlet, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+           "inlet upload");
+    } else {
+        std::vector<float> vf(v.begin(), v.end());
+        CK(cudaMemcpyAsync(c->d_inlet, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "inlet upload");
+    }
+    CK(cudaStreamSynchronize(c->stream), "inlet upload");
+    return LBM_OK;
+}
+
+void free_geometry(lbm_ctx* c) {
+    cudaFree(c->d_wnode);
+    cudaFree(c->d_segbase);
+    cudaFree(c->d_wmask);
+    cudaFree(c->d_woff);
+    cudaFree(c->d_lq);
+    cudaFree(c->d_lwall);
+    c->d_wnode = nullptr;
+    c->d_segbase = nullptr;
+    c->d_wmask = nullptr;
+    c->d_woff = nullptr;
+    c->d_lq = nullptr;
+    c->d_lwall = nullptr;
+    c->nw = 0;
+    c->nl = 0;
+}
+
+template <typename T> lbm_status to_host(lbm_ctx* c, const T* src, size_t count, int is_device, std::vector<T>& out) {
+    out.resize(count);
+    if (count == 0) return LBM_OK;
+    if (!src) return fail(c, LBM_ERR_INVALID, "null array");
+    if (is_device) {
+        CK(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost), "device->host copy");
+    } else {
+        std::memcpy(out.data(), src, count * sizeof(T));
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
+    g_create_err.clear();
+    if (!params || !out) return fail(nullptr, LBM_ERR_INVALID, "null argument");
+    *out = nullptr;
+    lbm_params p = *params;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return fail(nullptr, LBM_ERR_INVALID, "grid dimensions must be >= 1");
+    const int64_t N = (int64_t)p.nx * p.ny * p.nz;
+    if (N * 27 >= (int64_t(1) << 31)) return fail(nullptr, LBM_ERR_INVALID, "nx*ny*nz*27 must stay below 2^31");
+    if (!p.periodic_x && p.nx < 4) return fail(nullptr, LBM_ERR_INVALID, "an inlet/outlet channel needs nx >= 4");
+    if (p.lat_h != 27 && p.lat_h != 7) return fail(nullptr, LBM_ERR_INVALID, "lat_h must be 27 or 7");
+    if (p.hkind < 0 || p.hkind > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown hkind");
+    if (p.storage < 0 || p.storage > 3) return fail(nullptr, LBM_ERR_INVALID, "unknown storage");
+    if (!(p.nu > 0.0) || !std::isfinite(p.nu)) return fail(nullptr, LBM_ERR_INVALID, "nu must be > 0");
+    double k = p.k, Pr = p.Pr;
+    if (k > 0.0 && Pr > 0.0) {
+        if (std::fabs(p.nu / k - Pr) > 1e-12 * Pr) return fail(nullptr, LBM_ERR_INVALID, "nu/k disagrees with Pr");
+    } else if (k > 0.0) {
+        Pr = p.nu / k;
+    } else if (Pr > 0.0) {
+        k = p.nu / Pr;
+    } else {
+        return fail(nullptr, LBM_ERR_INVALID, "one of k, Pr must be > 0");
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) return fail(nullptr, LBM_ERR_INVALID, "k must be > 0");
+    if (!(p.omega_bulk > 0.0 && p.omega_bulk < 2.0))
+        return fail(nullptr, LBM_ERR_INVALID, "omega_bulk must lie in (0, 2)");
+    p.k = k;
+    p.Pr = Pr;
+
+    lbm_ctx* ctx = new lbm_ctx();
+    lbm_ctx* c = ctx;
+    c->p = p;
+    c->N = (int)N;
+    c->qh = p.lat_h;
+    c->ssize = p.storage == LBM_F64 ? 8 : (p.storage == LBM_F32 ? 4 : 2);
+    cudaGetDevice(&c->device);
+    auto bail = [&](lbm_status s) {
+        g_create_err = c->err;
+        lbm_destroy(ctx);
+        return s;
+    };
+    if (p.cuda_stream) {
+        c->stream = (cudaStream_t)p.cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "stream create"));
+        c->own_stream = true;
+    }
+    const size_t fb = (size_t)27 * N * c->ssize, hb = (size_t)c->qh * N * c->ssize;
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&c->f[i], fb) != cudaSuccess || cudaMalloc(&c->h[i], hb) != cudaSuccess)
+            return bail(fail(c, LBM_ERR_NOMEM, "population arrays: out of device memory"));
+        cudaMemsetAsync(c->f[i], 0, fb, c->stream);
+        cudaMemsetAsync(c->h[i], 0, hb, c->stream);
+    }
+    if (cudaMalloc(&c->d_flags, N) != cudaSuccess ||
+        cudaMalloc(&c->d_inlet, (27 + 27) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_scratch, (3 * lbmd::kRedBlocks + 4) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_Twall, sizeof(float)) != cudaSuccess)
+        return bail(fail(c, LBM_ERR_NOMEM, "context buffers: out of device memory"));
+    cudaMemsetAsync(c->d_flags, 0, N, c->stream);
+    cudaMemsetAsync(c->d_Twall, 0, sizeof(float), c->stream);
+
+    DevParams& d = c->dp;
+    d.nx = p.nx;
+    d.ny = p.ny;
+    d.nz = p.nz;
+    d.N = (int)N;
+    d.periodic_x = p.periodic_x ? 1 : 0;
+    d.omega1 = 1.0 / (3.0 * p.nu + 0.5);
+    d.omega_bulk = p.omega_bulk;
+    const double sH = 1.0 / (3.0 * k + 0.5);  // Sec. 2.1.1: s^H = 1/(k/cs^2 + 1/2)
+    for (int o = 0; o <= 6; ++o) {
+        double s = 1.0;
+        if (p.hkind == LBM_H_CM_SRT) s = sH;
+        else if (p.hkind == LBM_H_CM_1ST) s = (o == 1) ? sH : 1.0;
+        else s = (o % 2 == 1) ? sH : 1.0;
+        d.sh[o] = s;
+    }
+    d.rho0 = p.rho0;
+    d.Tref = p.T_ref;
+    for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
+    d.Tin = 0.0;
+    lbm_status s = upload_inlet(c);
+    if (s != LBM_OK) return bail(s);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "create"));
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->f[i]);
+        cudaFree(c->h[i]);
+    }
+    free_geometry(c);
+    cudaFree(c->d_flags);
+    cudaFree(c->d_inlet);
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_Twall);
+    cudaFree(c->d_theta);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, const int32_t* link_node,
+                            const int32_t* link_dir, const float* link_q, const int32_t* link_wall, int n_walls,
+                            int is_device) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (n_links < 0 || n_walls < 1 || n_walls > (1 << 20)) return fail(c, LBM_ERR_INVALID, "bad n_links or n_walls");
+    const int N = c->N, nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    std::vector<uint8_t> fl;
+    std::vector<int32_t> ln, ld, lw;
+    std::vector<float> lq;
+    lbm_status s;
+    if ((s = to_host(c, flags, (size_t)N, is_device, fl)) != LBM_OK) return s;
+    if ((s = to_host(c, link_node, (size_t)n_links, is_device, ln)) != LBM_OK) return s;
+    if ((s = to_host(c, link_dir, (size_t)n_links, is_device, ld)) != LBM_OK) return s;
+    if ((s = to_host(c, link_q, (size_t)n_links, is_device, lq)) != LBM_OK) return s;
+    if ((s = to_host(c, link_wall, (size_t)n_links, is_device, lw)) != LBM_OK) return s;
+
+    auto nbr = [&](int n, int ex, int ey, int ez) -> int {
+        int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+        x += ex;
+        y = (y + ey + ny) % ny;
+        z = (z + ez + nz) % nz;
+        if (c->p.periodic_x) x = (x + nx) % nx;
+        else if (x < 0 || x >= nx) return -1;
+        return x + nx * (y + ny * z);
+    };
+    int64_t nonsolid = 0;
+    for (int n = 0; n < N; ++n) {
+        const uint8_t t = fl[n];
+        if (t > 3) return fail(c, LBM_ERR_INVALID, "flag value above 3 at node " + std::to_string(n));
+        const int x = n % nx;
+        if (c->p.periodic_x) {
+            if (t == lbmd::T_INLET || t == lbmd::T_OUTLET)
+                return fail(c, LBM_ERR_INVALID, "inlet/outlet flag in a periodic-x grid");
+        } else {
+            if ((x == 0) != (t == lbmd::T_INLET)) return fail(c, LBM_ERR_INVALID, "the x=0 plane must be all inlet");
+            if ((x == nx - 1) != (t == lbmd::T_OUTLET))
+                return fail(c, LBM_ERR_INVALID, "the x=nx-1 plane must be all outlet");
+            if (x == nx - 2 && t == lbmd::T_SOLID) return fail(c, LBM_ERR_INVALID, "solid node next to the outlet");
+        }
+        if (t != lbmd::T_SOLID) ++nonsolid;
+    }
+    // links: validate, sort by (node, dir)
+    std::vector<int64_t> order(n_links);
+    for (int64_t l = 0; l < n_links; ++l) {
+        const int n = ln[l], a = ld[l];
+        if (n < 0 || n >= N || a < 1 || a >= 27) return fail(c, LBM_ERR_INVALID, "link node/dir out of range");
+        if (fl[n] != lbmd::T_FLUID) return fail(c, LBM_ERR_INVALID, "link from a non-fluid node " + std::to_string(n));
+        const int t = nbr(n, lbmd::EX(a), lbmd::EY(a), lbmd::EZ(a));
+        if (t < 0 || fl[t] != lbmd::T_SOLID)
+            return fail(c, LBM_ERR_INVALID, "link target is not solid (node " + std::to_string(n) + ")");
+        if (!(lq[l] > 0.0f && lq[l] <= 1.0f)) return fail(c, LBM_ERR_INVALID, "link q outside (0,1]");
+        if (lw[l] < 0 || lw[l] >= n_walls) return fail(c, LBM_ERR_INVALID, "link wall id out of range");
+        order[l] = l;
+    }
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return ln[a] != ln[b] ? ln[a] < ln[b] : ld[a] < ld[b];
+    });
+    std::vector<int32_t> wnode, woff;
+    std::vector<uint32_t> wmask;
+    std::vector<int32_t> sn(n_links), sd(n_links), sw(n_links);
+    std::vector<float> sq(n_links);
+    for (int64_t i = 0; i < n_links; ++i) {
+        const int64_t l = order[i];
+        sn[i] = ln[l];
+        sd[i] = ld[l];
+        sq[i] = lq[l];
+        sw[i] = lw[l];
+        if (i > 0 && sn[i] == sn[i - 1] && sd[i] == sd[i - 1]) return fail(c, LBM_ERR_INVALID, "duplicate link");
+        if (i == 0 || sn[i] != sn[i - 1]) {
+            wnode.push_back(sn[i]);
+            woff.push_back((int32_t)i);
+            wmask.push_back(0u);
+        }
+        wmask.back() |= 1u << sd[i];
+    }
+    // completeness: every fluid->solid link listed; outlet nodes see no solid
+    std::vector<uint8_t> iflags(fl);
+    size_t wi = 0;
+    for (int n = 0; n < N; ++n) {
+        if (fl[n] == lbmd::T_SOLID || fl[n] == lbmd::T_INLET) continue;
+        uint32_t m = 0;
+        for (int a = 1; a < 27; ++a) {
+            const int t = nbr(n, lbmd::EX(a), lbmd::EY(a), lbmd::EZ(a));
+            if (t >= 0 && fl[t] == lbmd::T_SOLID) m |= 1u << a;
+        }
+        if (!m) continue;
+        if (fl[n] == lbmd::T_OUTLET) return fail(c, LBM_ERR_INVALID, "outlet node next to a solid");
+        while (wi < wnode.size() && wnode[wi] < n) ++wi;
+        if (wi >= wnode.size() || wnode[wi] != n || wmask[wi] != m)
+            return fail(c, LBM_ERR_INVALID, "fluid->solid links of node " + std::to_string(n) + " are not all listed");
+        iflags[n] |= lbmd::F_WALL;
+    }
+    // wall nodes before each 32-node segment (warp) of the step kernel
+    const int nseg = (N + 31) / 32;
+    std::vector<int32_t> segbase(nseg);
+    {
+        size_t k = 0;
+        for (int sgm = 0; sgm < nseg; ++sgm) {
+            while (k < wnode.size() && wnode[k] < sgm * 32) ++k;
+            segbase[sgm] = (int32_t)k;
+        }
+    }
+    // upload
+    free_geometry(c);
+    c->nw = (int)wnode.size();
+    c->nl = n_links;
+    CK(cudaMemcpyAsync(c->d_flags, iflags.data(), N, cudaMemcpyHostToDevice, c->stream), "flags upload");
+    if (c->nw > 0) {
+        if (cudaMalloc(&c->d_wnode, c->nw * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_wmask, c->nw * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_segbase, nseg * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_woff, c->nw * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_lq, n_links * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&c->d_lwall, n_links * sizeof(int32_t)) != cudaSuccess) {
+            free_geometry(c);
+            return fail(c, LBM_ERR_NOMEM, "wall tables: out of device memory");
+        }
+        CK(cudaMemcpyAsync(c->d_wnode, wnode.data(), c->nw * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
+        CK(cudaMemcpyAsync(c->d_segbase, segbase.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
+        CK(cudaMemcpyAsync(c->d_wmask, wmask.data(), c->nw * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
+        CK(cudaMemcpyAsync(c->d_woff, woff.data(), c->nw * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
+        CK(cudaMemcpyAsync(c->d_lq, sq.data(), n_links * sizeof(float), cudaMemcpyHostToDevice, c->stream), "link upload");
+        CK(cudaMemcpyAsync(c->d_lwall, sw.data(), n_links * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "link upload");
+    }
+    if ((int)c->Twall.size() != n_walls) {
+        cudaFree(c->d_Twall);
+        c->d_Twall = nullptr;
+        if (cudaMalloc(&c->d_Twall, n_walls * sizeof(float)) != cudaSuccess)
+            return fail(c, LBM_ERR_NOMEM, "wall temperatures: out of device memory");
+        c->Twall.assign(n_walls, 0.0f);
+    }
+    c->n_walls = n_walls;
+    CK(cudaMemcpyAsync(c->d_Twall, c->Twall.data(), n_walls * sizeof(float), cudaMemcpyHostToDevice, c->stream), "wall T upload");
+    CK(cudaStreamSynchronize(c->stream), "geometry upload");
+    c->h_lnode = std::move(sn);
+    c->h_ldir = std::move(sd);
+    c->h_lq = std::move(sq);
+    c->h_lwall = std::move(sw);
+    c->n_fluid_like = nonsolid;
+    c->geometry = true;
+    c->initialised = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_bc(lbm_ctx* c, int wall_id, double T_wall) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (wall_id < 0 || wall_id >= (int)c->Twall.size()) return fail(c, LBM_ERR_INVALID, "wall id out of range");
+    if (!std::isfinite(T_wall)) return fail(c, LBM_ERR_INVALID, "wall temperature not finite");
+    c->Twall[wall_id] = (float)T_wall;
+    CK(cudaMemcpyAsync(c->d_Twall + wall_id, &c->Twall[wall_id], sizeof(float), cudaMemcpyHostToDevice, c->stream),
+       "wall T upload");
+    CK(cudaStreamSynchronize(c->stream), "wall T upload");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_inlet(lbm_ctx* c, double ux, double uy, double uz, double T_in) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (!std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz) || !std::isfinite(T_in))
+        return fail(c, LBM_ERR_INVALID, "inlet state not finite");
+    c->dp.uin[0] = ux;
+    c->dp.uin[1] = uy;
+    c->dp.uin[2] = uz;
+    c->dp.Tin = T_in;
+    return upload_inlet(c);
+}
+
+lbm_status lbm_set_force(lbm_ctx* c, double Fx, double Fy, double Fz) {
+    if (!c) return LBM_ERR_INVALID;
+    if (!std::isfinite(Fx) || !std::isfinite(Fy) || !std::isfinite(Fz)) return fail(c, LBM_ERR_INVALID, "force not finite");
+    c->dp.F[0] = Fx;
+    c->dp.F[1] = Fy;
+    c->dp.F[2] = Fz;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_source(lbm_ctx* c, const float* theta, int is_device) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (!theta) {
+        CK(cudaStreamSynchronize(c->stream), "source clear");
+        cudaFree(c->d_theta);
+        c->d_theta = nullptr;
+        return LBM_OK;
+    }
+    if (!c->d_theta && cudaMalloc(&c->d_theta, (size_t)c->N * sizeof(float)) != cudaSuccess)
+        return fail(c, LBM_ERR_NOMEM, "source: out of device memory");
+    CK(cudaMemcpyAsync(c->d_theta, theta, (size_t)c->N * sizeof(float),
+                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+       "source upload");
+    CK(cudaStreamSynchronize(c->stream), "source upload");
+    return LBM_OK;
+}
+
+static lbm_status ensure_stage(lbm_ctx* c) {
+    if (!c->d_stage && cudaMalloc(&c->d_stage, (size_t)5 * c->N * sizeof(double)) != cudaSuccess)
+        return fail(c, LBM_ERR_NOMEM, "staging buffer: out of device memory");
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double* T, int is_device) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    if (!rho || !u || !T) return fail(c, LBM_ERR_INVALID, "null field");
+    const size_t N = (size_t)c->N;
+    const double *dr = rho, *du = u, *dT = T;
+    if (!is_device) {
+        lbm_status s = ensure_stage(c);
+        if (s != LBM_OK) return s;
+        CK(cudaMemcpyAsync(c->d_stage, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "fields upload");
+        CK(cudaMemcpyAsync(c->d_stage + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "fields upload");
+        CK(cudaMemcpyAsync(c->d_stage + 4 * N, T, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "fields upload");
+        dr = c->d_stage;
+        du = c->d_stage + N;
+        dT = c->d_stage + 4 * N;
+    }
+    Buffers b = buffers(c);
+    b.fB = c->f[c->cur];  // write the current level in place
+    b.hB = c->h[c->cur];
+    const DevParams p = c->dp;
+    cudaStream_t s = c->stream;
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_init<typename Tg::S, Tg::Q>(b, p, dr, du, dT, s);
+       }),
+       "init launch");
+    if (!is_device) CK(cudaStreamSynchronize(c->stream), "init");
+    c->initialised = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int n) {
+    if (!c) return LBM_ERR_INVALID;
+    if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    DeviceGuard g(c->device);
+    const DevParams p = c->dp;
+    for (int i = 0; i < n; ++i) {
+        const Buffers b = buffers(c);
+        cudaError_t e = dispatch(c, [&](auto tag) {
+            using Tg = decltype(tag);
+            return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c->cur = 1 - c->cur;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx* c, double* rho, double* u, double* T, int is_device) {
+    if (!c) return LBM_ERR_INVALID;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    if (!rho || !u || !T) return fail(c, LBM_ERR_INVALID, "null output");
+    DeviceGuard g(c->device);
+    const size_t N = (size_t)c->N;
+    double *dr = rho, *du = u, *dT = T;
+    if (!is_device) {
+        lbm_status s = ensure_stage(c);
+        if (s != LBM_OK) return s;
+        dr = c->d_stage;
+        du = c->d_stage + N;
+        dT = c->d_stage + 4 * N;
+    }
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_macros<typename Tg::S, Tg::Q>(b, p, dr, du, dT, c->stream);
+       }),
+       "macros launch");
+    if (!is_device) {
+        CK(cudaMemcpyAsync(rho, dr, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "macros copy");
+        CK(cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "macros copy");
+        CK(cudaMemcpyAsync(T, dT, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "macros copy");
+    }
+    CK(cudaStreamSynchronize(c->stream), "macros");
+    if (!is_device) {
+        for (size_t i = 0; i < N; ++i)
+            if (!std::isfinite(rho[i]) || !std::isfinite(T[i]) || !std::isfinite(u[i]) ||
+                !std::isfinite(u[N + i]) || !std::isfinite(u[2 * N + i]))
+                return fail(c, LBM_ERR_DIVERGED, "non-finite macroscopic value at node " + std::to_string(i));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* h, int is_device) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    const size_t N = (size_t)c->N;
+    double *df = f, *dh = h;
+    double* tmp = nullptr;
+    if (!is_device) {
+        if (cudaMalloc(&tmp, (27 + c->qh) * N * sizeof(double)) != cudaSuccess)
+            return fail(c, LBM_ERR_NOMEM, "population staging: out of device memory");
+        df = f ? tmp : nullptr;
+        dh = h ? tmp + 27 * N : nullptr;
+    }
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    cudaError_t e = dispatch(c, [&](auto tag) {
+        using Tg = decltype(tag);
+        return lbmd::launch_populations<typename Tg::S, Tg::Q>(b, p, df, dh, c->stream);
+    });
+    if (e == cudaSuccess && !is_device) {
+        if (f) e = cudaMemcpyAsync(f, df, 27 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && h) e = cudaMemcpyAsync(h, dh, c->qh * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_balances(lbm_ctx* c, double* mass, double* energy) {
+    if (!c) return LBM_ERR_INVALID;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    DeviceGuard g(c->device);
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    double* out = c->d_scratch + 3 * lbmd::kRedBlocks;
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_balances<typename Tg::S, Tg::Q>(b, p, c->d_scratch, out, c->stream);
+       }),
+       "balances launch");
+    double r[3];
+    CK(cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, c->stream), "balances copy");
+    CK(cudaStreamSynchronize(c->stream), "balances");
+    if (mass) *mass = r[0] + c->dp.rho0 * (double)c->n_fluid_like;
+    if (energy) *energy = r[1] + c->dp.Tref * (double)c->n_fluid_like;
+    if (r[2] != 0.0) return fail(c, LBM_ERR_DIVERGED, std::to_string((long long)r[2]) + " nodes hold non-finite populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_surface_flux(lbm_ctx* c, int wall_id, double* flux) {
+    if (!c || !flux) return LBM_ERR_INVALID;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    if (wall_id < 0 || wall_id >= c->n_walls) return fail(c, LBM_ERR_INVALID, "wall id out of range");
+    DeviceGuard g(c->device);
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    double* out = c->d_scratch + 3 * lbmd::kRedBlocks;
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_surface_flux<typename Tg::S, Tg::Q>(b, p, wall_id, c->d_scratch, out, c->stream);
+       }),
+       "flux launch");
+    CK(cudaMemcpyAsync(flux, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "flux copy");
+    CK(cudaStreamSynchronize(c->stream), "flux");
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt(lbm_ctx* c, int wall_id, double length, double area, double dT, double* nu_out) {
+    if (!c || !nu_out) return LBM_ERR_INVALID;
+    if (!(area > 0.0) || dT == 0.0 || !(length > 0.0)) return fail(c, LBM_ERR_INVALID, "length, area must be > 0, dT != 0");
+    double q = 0.0;
+    lbm_status s = lbm_surface_flux(c, wall_id, &q);
+    if (s != LBM_OK) return s;
+    *nu_out = q * length / (c->p.k * area * dT);
+    return LBM_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t nx, ny, nz, qh, storage;
+    uint64_t fbytes, hbytes;
+};
+
+lbm_status lbm_state_size(lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return LBM_ERR_INVALID;
+    *bytes = sizeof(StateHeader) + (size_t)(27 + c->qh) * c->N * c->ssize;
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t* bytes) {
+    if (!c || !bytes || !host_buf) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    size_t need = 0;
+    lbm_state_size(c, &need);
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(c, LBM_ERR_INVALID, "state buffer too small");
+    }
+    StateHeader hd{};
+    std::memcpy(hd.magic, "LBMSTATE", 8);
+    hd.version = 1;
+    hd.nx = c->p.nx;
+    hd.ny = c->p.ny;
+    hd.nz = c->p.nz;
+    hd.qh = c->qh;
+    hd.storage = c->p.storage;
+    hd.fbytes = (uint64_t)27 * c->N * c->ssize;
+    hd.hbytes = (uint64_t)c->qh * c->N * c->ssize;
+    char* out = (char*)host_buf;
+    std::memcpy(out, &hd, sizeof(hd));
+    CK(cudaMemcpyAsync(out + sizeof(hd), c->f[c->cur], hd.fbytes, cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaMemcpyAsync(out + sizeof(hd) + hd.fbytes, c->h[c->cur], hd.hbytes, cudaMemcpyDeviceToHost, c->stream),
+       "state copy");
+    CK(cudaStreamSynchronize(c->stream), "state copy");
+    *bytes = need;
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
+    if (!c || !host_buf) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    StateHeader hd{};
+    if (bytes < sizeof(hd)) return fail(c, LBM_ERR_INVALID, "state buffer too small");
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "LBMSTATE", 8) != 0 || hd.version != 1 || hd.nx != c->p.nx || hd.ny != c->p.ny ||
+        hd.nz != c->p.nz || hd.qh != c->qh || hd.storage != c->p.storage ||
+        hd.fbytes != (uint64_t)27 * c->N * c->ssize || hd.hbytes != (uint64_t)c->qh * c->N * c->ssize ||
+        bytes < sizeof(hd) + hd.fbytes + hd.hbytes)
+        return fail(c, LBM_ERR_INVALID, "state does not match this context");
+    const char* in = (const char*)host_buf;
+    CK(cudaMemcpyAsync(c->f[c->cur], in + sizeof(hd), hd.fbytes, cudaMemcpyHostToDevice, c->stream), "state load");
+    CK(cudaMemcpyAsync(c->h[c->cur], in + sizeof(hd) + hd.fbytes, hd.hbytes, cudaMemcpyHostToDevice, c->stream),
+       "state load");
+    CK(cudaStreamSynchronize(c->stream), "state load");
+    c->initialised = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_stream_map(lbm_ctx* c, int32_t* src, int is_device) {
+    if (!c || !src) return LBM_ERR_INVALID;
+    if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    DeviceGuard g(c->device);
+    const size_t count = (size_t)27 * c->N;
+    int32_t* d = src;
+    if (!is_device && cudaMalloc(&d, count * sizeof(int32_t)) != cudaSuccess)
+        return fail(c, LBM_ERR_NOMEM, "stream map staging: out of device memory");
+    const Buffers b = buffers(c);
+    cudaError_t e = lbmd::launch_stream_map(b, c->dp, c->qh, d, c->stream);
+    if (e == cudaSuccess && !is_device) e = cudaMemcpyAsync(src, d, count * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (!is_device) cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream map");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_links(lbm_ctx* c, int64_t* n_links, int32_t* node, int32_t* dir, float* q, int32_t* wall) {
+    if (!c || !n_links) return LBM_ERR_INVALID;
+    const int64_t cap = *n_links;
+    const int64_t total = (int64_t)c->h_lnode.size();
+    const int64_t m = std::min(cap, total);
+    for (int64_t i = 0; i < m; ++i) {
+        if (node) node[i] = c->h_lnode[i];
+        if (dir) dir[i] = c->h_ldir[i];
+        if (q) q[i] = c->h_lq[i];
+        if (wall) wall[i] = c->h_lwall[i];
+    }
+    *n_links = total;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    CK(cudaGetLastError(), "sync");
+    return LBM_OK;
+}
+
+const char* lbm_last_error(lbm_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

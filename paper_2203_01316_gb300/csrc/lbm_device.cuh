@@ -1,0 +1,395 @@
+// Device-side lattice tables and collision operators of the thermal LBM
+// (arXiv 2203.01316).  Everything here runs in registers of one thread per
+// node.
+//
+// Storage is "deviation" form: a stored f value is f - w*rho0 and a stored h
+// value is h - w*T_ref (h being the App. D shifted variable).  The collision
+// works on the central moments of these deviations,
+//     dk_mno = kappa_mno(f) - rho0 * K_mno(v),
+// where K_mno(v) = K_m(v_x) K_n(v_y) K_o(v_z) are the central moments of the
+// weights about the shift v: K_0 = 1, K_1(v) = -v, K_2(v) = cs^2 + v^2.
+// All quantities handled are then small, so FP32 (and FP16/BF16 storage)
+// keep their relative precision.
+//
+// The central-moment transform T(v) of Appendix C factorises over the three
+// axes (T = T1(v_x) x T1(v_y) x T1(v_z) on the 27-moment set of Sec. 2.1), so
+// it is applied as 3 passes of nine 3-point transforms; the inverse likewise.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmd {
+
+// ---- D3Q27 velocity list of Sec. 2.1 ------------------------------------
+__host__ __device__ __forceinline__ constexpr int EX(int a) {
+    constexpr int t[27] = {0, 1, 0, 0, 1, 1, 0, -1, 0, 0, 1, 1, -1, -1, 0, 0, 1, -1, -1, 0, -1, 1, 1, 1, -1, -1, -1};
+    return t[a];
+}
+__host__ __device__ __forceinline__ constexpr int EY(int a) {
+    constexpr int t[27] = {0, 0, 1, 0, 1, 0, 1, 0, -1, 0, -1, 0, 1, 0, 1, -1, 1, -1, 0, -1, 1, -1, 1, -1, 1, -1, -1};
+    return t[a];
+}
+__host__ __device__ __forceinline__ constexpr int EZ(int a) {
+    constexpr int t[27] = {0, 0, 0, 1, 0, 1, 1, 0, 0, -1, 0, -1, 0, 1, -1, 1, 1, 0, -1, -1, 1, 1, -1, -1, -1, 1, -1};
+    return t[a];
+}
+// direction with velocity (x, y, z)
+__host__ __device__ __forceinline__ constexpr int DIR(int x, int y, int z) {
+    int r = -1;
+    for (int a = 0; a < 27; ++a)
+        if (EX(a) == x && EY(a) == y && EZ(a) == z) r = a;
+    return r;
+}
+__host__ __device__ __forceinline__ constexpr int OPP(int a) { return DIR(-EX(a), -EY(a), -EZ(a)); }
+// slot of direction a in the 3x3x3 cube used by the transforms: (ez+1)*9 + (ey+1)*3 + (ex+1)
+__host__ __device__ __forceinline__ constexpr int CUBE(int a) { return (EZ(a) + 1) * 9 + (EY(a) + 1) * 3 + (EX(a) + 1); }
+// D3Q27 weights: product of the 1-D weights (2/3 at rest, 1/6 moving)
+__host__ __device__ __forceinline__ constexpr double W1(int e) { return e == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ __forceinline__ constexpr double W27(int a) { return W1(EX(a)) * W1(EY(a)) * W1(EZ(a)); }
+
+// ---- D3Q7 (velocities {0,+x,+y,+z,-x,-y,-z} = D3Q27 indices 0,1,2,3,7,8,9)
+__host__ __device__ __forceinline__ constexpr int D7(int i) {
+    constexpr int t[7] = {0, 1, 2, 3, 7, 8, 9};
+    return t[i];
+}
+__host__ __device__ __forceinline__ constexpr int OPP7(int i) { return i == 0 ? 0 : (i <= 3 ? i + 3 : i - 3); }
+__host__ __device__ __forceinline__ constexpr double W7(int i) { return i == 0 ? 0.0 : 1.0 / 6.0; }
+
+// h lattice helpers: velocity index in the D3Q27 list, opposite, weight
+template <int QH> __host__ __device__ __forceinline__ constexpr int HDIR(int i) { return QH == 27 ? i : D7(i); }
+template <int QH> __host__ __device__ __forceinline__ constexpr int HOPP(int i) { return QH == 27 ? OPP(i) : OPP7(i); }
+template <int QH> __host__ __device__ __forceinline__ constexpr double HW(int i) { return QH == 27 ? W27(i) : W7(i); }
+
+// ---- storage types -------------------------------------------------------
+template <typename S> struct Acc { using R = float; };
+template <> struct Acc<double> { using R = double; };
+
+template <typename R> __device__ __forceinline__ R ld(const float* p) { return (R)__ldg(p); }
+template <typename R> __device__ __forceinline__ R ld(const double* p) { return (R)__ldg(p); }
+template <typename R> __device__ __forceinline__ R ld(const __half* p) { return (R)__half2float(__ldg(p)); }
+template <typename R> __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return (R)__bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ void st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// ---- moment algebra --------------------------------------------------------
+template <typename R> __device__ __forceinline__ constexpr R cs2() { return R(1) / R(3); }
+
+// slot of moment mno in the cube after the forward passes
+__host__ __device__ __forceinline__ constexpr int MIDX(int m, int n, int o) { return o * 9 + n * 3 + m; }
+
+// equilibrium central moments for psi = 1 (Sec. 2.1.1): 1 at 000, cs^2 per
+// index 2, zero when any index is 1
+template <typename R> __device__ __forceinline__ R Eq(int m, int n, int o) {
+    if (m == 1 || n == 1 || o == 1) return R(0);
+    R v = R(1);
+    if (m == 2) v *= cs2<R>();
+    if (n == 2) v *= cs2<R>();
+    if (o == 2) v *= cs2<R>();
+    return v;
+}
+
+template <typename R> __device__ __forceinline__ R Kd(int m, R v) {
+    return m == 0 ? R(1) : (m == 1 ? -v : cs2<R>() + v * v);
+}
+
+// D_mno(v) = E_mno - K_mno(v), expanded so the result keeps its relative
+// precision (it is O(v)).
+template <typename R>
+__device__ __forceinline__ R Dm(int m, int n, int o, R vx, R vy, R vz, R tx, R ty, R tz) {
+    if (m == 1 || n == 1 || o == 1) return -(Kd<R>(m, vx) * Kd<R>(n, vy) * Kd<R>(o, vz));
+    const R c = cs2<R>();
+    const R a = (m == 2) ? tx : R(0);
+    const R b = (n == 2) ? ty : R(0);
+    const R d = (o == 2) ? tz : R(0);
+    const int cnt = (m == 2) + (n == 2) + (o == 2);
+    if (cnt == 0) return R(0);
+    if (cnt == 1) return -(a + b + d);
+    if (cnt == 2) {
+        // two of a, b, d are non-zero: cs^2 (p + q) + p q
+        const R p = (m == 2) ? a : b;
+        const R q = (o == 2) ? d : b;
+        return -(c * (p + q) + p * q);
+    }
+    return -(c * c * (a + b + d) + c * (a * b + a * d + b * d) + a * b * d);
+}
+
+// forward 3-point central transform with shift v: (g-, g0, g+) -> (k0, k1, k2)
+template <typename R> __device__ __forceinline__ void fwd3(R& a, R& b, R& c, R v) {
+    const R m0 = a + b + c;
+    const R m1 = c - a;
+    const R m2 = c + a;
+    const R k1 = m1 - v * m0;
+    const R k2 = m2 - v * (m1 + k1);
+    a = m0;
+    b = k1;
+    c = k2;
+}
+// inverse: (k0, k1, k2) -> (g-, g0, g+)
+template <typename R> __device__ __forceinline__ void inv3(R& a, R& b, R& c, R v) {
+    const R m0 = a;
+    const R m1 = b + v * m0;
+    const R m2 = c + v * (b + m1);
+    a = R(0.5) * (m2 - m1);
+    b = m0 - m2;
+    c = R(0.5) * (m2 + m1);
+}
+
+template <typename R> __device__ __forceinline__ void forward_cube(R* c, R vx, R vy, R vz) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) fwd3<R>(c[3 * j], c[3 * j + 1], c[3 * j + 2], vx);
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) fwd3<R>(c[9 * z + x], c[9 * z + 3 + x], c[9 * z + 6 + x], vy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) fwd3<R>(c[j], c[9 + j], c[18 + j], vz);
+}
+
+template <typename R> __device__ __forceinline__ void inverse_cube(R* c, R vx, R vy, R vz) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3<R>(c[j], c[9 + j], c[18 + j], vz);
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) inv3<R>(c[9 * z + x], c[9 * z + 3 + x], c[9 * z + 6 + x], vy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3<R>(c[3 * j], c[3 * j + 1], c[3 * j + 2], vx);
+}
+
+// ---- parameters -------------------------------------------------------------
+struct DevParams {
+    int nx, ny, nz, N, periodic_x;
+    double omega1, omega_bulk;  // f: shear and bulk rates
+    double sh[7];               // h: rate of central moments of each order 0..6
+    double rho0, Tref;
+    double F[3];
+    double uin[3], Tin;
+};
+
+// ---- f: cumulant collision (Eq. hydro_cu_collision) ----------------------
+// fd: pulled deviations in, post-collision deviations out.  Second-order
+// cumulants relax with omega1 (off-diagonal, deviators) and omega_bulk
+// (trace); cumulants of order >= 3 go to zero (rate 1), so the post-collision
+// central moments about the new mean mu* = mu + F/rho are those of a
+// distribution whose cumulants stop at order two (Isserlis' products).
+// Returns u = mu + F/(2 rho) (velocity that shifts h) and rho.
+template <typename R>
+__device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& uy, R& uz, R& rho_out) {
+    R drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const R v = fd[a];
+        drho += v;
+        if (EX(a) != 0) { jx += EX(a) * v; mxx += v; }
+        if (EY(a) != 0) { jy += EY(a) * v; myy += v; }
+        if (EZ(a) != 0) { jz += EZ(a) * v; mzz += v; }
+        if (EX(a) * EY(a) != 0) mxy += (EX(a) * EY(a)) * v;
+        if (EX(a) * EZ(a) != 0) mxz += (EX(a) * EZ(a)) * v;
+        if (EY(a) * EZ(a) != 0) myz += (EY(a) * EZ(a)) * v;
+    }
+    const R c = cs2<R>();
+    const R rho0 = (R)p.rho0;
+    const R rho = rho0 + drho;
+    const R irho = R(1) / rho;
+    const R mux = jx * irho, muy = jy * irho, muz = jz * irho;
+    // second central moments about mu, minus rho cs^2 on the diagonal
+    R axx = mxx - drho * c - jx * mux;
+    R ayy = myy - drho * c - jy * muy;
+    R azz = mzz - drho * c - jz * muz;
+    R kxy = mxy - jx * muy;
+    R kxz = mxz - jx * muz;
+    R kyz = myz - jy * muz;
+    const R om1 = R(1) - (R)p.omega1;
+    const R omb = R(1) - (R)p.omega_bulk;
+    R dxy = (axx - ayy) * om1;
+    R dxz = (axx - azz) * om1;
+    R tr = (axx + ayy + azz) * omb;
+    kxy *= om1;
+    kxz *= om1;
+    kyz *= om1;
+    const R sxx = (tr + dxy + dxz) * (R(1) / R(3));
+    const R syy = sxx - dxy;
+    const R szz = sxx - dxz;
+    // shifts: mean after collision, velocity for h
+    const R Fx = (R)p.F[0], Fy = (R)p.F[1], Fz = (R)p.F[2];
+    const R vx = mux + Fx * irho, vy = muy + Fy * irho, vz = muz + Fz * irho;
+    ux = mux + R(0.5) * Fx * irho;
+    uy = muy + R(0.5) * Fy * irho;
+    uz = muz + R(0.5) * Fz * irho;
+    rho_out = rho;
+    const R tx = vx * vx, ty = vy * vy, tz = vz * vz;
+
+    // non-equilibrium part of the post-collision central moments
+    // (kappa* - rho E); zero for odd orders
+    const R n220 = c * (sxx + syy) + (sxx * syy + R(2) * kxy * kxy) * irho;
+    const R n202 = c * (sxx + szz) + (sxx * szz + R(2) * kxz * kxz) * irho;
+    const R n022 = c * (syy + szz) + (syy * szz + R(2) * kyz * kyz) * irho;
+    const R n211 = c * kyz + (sxx * kyz + R(2) * kxy * kxz) * irho;
+    const R n121 = c * kxz + (syy * kxz + R(2) * kxy * kyz) * irho;
+    const R n112 = c * kxy + (szz * kxy + R(2) * kxz * kyz) * irho;
+    const R n222 = c * c * (sxx + syy + szz) +
+                   (c * (sxx * syy + sxx * szz + syy * szz) + R(2) * c * (kxy * kxy + kxz * kxz + kyz * kyz)) * irho +
+                   (sxx * syy * szz + R(2) * (sxx * kyz * kyz + syy * kxz * kxz + szz * kxy * kxy) +
+                    R(8) * kxy * kxz * kyz) * irho * irho;
+
+    R cb[27];
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                R neq = R(0);
+                if (m == 1 && n == 1 && o == 0) neq = kxy;
+                if (m == 1 && n == 0 && o == 1) neq = kxz;
+                if (m == 0 && n == 1 && o == 1) neq = kyz;
+                if (m == 2 && n == 0 && o == 0) neq = sxx;
+                if (m == 0 && n == 2 && o == 0) neq = syy;
+                if (m == 0 && n == 0 && o == 2) neq = szz;
+                if (m == 2 && n == 2 && o == 0) neq = n220;
+                if (m == 2 && n == 0 && o == 2) neq = n202;
+                if (m == 0 && n == 2 && o == 2) neq = n022;
+                if (m == 2 && n == 1 && o == 1) neq = n211;
+                if (m == 1 && n == 2 && o == 1) neq = n121;
+                if (m == 1 && n == 1 && o == 2) neq = n112;
+                if (m == 2 && n == 2 && o == 2) neq = n222;
+                cb[MIDX(m, n, o)] = neq + drho * Eq<R>(m, n, o) + rho0 * Dm<R>(m, n, o, vx, vy, vz, tx, ty, tz);
+            }
+    inverse_cube<R>(cb, vx, vy, vz);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) fd[a] = cb[CUBE(a)];
+}
+
+// ---- h: central-moment collision (Eq. H_cm_collision + App. D source) ----
+// Y* = Y + s (H E - Y) + (1 - s/2) Q E per moment, s = p.sh[order]; with
+// Y = dY + Tref K:  dY* = (1-s) dY + s (dH E + Tref D) + (1 - s/2) Q E,
+// dH = H - Tref, H = sum(h) + Q/2.
+template <typename R>
+__device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+    R cb[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) cb[CUBE(a)] = hd[a];
+    forward_cube<R>(cb, ux, uy, uz);
+    const R Tref = (R)p.Tref;
+    const R dH = cb[0] + R(0.5) * Q;
+    const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const R s = (R)p.sh[m + n + o];
+                const R E = Eq<R>(m, n, o);
+                const R D = Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
+                R& y = cb[MIDX(m, n, o)];
+                y = (R(1) - s) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
+            }
+    inverse_cube<R>(cb, ux, uy, uz);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) hd[a] = cb[CUBE(a)];
+}
+
+// D3Q7 (pops 0, +x, +y, +z, -x, -y, -z; moments 000, 100, 010, 001, 200, 020, 002)
+template <typename R>
+__device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+    const R u[3] = {ux, uy, uz};
+    const R m0 = hd[0] + hd[1] + hd[2] + hd[3] + hd[4] + hd[5] + hd[6];
+    const R Tref = (R)p.Tref;
+    const R dH = m0 + R(0.5) * Q;
+    const R c = cs2<R>();
+    const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+    // order 0
+    const R y0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
+    R y1[3], y2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const R m1 = hd[1 + d] - hd[4 + d];
+        const R m2 = hd[1 + d] + hd[4 + d];
+        const R k1 = m1 - u[d] * m0;
+        const R k2 = m2 - u[d] * (m1 + k1);
+        // D_1 = u, D_2 = -u^2; E_1 = 0, E_2 = cs^2
+        y1[d] = (R(1) - s1) * k1 + s1 * (Tref * u[d]);
+        y2[d] = (R(1) - s2) * k2 + s2 * (dH * c - Tref * u[d] * u[d]) + (R(1) - R(0.5) * s2) * Q * c;
+    }
+    R rest = y0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const R M1 = y1[d] + u[d] * y0;
+        const R M2 = y2[d] + u[d] * (y1[d] + M1);
+        hd[1 + d] = R(0.5) * (M2 + M1);
+        hd[4 + d] = R(0.5) * (M2 - M1);
+        rest -= M2;
+    }
+    hd[0] = rest;
+}
+
+template <typename R, int QH>
+__device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+    if constexpr (QH == 27) collide_h27<R>(hd, ux, uy, uz, Q, p);
+    else collide_h7<R>(hd, ux, uy, uz, Q, p);
+}
+
+// ---- equilibria in deviation form ------------------------------------------
+// f^eq(rho, u) - w rho0: central moments about u are (rho - rho0) E + rho0 D(u)
+template <typename R>
+__device__ __forceinline__ void feq_dev(R* fd, R rho, R ux, R uy, R uz, const DevParams& p) {
+    const R rho0 = (R)p.rho0;
+    const R drho = rho - rho0;
+    const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
+    R cb[27];
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+                cb[MIDX(m, n, o)] = drho * Eq<R>(m, n, o) + rho0 * Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
+    inverse_cube<R>(cb, ux, uy, uz);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) fd[a] = cb[CUBE(a)];
+}
+
+// h^eq(psi, u) - w Tref on the h lattice
+template <typename R, int QH>
+__device__ __forceinline__ void heq_dev(R* hd, R psi, R ux, R uy, R uz, const DevParams& p) {
+    const R Tref = (R)p.Tref;
+    const R dpsi = psi - Tref;
+    if constexpr (QH == 27) {
+        const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
+        R cb[27];
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int n = 0; n < 3; ++n)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    cb[MIDX(m, n, o)] = dpsi * Eq<R>(m, n, o) + Tref * Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
+        inverse_cube<R>(cb, ux, uy, uz);
+#pragma unroll
+        for (int a = 0; a < 27; ++a) hd[a] = cb[CUBE(a)];
+    } else {
+        const R u[3] = {ux, uy, uz};
+        R rest = dpsi;
+        const R c = cs2<R>();
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R y1 = Tref * u[d];
+            const R y2 = dpsi * c - Tref * u[d] * u[d];
+            const R M1 = y1 + u[d] * dpsi;
+            const R M2 = y2 + u[d] * (y1 + M1);
+            hd[1 + d] = R(0.5) * (M2 + M1);
+            hd[4 + d] = R(0.5) * (M2 - M1);
+            rest -= M2;
+        }
+        hd[0] = rest;
+    }
+}
+
+}  // namespace lbmd

@@ -1,0 +1,488 @@
+// Kernel templates and their launchers.  The launchers are declared for every
+// translation unit; their bodies (and the kernels) are compiled only where
+// LBM_KERNEL_TU is defined, one translation unit per storage type.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbmd {
+
+// internal node flags: bits 0-1 type, bit 2 = has at least one wall link
+enum : uint8_t { T_FLUID = 0, T_SOLID = 1, T_INLET = 2, T_OUTLET = 3, F_WALL = 4 };
+
+struct Buffers {
+    const void* fA;  // post-collision state, time t
+    void* fB;        // post-collision state, time t+1
+    const void* hA;
+    void* hB;
+    const uint8_t* flags;
+    const float* theta;       // per-node source or nullptr
+    const void* inlet_post;   // R[27 + QH]: inlet post-collision deviations
+    const int32_t* wnode;     // wall nodes (sorted)
+    const int32_t* seg_base;  // wall nodes before each 32-node segment
+    const uint32_t* wmask;    // bit a set: node + e_a is solid
+    const int32_t* woff;      // first link of the wall node
+    const float* lq;          // per link q, sorted by (node, dir)
+    const int32_t* lwall;     // per link wall id
+    const float* Twall;       // per wall temperature
+    int nw;                   // number of wall nodes
+};
+
+constexpr int kBlock = 128;
+constexpr int kRedBlocks = 1216;  // 8 x 152 SMs, partial sums of the reductions
+constexpr int kRedThreads = 256;
+
+template <typename S, int QH> cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s);
+template <typename S, int QH>
+cudaError_t launch_init(const Buffers& b, const DevParams& p, const double* rho, const double* u, const double* T,
+                        cudaStream_t s);
+template <typename S, int QH>
+cudaError_t launch_macros(const Buffers& b, const DevParams& p, double* rho, double* u, double* T, cudaStream_t s);
+template <typename S, int QH>
+cudaError_t launch_populations(const Buffers& b, const DevParams& p, double* f, double* h, cudaStream_t s);
+// partial sums: scratch[3*kRedBlocks] -> out[3] = (sum of rho, sum of H, non-finite count)
+template <typename S, int QH>
+cudaError_t launch_balances(const Buffers& b, const DevParams& p, double* scratch, double* out, cudaStream_t s);
+template <typename S, int QH>
+cudaError_t launch_surface_flux(const Buffers& b, const DevParams& p, int wall, double* scratch, double* out,
+                                cudaStream_t s);
+cudaError_t launch_stream_map(const Buffers& b, const DevParams& p, int qh, int32_t* src, cudaStream_t s);
+
+#ifdef LBM_KERNEL_TU
+
+// ---- pull addressing -------------------------------------------------------
+struct Nbr {
+    int xs[3];  // source x for e_x = -1, 0, +1 (the source is x - e_x)
+    int ys[3];  // ny*nx * ... offsets
+    int zs[3];
+};
+
+__device__ __forceinline__ void node_xyz(int n, const DevParams& p, int& x, int& y, int& z) {
+    x = n % p.nx;
+    const int r = n / p.nx;
+    y = r % p.ny;
+    z = r / p.ny;
+}
+
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const DevParams& p) {
+    Nbr b;
+    int xm = x - 1, xp = x + 1;
+    if (p.periodic_x) {
+        if (xm < 0) xm += p.nx;
+        if (xp >= p.nx) xp -= p.nx;
+    } else {
+        // only the outlet plane reaches past the box: zero normal gradient
+        xm = max(xm, 0);
+        xp = min(xp, p.nx - 1);
+    }
+    const int ym = (y == 0) ? p.ny - 1 : y - 1, yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int zm = (z == 0) ? p.nz - 1 : z - 1, zp = (z == p.nz - 1) ? 0 : z + 1;
+    // index 0 <-> e = -1 (source +1), 2 <-> e = +1 (source -1)
+    b.xs[0] = xp; b.xs[1] = x; b.xs[2] = xm;
+    b.ys[0] = yp * p.nx; b.ys[1] = y * p.nx; b.ys[2] = ym * p.nx;
+    const int pl = p.nx * p.ny;
+    b.zs[0] = zp * pl; b.zs[1] = z * pl; b.zs[2] = zm * pl;
+    return b;
+}
+
+// node from which population a is pulled
+__device__ __forceinline__ int src_of(const Nbr& b, int a) {
+    return b.xs[EX(a) + 1] + b.ys[EY(a) + 1] + b.zs[EZ(a) + 1];
+}
+
+// ---- collision + store shared by the bulk and the wall kernels ----------------
+template <typename S, int QH>
+__device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __restrict__ fB, int n,
+                                                const DevParams& p, typename Acc<S>::R& ux,
+                                                typename Acc<S>::R& uy, typename Acc<S>::R& uz) {
+    using R = typename Acc<S>::R;
+    R rho;
+    collide_f<R>(fd, p, ux, uy, uz, rho);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) st(fB + a * p.N + n, fd[a]);
+}
+
+template <typename S, int QH>
+__device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __restrict__ hB, int n,
+                                                const DevParams& p, typename Acc<S>::R ux,
+                                                typename Acc<S>::R uy, typename Acc<S>::R uz,
+                                                typename Acc<S>::R Q) {
+    using R = typename Acc<S>::R;
+    collide_h<R, QH>(hd, ux, uy, uz, Q, p);
+#pragma unroll
+    for (int i = 0; i < QH; ++i) st(hB + i * p.N + n, hd[i]);
+}
+
+// ---- the step: pull streaming, Eq. IBB / Eq. IABB on wall links, planes,
+// collision of f and h; one thread per node --------------------------------
+// Wall nodes find their entry in the wall table without a search: the nodes
+// of one warp are 32 consecutive node indices, so the entry is the number of
+// wall nodes before the warp (seg_base[n/32]) plus the wall nodes of lower
+// lanes (ballot + popc).
+template <typename S, int QH>
+__global__ void __launch_bounds__(kBlock) k_step(const S* __restrict__ fA, S* __restrict__ fB,
+                                                  const S* __restrict__ hA, S* __restrict__ hB,
+                                                  const uint8_t* __restrict__ flags,
+                                                  const float* __restrict__ theta,
+                                                  const typename Acc<S>::R* __restrict__ inlet,
+                                                  const int32_t* __restrict__ seg_base,
+                                                  const uint32_t* __restrict__ wmask,
+                                                  const int32_t* __restrict__ woff,
+                                                  const float* __restrict__ lq,
+                                                  const int32_t* __restrict__ lwall,
+                                                  const float* __restrict__ Twall, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = n < p.N;
+    const uint8_t fl = in_range ? flags[n] : (uint8_t)T_SOLID;
+    const bool is_wall = (fl & F_WALL) != 0;
+    const uint32_t ballot = __ballot_sync(0xffffffffu, is_wall);
+    if (!in_range) return;
+    const int type = fl & 3;
+    if (type == T_SOLID) return;
+    const int N = p.N;
+    if (type == T_INLET) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) st(fB + a * N + n, inlet[a]);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
+        return;
+    }
+    uint32_t mask = 0;
+    int off = 0;
+    if (is_wall) {
+        const int lane = threadIdx.x & 31;
+        const int idx = __ldg(seg_base + (n >> 5)) + __popc(ballot & ((1u << lane) - 1u));
+        mask = __ldg(wmask + idx);
+        off = __ldg(woff + idx);
+    }
+    int x, y, z;
+    node_xyz(n, p, x, y, z);
+    const Nbr nb = make_nbr(x, y, z, p);
+    R fd[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + a * N + src_of(nb, a));
+    if (mask) {
+        // the arrival b whose source x_b - e_b = x_b + e_a (a = opp b) is solid
+#pragma unroll
+        for (int b = 0; b < 27; ++b) {
+            const int a = OPP(b);
+            if (!(mask & (1u << a))) continue;
+            const float q = __ldg(lq + off + __popc(mask & ((1u << a) - 1u)));
+            const bool thin = (mask >> b) & 1u;  // x_f = x_b - e_a is solid too
+            const R fa_b = ld<R>(fA + a * N + n);
+            if (q <= 0.5f && !thin) {
+                fd[b] = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];  // fd[a] = f*_a(x_f)
+            } else {
+                const R qq = (R)fmaxf(q, 0.5f);
+                const R fb_b = ld<R>(fA + b * N + n);
+                fd[b] = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
+            }
+        }
+    }
+    R ux, uy, uz;
+    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
+    R hd[QH];
+#pragma unroll
+    for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + i * N + src_of(nb, HDIR<QH>(i)));
+    if (mask) {
+        const R Tref = (R)p.Tref;
+#pragma unroll
+        for (int ib = 0; ib < QH; ++ib) {
+            const int b = HDIR<QH>(ib);
+            const int ia = HOPP<QH>(ib);
+            const int a = HDIR<QH>(ia);
+            if (!(mask & (1u << a))) continue;
+            const int l = off + __popc(mask & ((1u << a) - 1u));
+            const float q = __ldg(lq + l);
+            const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref);
+            const bool thin = (mask >> b) & 1u;
+            const R ha_b = ld<R>(hA + ia * N + n);
+            if (q <= 0.5f && !thin) {
+                hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
+            } else {
+                const R qq = (R)fmaxf(q, 0.5f);
+                const R hb_b = ld<R>(hA + ib * N + n);
+                hd[ib] = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+            }
+        }
+    }
+    const R Q = theta ? (R)__ldg(theta + n) : R(0);
+    collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+}
+
+template <typename S, int QH> cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s) {
+    using R = typename Acc<S>::R;
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_step<S, QH><<<grid, kBlock, 0, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta,
+                                          (const R*)b.inlet_post, b.seg_base, b.wmask, b.woff, b.lq, b.lwall,
+                                          b.Twall, p);
+    return cudaGetLastError();
+}
+
+// ---- initialisation: equilibria, App. D shift, one collision -------------
+template <typename S, int QH>
+__global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restrict__ hB,
+                                                  const uint8_t* __restrict__ flags, const float* __restrict__ theta,
+                                                  const typename Acc<S>::R* __restrict__ inlet,
+                                                  const double* __restrict__ rho, const double* __restrict__ u,
+                                                  const double* __restrict__ T, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const int type = flags[n] & 3;
+    if (type == T_SOLID) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) st(fB + (size_t)a * p.N + n, R(0));
+#pragma unroll
+        for (int i = 0; i < QH; ++i) st(hB + (size_t)i * p.N + n, R(0));
+        return;
+    }
+    if (type == T_INLET) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) st(fB + (size_t)a * p.N + n, inlet[a]);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) st(hB + (size_t)i * p.N + n, inlet[27 + i]);
+        return;
+    }
+    const R r = (R)rho[n];
+    const R vx = (R)u[n], vy = (R)u[(size_t)p.N + n], vz = (R)u[2 * (size_t)p.N + n];
+    const R Q = theta ? (R)theta[n] : R(0);
+    R fd[27];
+    feq_dev<R>(fd, r, vx, vy, vz, p);
+    // h = h^eq(rho T, u) - q/2 with q = h^eq(Q, u): one equilibrium at rho T - Q/2
+    R hd[QH];
+    heq_dev<R, QH>(hd, r * (R)T[n] - R(0.5) * Q, vx, vy, vz, p);
+    R ux, uy, uz;
+    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
+    collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+}
+
+template <typename S, int QH>
+cudaError_t launch_init(const Buffers& b, const DevParams& p, const double* rho, const double* u, const double* T,
+                        cudaStream_t s) {
+    using R = typename Acc<S>::R;
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_init<S, QH><<<grid, kBlock, 0, s>>>((S*)b.fB, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, rho, u, T, p);
+    return cudaGetLastError();
+}
+
+// ---- macroscopic fields from the post-collision state --------------------
+// conservation gives rho = sum f*, u = (sum e f* - F/2)/rho,
+// H = sum h* - Q/2 (App. D), T = H / rho
+template <typename S, int QH>
+__global__ void k_macros(const S* __restrict__ fA, const S* __restrict__ hA, const uint8_t* __restrict__ flags,
+                         const float* __restrict__ theta, double* __restrict__ rho, double* __restrict__ u,
+                         double* __restrict__ T, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const int type = flags[n] & 3;
+    const size_t N = (size_t)p.N;
+    if (type == T_SOLID) {
+        rho[n] = 0.0; u[n] = 0.0; u[N + n] = 0.0; u[2 * N + n] = 0.0; T[n] = 0.0;
+        return;
+    }
+    if (type == T_INLET) {
+        rho[n] = 1.0; u[n] = p.uin[0]; u[N + n] = p.uin[1]; u[2 * N + n] = p.uin[2]; T[n] = p.Tin;
+        return;
+    }
+    R dr = 0, jx = 0, jy = 0, jz = 0, dh = 0;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const R v = ld<R>(fA + a * N + n);
+        dr += v;
+        jx += EX(a) * v;
+        jy += EY(a) * v;
+        jz += EZ(a) * v;
+    }
+#pragma unroll
+    for (int i = 0; i < QH; ++i) dh += ld<R>(hA + i * N + n);
+    const R r = (R)p.rho0 + dr;
+    const R Q = theta ? (R)theta[n] : R(0);
+    rho[n] = (double)r;
+    u[n] = (double)((jx - R(0.5) * (R)p.F[0]) / r);
+    u[N + n] = (double)((jy - R(0.5) * (R)p.F[1]) / r);
+    u[2 * N + n] = (double)((jz - R(0.5) * (R)p.F[2]) / r);
+    T[n] = (double)(((R)p.Tref + dh - R(0.5) * Q) / r);
+}
+
+template <typename S, int QH>
+cudaError_t launch_macros(const Buffers& b, const DevParams& p, double* rho, double* u, double* T, cudaStream_t s) {
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_macros<S, QH><<<grid, kBlock, 0, s>>>((const S*)b.fA, (const S*)b.hA, b.flags, b.theta, rho, u, T, p);
+    return cudaGetLastError();
+}
+
+template <typename S, int QH>
+__global__ void k_populations(const S* __restrict__ fA, const S* __restrict__ hA, const uint8_t* __restrict__ flags,
+                              double* __restrict__ f, double* __restrict__ h, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const bool solid = (flags[n] & 3) == T_SOLID;
+    const size_t N = (size_t)p.N;
+    if (f) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a)
+            f[a * N + n] = solid ? 0.0 : (double)ld<R>(fA + a * N + n) + W27(a) * p.rho0;
+    }
+    if (h) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i)
+            h[i * N + n] = solid ? 0.0 : (double)ld<R>(hA + i * N + n) + HW<QH>(i) * p.Tref;
+    }
+}
+
+template <typename S, int QH>
+cudaError_t launch_populations(const Buffers& b, const DevParams& p, double* f, double* h, cudaStream_t s) {
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_populations<S, QH><<<grid, kBlock, 0, s>>>((const S*)b.fA, (const S*)b.hA, b.flags, f, h, p);
+    return cudaGetLastError();
+}
+
+// ---- reductions: warp shuffle -> block -> per-block partials -> one block --
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[wid * NV + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+        const int nwarps = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = (lane < nwarps) ? sh[lane * NV + k] : 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+}
+
+template <int NV>
+__global__ void k_reduce_partials(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    __shared__ double sh[32 * NV];
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += part[i * NV + k];
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+// sums of the deviations (rho - rho0, H - Tref) and of non-finite values over
+// non-solid nodes; the host adds rho0 and Tref times the node count
+template <typename S, int QH>
+__global__ void __launch_bounds__(kRedThreads) k_balances(const S* __restrict__ fA, const S* __restrict__ hA,
+                                                          const uint8_t* __restrict__ flags,
+                                                          const float* __restrict__ theta,
+                                                          double* __restrict__ part, const DevParams p) {
+    using R = typename Acc<S>::R;
+    __shared__ double sh[32 * 3];
+    double v[3] = {0.0, 0.0, 0.0};
+    const size_t N = (size_t)p.N;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
+        if ((flags[n] & 3) == T_SOLID) continue;
+        R dr = 0, dh = 0;
+        bool bad = false;
+#pragma unroll
+        for (int a = 0; a < 27; ++a) {
+            const R x = ld<R>(fA + a * N + n);
+            bad |= !isfinite(x);
+            dr += x;
+        }
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const R x = ld<R>(hA + i * N + n);
+            bad |= !isfinite(x);
+            dh += x;
+        }
+        v[0] += (double)dr;
+        v[1] += (double)dh - (theta ? 0.5 * (double)theta[n] : 0.0);
+        v[2] += bad ? 1.0 : 0.0;
+    }
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = v[k];
+}
+
+template <typename S, int QH>
+cudaError_t launch_balances(const Buffers& b, const DevParams& p, double* scratch, double* out, cudaStream_t s) {
+    k_balances<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.fA, (const S*)b.hA, b.flags, b.theta, scratch, p);
+    k_reduce_partials<3><<<1, 1024, 0, s>>>(scratch, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+// surface heat flux of one wall (Sec. 4.4): for every IABB link of the wall,
+// h_ibar(x_b, t+1) from Eq. IABB minus h*_i(x_b, t); the shifts cancel
+template <typename S, int QH>
+__global__ void __launch_bounds__(kRedThreads) k_surface_flux(const S* __restrict__ hA,
+                                                              const int32_t* __restrict__ wnode,
+                                                              const uint32_t* __restrict__ wmask,
+                                                              const int32_t* __restrict__ woff,
+                                                              const float* __restrict__ lq,
+                                                              const int32_t* __restrict__ lwall,
+                                                              const float* __restrict__ Twall, int nw, int wall,
+                                                              double* __restrict__ part, const DevParams p) {
+    using R = typename Acc<S>::R;
+    __shared__ double sh[32];
+    double v[1] = {0.0};
+    const size_t N = (size_t)p.N;
+    const R Tref = (R)p.Tref;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        const int n = wnode[w];
+        const uint32_t mask = wmask[w];
+        const int off = woff[w];
+        int x, y, z;
+        node_xyz(n, p, x, y, z);
+        const Nbr nb = make_nbr(x, y, z, p);
+#pragma unroll
+        for (int ia = 0; ia < QH; ++ia) {
+            const int a = HDIR<QH>(ia);
+            if (!(mask & (1u << a))) continue;
+            const int l = off + __popc(mask & ((1u << a) - 1u));
+            if (lwall[l] != wall) continue;
+            const int ib = HOPP<QH>(ia);
+            const int b = HDIR<QH>(ib);
+            const float q = lq[l];
+            const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)Twall[wall] - Tref);
+            const bool thin = (mask >> b) & 1u;
+            const R ha_b = ld<R>(hA + ia * N + n);
+            R hin;
+            if (q <= 0.5f && !thin) {
+                const R ha_f = ld<R>(hA + ia * N + src_of(nb, a));
+                hin = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * ha_f) + heq2;
+            } else {
+                const R qq = (R)fmaxf(q, 0.5f);
+                const R hb_b = ld<R>(hA + ib * N + n);
+                hin = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+            }
+            v[0] += (double)hin - (double)ha_b;
+        }
+    }
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+template <typename S, int QH>
+cudaError_t launch_surface_flux(const Buffers& b, const DevParams& p, int wall, double* scratch, double* out,
+                                cudaStream_t s) {
+    k_surface_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.wnode, b.wmask, b.woff, b.lq, b.lwall,
+                                                            b.Twall, b.nw, wall, scratch, p);
+    k_reduce_partials<1><<<1, 1024, 0, s>>>(scratch, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+#endif  // LBM_KERNEL_TU
+
+}  // namespace lbmd

@@ -1,0 +1,56 @@
+// Kernel instantiations for FP32 storage.
+#define LBM_KERNEL_TU
+#include "lbm_kernels.cuh"
+
+namespace lbmd {
+#define LBM_INST(Q)                                                                                              \
+    template cudaError_t launch_step<float, Q>(const Buffers&, const DevParams&, cudaStream_t);                    \
+    template cudaError_t launch_init<float, Q>(const Buffers&, const DevParams&, const double*, const double*,     \
+                                             const double*, cudaStream_t);                                       \
+    template cudaError_t launch_macros<float, Q>(const Buffers&, const DevParams&, double*, double*, double*,      \
+                                               cudaStream_t);                                                    \
+    template cudaError_t launch_populations<float, Q>(const Buffers&, const DevParams&, double*, double*,          \
+                                                    cudaStream_t);                                               \
+    template cudaError_t launch_balances<float, Q>(const Buffers&, const DevParams&, double*, double*,             \
+                                                 cudaStream_t);                                                  \
+    template cudaError_t launch_surface_flux<float, Q>(const Buffers&, const DevParams&, int, double*, double*,    \
+                                                     cudaStream_t);
+LBM_INST(27)
+LBM_INST(7)
+
+// streaming map of the step kernels (storage independent)
+__global__ void k_stream_map(const uint8_t* __restrict__ flags, const int32_t* __restrict__ wnode,
+                             const uint32_t* __restrict__ wmask, int nw, int32_t* __restrict__ src,
+                             const DevParams p) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const size_t N = (size_t)p.N;
+    const int type = flags[n] & 3;
+    if (type == T_SOLID || type == T_INLET) {
+        for (int a = 0; a < 27; ++a) src[a * N + n] = -2;
+        return;
+    }
+    uint32_t mask = 0;
+    if (flags[n] & F_WALL) {
+        int lo = 0, hi = nw - 1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const int v = wnode[mid];
+            if (v == n) { mask = wmask[mid]; break; }
+            if (v < n) lo = mid + 1; else hi = mid - 1;
+        }
+    }
+    int x, y, z;
+    node_xyz(n, p, x, y, z);
+    const Nbr nb = make_nbr(x, y, z, p);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) src[a * N + n] = (mask & (1u << OPP(a))) ? -1 : src_of(nb, a);
+}
+
+cudaError_t launch_stream_map(const Buffers& b, const DevParams& p, int qh, int32_t* src, cudaStream_t s) {
+    (void)qh;
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_stream_map<<<grid, kBlock, 0, s>>>(b.flags, b.wnode, b.wmask, b.nw, src, p);
+    return cudaGetLastError();
+}
+}  // namespace lbmd

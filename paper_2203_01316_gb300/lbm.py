@@ -1,0 +1,258 @@
+"""Python binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers and lbm_status codes to exceptions.  There
+is no fallback: if the library is missing the import of `lib()` fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
+
+LBM_OK, LBM_ERR_INVALID, LBM_ERR_NOMEM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = range(6)
+STATUS = {1: "LBM_ERR_INVALID", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_STATE"}
+HKIND = {"trt": 0, "srt": 1, "1st": 2}
+STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
+
+# every symbol declared in include/lbm.h
+SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_set_inlet", "lbm_set_force",
+           "lbm_set_source", "lbm_init_fields", "lbm_step", "lbm_macros", "lbm_get_populations", "lbm_balances",
+           "lbm_surface_flux", "lbm_nusselt", "lbm_state_size", "lbm_save_state", "lbm_load_state",
+           "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error"]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lat_h", C.c_int), ("hkind", C.c_int),
+                ("storage", C.c_int), ("periodic_x", C.c_int), ("nu", C.c_double), ("k", C.c_double),
+                ("Pr", C.c_double), ("omega_bulk", C.c_double), ("rho0", C.c_double), ("T_ref", C.c_double),
+                ("cuda_stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblbm.so (built by paper_2203_01316_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblbm.so is not built ({LIB_PATH}); run python -m paper_2203_01316_gb300.build")
+    try:  # let the CUDA runtime come from the one PyTorch loaded
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "lbm_create": [C.POINTER(Params), C.POINTER(vp)],
+        "lbm_destroy": [vp],
+        "lbm_set_geometry": [vp, vp, i64, vp, vp, vp, vp, i32, i32],
+        "lbm_set_bc": [vp, i32, dbl],
+        "lbm_set_inlet": [vp, dbl, dbl, dbl, dbl],
+        "lbm_set_force": [vp, dbl, dbl, dbl],
+        "lbm_set_source": [vp, vp, i32],
+        "lbm_init_fields": [vp, vp, vp, vp, i32],
+        "lbm_step": [vp, i32],
+        "lbm_macros": [vp, vp, vp, vp, i32],
+        "lbm_get_populations": [vp, vp, vp, i32],
+        "lbm_balances": [vp, C.POINTER(dbl), C.POINTER(dbl)],
+        "lbm_surface_flux": [vp, i32, C.POINTER(dbl)],
+        "lbm_nusselt": [vp, i32, dbl, dbl, dbl, C.POINTER(dbl)],
+        "lbm_state_size": [vp, C.POINTER(C.c_size_t)],
+        "lbm_save_state": [vp, vp, C.POINTER(C.c_size_t)],
+        "lbm_load_state": [vp, vp, C.c_size_t],
+        "lbm_stream_map": [vp, vp, i32],
+        "lbm_get_links": [vp, C.POINTER(i64), vp, vp, vp, vp],
+        "lbm_sync": [vp],
+        "lbm_last_error": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.lbm_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, is_device, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+               np.uint8: torch.uint8}[dtype]
+        t = x.contiguous()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        return t.data_ptr(), 1 if t.is_cuda else 0, t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+class Solver:
+    """One lattice Boltzmann context (see include/lbm.h for the semantics).
+
+    nx, ny, nz: grid; nu: viscosity; k or Pr: thermal diffusivity or Prandtl
+    number; lat_h: 27 or 7; hkind: 'trt' | 'srt' | '1st'; storage:
+    'f32' | 'f64' | 'f16' | 'bf16'; periodic_x: True, or False for an
+    inlet/outlet channel; stream: a torch.cuda.Stream or raw handle, or None
+    for a library-owned stream."""
+
+    def __init__(self, nx, ny, nz, nu, k=0.0, Pr=0.0, lat_h=27, hkind="trt", storage="f32", periodic_x=True,
+                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None):
+        self.L = lib()
+        p = Params()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.lat_h = int(lat_h)
+        p.hkind = HKIND[hkind] if isinstance(hkind, str) else int(hkind)
+        p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        p.periodic_x = 1 if periodic_x else 0
+        p.nu, p.k, p.Pr = float(nu), float(k), float(Pr)
+        p.omega_bulk, p.rho0, p.T_ref = float(omega_bulk), float(rho0), float(T_ref)
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        p.cuda_stream = stream
+        self.params = p
+        self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
+        self.N = p.nx * p.ny * p.nz
+        self.qh = p.lat_h
+        h = C.c_void_p()
+        st = self.L.lbm_create(C.byref(p), C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, self.L.lbm_last_error(None).decode())
+        self._h = h
+
+    # -- plumbing --
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self.L.lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up --
+    def set_geometry(self, flags, links=None, n_walls=1):
+        fp, fdev, k0 = _ptr(flags, np.uint8)
+        if links is None or len(links["node"]) == 0:
+            self._check(self.L.lbm_set_geometry(self._h, fp, 0, None, None, None, None, int(n_walls), fdev))
+            return
+        n_p, n_dev, k1 = _ptr(links["node"], np.int32)
+        d_p, d_dev, k2 = _ptr(links["dir"], np.int32)
+        q_p, q_dev, k3 = _ptr(links["q"], np.float32)
+        w_p, w_dev, k4 = _ptr(links["wall"], np.int32)
+        if len({fdev, n_dev, d_dev, q_dev, w_dev}) != 1:
+            raise ValueError("flags and links must all be host arrays or all device tensors")
+        self._check(self.L.lbm_set_geometry(self._h, fp, len(links["node"]), n_p, d_p, q_p, w_p, int(n_walls), fdev))
+
+    def set_bc(self, wall, T):
+        self._check(self.L.lbm_set_bc(self._h, int(wall), float(T)))
+
+    def set_inlet(self, u, T):
+        self._check(self.L.lbm_set_inlet(self._h, float(u[0]), float(u[1]), float(u[2]), float(T)))
+
+    def set_force(self, F):
+        self._check(self.L.lbm_set_force(self._h, float(F[0]), float(F[1]), float(F[2])))
+
+    def set_source(self, theta):
+        p, dev, keep = _ptr(theta, np.float32)
+        self._check(self.L.lbm_set_source(self._h, p, dev))
+
+    def init_fields(self, rho, u, T):
+        rp, rd, k0 = _ptr(rho, np.float64)
+        up, ud, k1 = _ptr(u, np.float64)
+        tp, td, k2 = _ptr(T, np.float64)
+        if len({rd, ud, td}) != 1:
+            raise ValueError("rho, u, T must all be host arrays or all device tensors")
+        self._check(self.L.lbm_init_fields(self._h, rp, up, tp, rd))
+
+    # -- time stepping --
+    def step(self, n=1):
+        self._check(self.L.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self.L.lbm_sync(self._h))
+
+    # -- outputs --
+    def macros(self, device=None):
+        """(rho[N], u[3, N], T[N]) as numpy (device None) or torch tensors on `device`."""
+        if device is None:
+            rho = np.empty(self.N); u = np.empty(3 * self.N); T = np.empty(self.N)
+            self._check(self.L.lbm_macros(self._h, rho.ctypes.data, u.ctypes.data, T.ctypes.data, 0))
+            return rho, u.reshape(3, self.N), T
+        import torch
+        rho = torch.empty(self.N, dtype=torch.float64, device=device)
+        u = torch.empty(3 * self.N, dtype=torch.float64, device=device)
+        T = torch.empty(self.N, dtype=torch.float64, device=device)
+        self._check(self.L.lbm_macros(self._h, rho.data_ptr(), u.data_ptr(), T.data_ptr(), 1))
+        return rho, u.view(3, self.N), T
+
+    def populations(self):
+        f = np.empty((27, self.N)); h = np.empty((self.qh, self.N))
+        self._check(self.L.lbm_get_populations(self._h, f.ctypes.data, h.ctypes.data, 0))
+        return f, h
+
+    def balances(self):
+        m = C.c_double(); e = C.c_double()
+        self._check(self.L.lbm_balances(self._h, C.byref(m), C.byref(e)))
+        return m.value, e.value
+
+    def surface_flux(self, wall):
+        q = C.c_double()
+        self._check(self.L.lbm_surface_flux(self._h, int(wall), C.byref(q)))
+        return q.value
+
+    def nusselt(self, wall, length, area, dT):
+        v = C.c_double()
+        self._check(self.L.lbm_nusselt(self._h, int(wall), float(length), float(area), float(dT), C.byref(v)))
+        return v.value
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self.L.lbm_state_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.L.lbm_save_state(self._h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def load_state(self, data: bytes):
+        self._check(self.L.lbm_load_state(self._h, data, len(data)))
+
+    def stream_map(self):
+        src = np.empty((27, self.N), np.int32)
+        self._check(self.L.lbm_stream_map(self._h, src.ctypes.data, 0))
+        return src
+
+    def links(self):
+        n = C.c_int64(0)
+        self._check(self.L.lbm_get_links(self._h, C.byref(n), None, None, None, None))
+        node = np.empty(n.value, np.int32); dr = np.empty(n.value, np.int32)
+        q = np.empty(n.value, np.float32); wall = np.empty(n.value, np.int32)
+        cap = C.c_int64(n.value)
+        self._check(self.L.lbm_get_links(self._h, C.byref(cap), node.ctypes.data, dr.ctypes.data,
+                                         q.ctypes.data, wall.ctypes.data))
+        return {"node": node, "dir": dr, "q": q, "wall": wall}

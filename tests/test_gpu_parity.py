@@ -1,0 +1,209 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Integer outputs (streaming map, wall links) must match bit for bit;
+floating-point outputs within tolerances derived from the arithmetic:
+
+* one FP32 step from identical populations: every population within
+  2e-6 (absolute, populations are O(0.3)): a few FP32 ulps of the O(0.05)
+  deviations the kernel carries, amplified by at most a few terms;
+* one FP64 step: 1e-13;
+* 200 FP32 steps of the periodic 32^3 workload: relative L2 error of u
+  and of T at most 1e-5 (the target stated for the FP32 path).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_01316_gb300 import inputs as I
+
+from _cases import make_pair, rel_l2, small_channel
+
+pytestmark = pytest.mark.gpu
+
+TOL1 = {"f32": 2e-6, "f64": 1e-13}
+
+
+def _oracle_stream_map(o, N):
+    """The oracle's push streaming read back as a pull map: stream unique
+    values and see where each arrival came from."""
+    fs = np.tile(np.arange(N, dtype=np.float64), (27, 1)) + 1.0
+    o.set_post(fs, np.zeros((o.qh, N)))
+    o.stream()
+    f, _ = o.state()
+    return f
+
+
+@pytest.mark.parametrize("case", ["periodic", "channel"])
+def test_stream_map_and_links_bit_exact(case):
+    if case == "periodic":
+        w = I.periodic_tgv(6)
+        w["dims"] = (6, 6, 6)
+    else:
+        w = small_channel()
+    s, o = make_pair(w, nu=0.02, k=1e-3)
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    gmap = s.stream_map()
+    omap = _oracle_stream_map(o, N)
+    flags = np.asarray(w["flags"]).reshape(-1)
+    pulls = (flags == I.FLUID) | (flags == I.OUTLET)
+    for a in range(27):
+        g = gmap[a, pulls]
+        ref = omap[a, pulls]
+        streamed = g >= 0
+        # streamed arrivals: same source node, bit for bit
+        assert np.array_equal(g[streamed] + 1.0, ref[streamed]), a
+        # wall arrivals: the oracle filled them from the wall link (not a plain source)
+    assert np.all(gmap[:, ~pulls] == -2)
+    lk = s.links()
+    ref = w["links"]
+    for key in ("node", "dir", "wall"):
+        assert np.array_equal(lk[key], ref[key])
+    assert np.array_equal(lk["q"].view(np.uint32), ref["q"].view(np.uint32))
+    # the wall-replaced arrivals are exactly the listed links
+    wall_arrivals = set()
+    for a in range(27):
+        for n in np.nonzero(gmap[a] == -1)[0]:
+            wall_arrivals.add((int(n), int(O.lattice(27)[2][a])))
+    assert wall_arrivals == set(zip(ref["node"].tolist(), ref["dir"].tolist()))
+
+
+def _one_step_parity(s, o, tol, qh):
+    """GPU post-collision state -> oracle stream + collide -> compare with the
+    GPU's next post-collision state, every population of every node."""
+    f0, h0 = s.populations()
+    o.set_post(f0, h0)
+    assert o.stream() == 0
+    fo, ho = o.post()
+    s.step(1)
+    f1, h1 = s.populations()
+    assert np.abs(f1 - fo).max() < tol
+    assert np.abs(h1 - ho).max() < tol
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("qh,kind", [(27, "trt"), (27, "srt"), (27, "1st"), (7, "trt"), (7, "srt")])
+def test_one_step_small_channel(storage, qh, kind):
+    w = small_channel()
+    s, o = make_pair(w, nu=0.03, k=2e-3, qh=qh, hkind=kind, storage=storage, wall_T=(0.8,), T_ref=0.1)
+    s.step(7)
+    _one_step_parity(s, o, TOL1[storage], qh)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_one_step_plate_with_force_and_source(storage):
+    w = I.plate_channel(nx=33, ny=13, nz=9, q_bottom=0.3, q_top=0.7, theta_max=1e-3, seed=3)
+    s, o = make_pair(w, nu=0.05, k=5e-3, storage=storage, F=(2e-4, -1e-4, 5e-5), wall_T=(1.0, 0.0),
+                     theta=w["theta"], T_ref=0.5, omega_bulk=0.8)
+    s.step(5)
+    _one_step_parity(s, o, TOL1[storage], 27)
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-6), ("f64", 1e-12)])
+def test_init_state_and_macros(storage, tol):
+    w = I.plate_channel(nx=20, ny=10, nz=6, q_bottom=0.4, q_top=0.9, theta_max=1e-3, seed=5)
+    w["u"] = I.uniform(11, 3 * len(w["rho"]), -0.05, 0.05).reshape(3, -1)
+    w["T"] = I.uniform(12, len(w["rho"]), 0.2, 1.0)
+    s, o = make_pair(w, nu=0.04, k=3e-3, storage=storage, F=(1e-4, 0, 0), wall_T=(1.0, 0.0),
+                     theta=w["theta"], T_ref=0.5)
+    fo, ho = o.post()
+    fg, hg = s.populations()
+    assert np.abs(fg - fo).max() < tol and np.abs(hg - ho).max() < tol
+    rg, ug, Tg = s.macros()
+    ro, uo, To = o.macros()
+    assert np.abs(rg - ro).max() < 10 * tol
+    assert np.abs(ug - uo).max() < 10 * tol
+    assert np.abs(Tg - To).max() < 10 * tol
+
+
+def test_periodic_32_cube_200_steps_fp32():
+    # periodic 32^3, D3Q27 cumulant f + D3Q27 CM h, 200 steps: rel. L2 of u and T <= 1e-5
+    w = I.periodic_tgv(32)
+    s, o = make_pair(w, nu=0.02, k=2e-4, storage="f32", T_ref=1.0)
+    s.step(200)
+    o.step(200)
+    rg, ug, Tg = s.macros()
+    ro, uo, To = o.macros()
+    assert rel_l2(ug, uo) <= 1e-5
+    assert rel_l2(Tg, To) <= 1e-5
+    assert rel_l2(rg, ro) <= 1e-6
+
+
+def test_channel_multi_step_fp64_matches_oracle():
+    w = small_channel(nx=29, ny=13, nz=9, D=5.0)
+    s, o = make_pair(w, nu=0.02, k=1e-3, storage="f64", wall_T=(1.0,))
+    s.step(30)
+    o.step(30)
+    fo, ho = o.post()
+    fg, hg = s.populations()
+    assert np.abs(fg - fo).max() < 1e-12 and np.abs(hg - ho).max() < 1e-12
+
+
+def test_balances_and_surface_flux():
+    w = small_channel()
+    s, o = make_pair(w, nu=0.03, k=2e-3, storage="f64", wall_T=(0.9,))
+    s.step(10)
+    o.step(10)
+    mg, eg = s.balances()
+    mo, eo = o.balances()
+    assert abs(mg - mo) < 1e-9 * abs(mo) and abs(eg - eo) < 1e-9 * abs(eo)
+    qg = s.surface_flux(0)
+    qo = o.surface_flux(0)
+    assert abs(qg - qo) <= 1e-10 * max(1.0, abs(qo))
+    assert abs(qo) > 1e-6
+
+
+def test_full_size_heated_sphere_one_step():
+    # 192 x 64 x 64 heated sphere (D = 16) in the launch configuration the
+    # benchmark times: every population of one step against the oracle
+    w = I.heated_sphere()
+    s, o = make_pair(w, nu=0.016, k=1.6e-5, storage="f32", wall_T=(1.0,))
+    s.step(20)
+    _one_step_parity(s, o, TOL1["f32"], 27)
+
+
+def test_zero_steps_and_determinism():
+    w = small_channel()
+    s1, _ = make_pair(w, nu=0.03, k=2e-3, oracle=False)
+    s2, _ = make_pair(w, nu=0.03, k=2e-3, oracle=False)
+    f0, _ = s1.populations()
+    s1.step(0)
+    assert np.array_equal(s1.populations()[0], f0)
+    s1.step(12)
+    s2.step(12)
+    a, b = s1.populations(), s2.populations()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_save_load_roundtrip():
+    w = small_channel()
+    s, _ = make_pair(w, nu=0.03, k=2e-3, oracle=False)
+    s.step(3)
+    blob = s.save_state()
+    s.step(4)
+    ref = s.populations()
+    s.load_state(blob)
+    s.step(4)
+    got = s.populations()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_geometry_rejections_match_oracle():
+    from paper_2203_01316_gb300 import LBMError
+    w = small_channel()
+    nx, ny, nz = w["dims"]
+    from paper_2203_01316_gb300 import Solver
+    s = Solver(nx, ny, nz, nu=0.03, k=2e-3, periodic_x=False)
+    o = O.Oracle(O.make_params(nx=nx, ny=ny, nz=nz, periodic_x=False))
+    bad_sets = []
+    short = {k: v[1:] for k, v in w["links"].items()}
+    bad_sets.append((w["flags"], short))
+    badq = dict(w["links"]); badq["q"] = w["links"]["q"].copy(); badq["q"][3] = 1.5
+    bad_sets.append((w["flags"], badq))
+    badf = np.array(w["flags"]).copy(); badf[5] = I.SOLID  # x=5 plane inlet row? (node 5 is x=5)
+    bad_sets.append((badf, w["links"]))
+    for fl, lk in bad_sets:
+        with pytest.raises(LBMError):
+            s.set_geometry(fl, lk, n_walls=1)
+        with pytest.raises(O.OracleError):
+            o.set_geometry(fl, lk, nwalls=1)
+    s.set_geometry(w["flags"], w["links"], n_walls=1)
