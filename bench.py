@@ -254,12 +254,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _config():
+def _config(w=None, storage="f32"):
     W = WORKLOAD
-    return {"workload": f"heated sphere channel {W['nx']}x{W['ny']}x{W['nz']}, D={W['D']:g}, "
+    nx, ny, nz = w["dims"] if w is not None else (W["nx"], W["ny"], W["nz"])
+    D = w["D"] if w is not None else W["D"]
+    traffic = nx * ny * nz * 2 * 54 * BYTES_PER_VALUE[storage] / 1e9
+    return {"workload": f"heated sphere channel {nx}x{ny}x{nz}, D={D:g}, "
                         f"D3Q27 cumulant f + D3Q27 CM-TRT h, IBB/IABB, Pr={W['Pr']:g}",
-            "grid": [W["nx"], W["ny"], W["nz"]], "storage": "f32", "lattice": "D3Q27/D3Q27",
-            "parallelism": "replicas", "l2": "inputs larger than L2 (2.7 GB population traffic per step)"}
+            "grid": [nx, ny, nz], "storage": storage, "lattice": "D3Q27/D3Q27",
+            "parallelism": "replicas",
+            "l2": f"inputs larger than L2 ({traffic:.2f} GB population traffic per step)"}
 
 
 def run_ours(args):
@@ -272,12 +276,12 @@ def run_ours(args):
     build.build()
     # a dedicated stream: the library launches on it and the events bracket it
     stream = torch.cuda.Stream()
-    w = make_workload()
+    w = make_workload(args.scale)
     nx, ny, nz = w["dims"]
     N = nx * ny * nz
     flags = np.asarray(w["flags"])
     n_active = int(np.count_nonzero(flags != 1))
-    s = make_solver(w, "f32", stream=stream.cuda_stream)
+    s = make_solver(w, args.storage, stream=stream.cuda_stream)
     s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
     with ClockSampler(local) as clk:
         dt = time_steps(s, args.steps, args.warmup, stream)
@@ -288,14 +292,26 @@ def run_ours(args):
     mass, energy = s.balances()  # also checks that nothing diverged
     value = ws * N * args.steps / dt / 1e6
     ms = dt / args.steps * 1e3
-    bpv = BYTES_PER_VALUE["f32"]
+    bpv = BYTES_PER_VALUE[args.storage]
     alg_bytes = n_active * 2 * (27 + 27) * bpv
     hbm, src = peaks()
     achieved = alg_bytes / (dt / args.steps) / 1e9
+    kname = {"f32": "float", "f64": "double", "f16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "peak_source": src, "kernel": "k_step<float,27>",
-            "traffic": recorded_traffic("k_step_f32_q27_heated_sphere_384"),
+            "peak_source": src, "kernel": f"k_step<{kname},27>",
+            "traffic": recorded_traffic(f"k_step_{args.storage}_q27_{nx}x{ny}x{nz}"),
             "algorithmic_bytes_per_launch": alg_bytes}
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic", "config": _config(w, args.storage),
+            "fluid_mlups": ws * n_active * args.steps / dt / 1e6,
+            "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
+            "balances": {"mass": mass, "energy": energy}}
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        s.close()
+        return
 
     # end to end through the public API with host buffers: fields from pinned
     # host memory -> K steps -> macroscopic fields back to pinned host memory
@@ -330,13 +346,8 @@ def run_ours(args):
                              "frac": bv / (dtv / vsteps) / 1e9 / hbm}
         sv.close()
 
-    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
-            "fluid_mlups": ws * n_active * args.steps / dt / 1e6,
-            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clk.summary(), "storage_variants": variants,
-            "balances": {"mass": mass, "energy": energy}}
+    line["e2e"] = e2e
+    line["storage_variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
@@ -356,6 +367,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="scale the workload grid (profiling of a smaller case)")
+    ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the end-to-end run and the storage variants")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
