@@ -51,6 +51,9 @@ struct lbm_ctx {
 
 static std::string g_create_err;
 
+// message slot of calls made without a context (read with lbm_last_error(NULL))
+void lbm_internal_set_global_error(const std::string& msg) { g_create_err = msg; }
+
 namespace {
 
 template <typename S_, int Q_> struct Tag {

@@ -23,7 +23,7 @@ STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
 SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_set_inlet", "lbm_set_force",
            "lbm_set_source", "lbm_init_fields", "lbm_step", "lbm_macros", "lbm_get_populations", "lbm_balances",
            "lbm_surface_flux", "lbm_nusselt", "lbm_state_size", "lbm_save_state", "lbm_load_state",
-           "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error"]
+           "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc"]
 
 
 class LBMError(RuntimeError):
@@ -77,6 +77,7 @@ def lib():
         "lbm_get_links": [vp, C.POINTER(i64), vp, vp, vp, vp],
         "lbm_sync": [vp],
         "lbm_last_error": [vp],
+        "lbm_balances_noalloc": [vp, vp, i32, i64, vp, dbl, dbl, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
