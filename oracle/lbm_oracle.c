@@ -547,6 +547,8 @@ void orc_get_state(const orc_sim* s, double* f, double* h) {
     memcpy(h, s->h, (size_t)s->p.qh * s->N * sizeof(double));
 }
 
+static double* g_record_u = NULL; /* when set, orc_collide stores u [3][N] there */
+
 /* Collision of every node: pre-collision state -> fs, hs. */
 void orc_collide(orc_sim* s) {
     const int N = s->N, qh = s->p.qh;
@@ -571,6 +573,8 @@ void orc_collide(orc_sim* s) {
         for (int a = 0; a < 27; ++a) f[a] = s->f[(size_t)a * N + n];
         for (int a = 0; a < qh; ++a) h[a] = s->h[(size_t)a * N + n];
         collide_f(&s->p, f, fs, u);
+        if (g_record_u)
+            for (int d = 0; d < 3; ++d) g_record_u[(size_t)d * N + n] = u[d];
         collide_h(&s->p, h, u, theta_at(s, n), hs);
         for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = fs[a];
         for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = hs[a];
@@ -795,4 +799,196 @@ int orc_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ---- adjoint of the h evolution (Sec. 2.1 evolution equation, Eq. H_cm_collision,
+ * Eq. IABB) ----------------------------------------------------------------
+ * With the velocity field fixed (one-way coupling, Sec. 2: h never feeds back
+ * into f), one step maps the post-collision h state s^k to
+ *     g^{k+1} = P s^k + b(T_w)          (streaming, Eq. IABB, planes)
+ *     s^{k+1} = L(u^{k+1}) g^{k+1} + e(u^{k+1}) theta   (collision, App. D source)
+ * Both maps are affine.  L and e are read off the forward collision itself:
+ * column j of L is collide_h(unit vector j, u, Q = 0), and e is
+ * collide_h(0, u, Q = 1).  The objective J is a weighted sum over a window of
+ * levels of a linear flux of s^k (the surface heat flux of one wall, or the
+ * x-flux sum e_x h through one plane).  The reverse sweep applies the
+ * transposes: lambda^k = P^T mu^{k+1} + dJ/ds^k, mu^k = L(u^k)^T lambda^k,
+ * dJ/dtheta += e(u^k)^T lambda^k, dJ/dT_w += (dg^{k+1}/dT_w)^T mu^{k+1}.
+ * The state s^0 is the given initial condition. */
+
+/* partial derivatives of one Eq. IABB arrival with respect to its inputs */
+static void iabb_partials(double q, int thin, double* d_ab, double* d_abb, double* d_af, double* d_T) {
+    if (q <= 0.5 && !thin) {
+        *d_ab = -2.0 * q; *d_af = -(1.0 - 2.0 * q); *d_abb = 0.0; *d_T = 2.0;
+    } else {
+        double qq = q <= 0.5 ? 0.5 : q;
+        *d_ab = -1.0 / (2.0 * qq); *d_abb = (2.0 * qq - 1.0) / (2.0 * qq); *d_af = 0.0; *d_T = 2.0 / (2.0 * qq);
+    }
+}
+
+/* lam += P^T mu (transpose of the h part of orc_stream), dTw += (db/dT_w)^T mu.
+ * mu is zero at solid and inlet nodes. */
+static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, double* dTw) {
+    const int N = s->N, qh = s->p.qh, nx = s->p.nx;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) continue;
+        for (int a = 0; a < qh; ++a) {
+            int t = neighbour(s, n, Lh->e[a][0], Lh->e[a][1], Lh->e[a][2]);
+            if (t < 0 || s->flags[t] == FL_SOLID || s->flags[t] == FL_INLET) continue;
+            lam[(size_t)a * N + n] += mu[(size_t)a * N + t];
+        }
+    }
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int i = 0; i < qh; ++i) {
+            int a = Lh->dir27[i];
+            if (a == 0) continue;
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f) continue;
+            int ib = Lh->opp[i];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double d_ab, d_abb, d_af, d_T;
+            iabb_partials(q, thin, &d_ab, &d_abb, &d_af, &d_T);
+            double m = mu[(size_t)ib * N + n];
+            lam[(size_t)i * N + n] += d_ab * m;
+            lam[(size_t)ib * N + n] += d_abb * m;
+            if (!thin) lam[(size_t)i * N + xf] += d_af * m;
+            if (dTw) dTw[s->wtab[(size_t)n * 27 + a]] += d_T * Lh->w[i] * m;
+        }
+    }
+    if (!s->p.periodic_x) {
+        for (int n = 0; n < N; ++n) {
+            if (s->flags[n] != FL_OUTLET || n % nx != nx - 1) continue;
+            for (int a = 0; a < qh; ++a) {
+                if (Lh->e[a][0] >= 0) continue;
+                int src = neighbour(s, n, 0, -Lh->e[a][1], -Lh->e[a][2]);
+                lam[(size_t)a * N + src] += mu[(size_t)a * N + n];
+            }
+        }
+    }
+}
+
+/* lam += weight * dF/ds and dTw += weight * dF/dT_w for the objective flux F */
+static void objective_gradient(const orc_sim* s, int kind, int wall, int plane, double weight, double* lam,
+                               double* dTw) {
+    const int N = s->N, qh = s->p.qh, nx = s->p.nx;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    if (kind == 1) { /* section flux sum e_x h over the plane x = plane */
+        for (int n = 0; n < N; ++n) {
+            if (n % nx != plane || s->flags[n] == FL_SOLID) continue;
+            for (int i = 0; i < qh; ++i) lam[(size_t)i * N + n] += weight * Lh->e[i][0];
+        }
+        return;
+    }
+    for (int n = 0; n < N; ++n) { /* surface flux of wall (reading R8) */
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int i = 0; i < qh; ++i) {
+            int a = Lh->dir27[i];
+            if (a == 0) continue;
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f || s->wtab[(size_t)n * 27 + a] != wall) continue;
+            int ib = Lh->opp[i];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double d_ab, d_abb, d_af, d_T;
+            iabb_partials(q, thin, &d_ab, &d_abb, &d_af, &d_T);
+            lam[(size_t)i * N + n] += weight * (d_ab - 1.0);
+            lam[(size_t)ib * N + n] += weight * d_abb;
+            if (!thin) lam[(size_t)i * N + xf] += weight * d_af;
+            if (dTw) dTw[wall] += weight * d_T * Lh->w[i];
+        }
+    }
+}
+
+/* the objective flux F(s) of the post-collision state in s->hs */
+static double objective_value(orc_sim* s, int kind, int wall, int plane) {
+    const int N = s->N, qh = s->p.qh, nx = s->p.nx;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    double F = 0.0;
+    if (kind == 1) {
+        for (int n = 0; n < N; ++n) {
+            if (n % nx != plane || s->flags[n] == FL_SOLID) continue;
+            for (int i = 0; i < qh; ++i) F += Lh->e[i][0] * s->hs[(size_t)i * N + n];
+        }
+        return F;
+    }
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int i = 0; i < qh; ++i) {
+            int a = Lh->dir27[i];
+            if (a == 0) continue;
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f || s->wtab[(size_t)n * 27 + a] != wall) continue;
+            int ib = Lh->opp[i];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
+            double hin = iabb(q, s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n], ha_f, thin,
+                              Lh->w[i] * s->Twall[wall]);
+            F += hin - s->hs[(size_t)i * N + n];
+        }
+    }
+    return F;
+}
+
+/* Forward run from the post-collision state (f_post, h_post) = s^0 over
+ * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
+ * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
+ * dJ/dT_w[nwalls] to them.  Returns 0, or -1 on a streaming error. */
+int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
+                int wall, int plane, double weight, double* J, double* dtheta, double* dTw) {
+    const int N = s->N, qh = s->p.qh;
+    const size_t HN = (size_t)qh * N;
+    double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
+    orc_set_post(s, f_post, h_post);
+    double Jv = 0.0;
+    for (int k = 0; k <= nsteps; ++k) {
+        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane);
+        if (k == nsteps) break;
+        if (orc_stream(s) != 0) { free(urec); return -1; }
+        g_record_u = urec ? urec + (size_t)(k + 1) * 3 * N : NULL;
+        orc_collide(s);
+        g_record_u = NULL;
+    }
+    *J = Jv;
+    if (!dtheta) return 0;
+    double* mu = (double*)calloc(HN, sizeof(double));
+    double* lam = (double*)calloc(HN, sizeof(double));
+    for (int k = nsteps; k >= 0; --k) {
+        for (size_t i = 0; i < HN; ++i) lam[i] = 0.0;
+        if (k < nsteps) stream_transpose_h(s, mu, lam, dTw);
+        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, weight, lam, dTw);
+        for (size_t i = 0; i < HN; ++i) mu[i] = 0.0;
+        if (k == 0) break;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int n = 0; n < N; ++n) {
+            if (s->flags[n] == FL_SOLID || s->flags[n] == FL_INLET) continue;
+            double u[3], Lm[27 * 27], col[27], unit[27], e[27], zero[27];
+            for (int d = 0; d < 3; ++d) u[d] = urec[(size_t)k * 3 * N + (size_t)d * N + n];
+            for (int j = 0; j < qh; ++j) {
+                for (int i = 0; i < qh; ++i) unit[i] = (i == j) ? 1.0 : 0.0;
+                collide_h(&s->p, unit, u, 0.0, col);
+                for (int i = 0; i < qh; ++i) Lm[i * qh + j] = col[i];
+            }
+            for (int i = 0; i < qh; ++i) zero[i] = 0.0;
+            collide_h(&s->p, zero, u, 1.0, e);
+            double dth = 0.0;
+            for (int i = 0; i < qh; ++i) dth += e[i] * lam[(size_t)i * N + n];
+            dtheta[n] += dth;
+            for (int j = 0; j < qh; ++j) {
+                double v = 0.0;
+                for (int i = 0; i < qh; ++i) v += Lm[i * qh + j] * lam[(size_t)i * N + n];
+                mu[(size_t)j * N + n] = v;
+            }
+        }
+    }
+    free(mu);
+    free(lam);
+    free(urec);
+    return 0;
 }

@@ -101,6 +101,10 @@ def lib():
         L.orc_collide_f.argtypes = [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_collide_h.argtypes = [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
         L.orc_num_threads.restype = C.c_int
+        L.orc_adjoint.restype = C.c_int
+        L.orc_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
+                                  C.c_void_p]
     return _lib
 
 
@@ -264,3 +268,23 @@ class Oracle:
 
     def surface_flux(self, wall):
         return float(lib().orc_surface_flux(self._h, int(wall)))
+
+    def adjoint(self, f_post, h_post, nsteps, window, objective, nwalls=1, gradients=True):
+        """J = weight * sum over levels k in window of the flux F(s^k), from the
+        post-collision state (f_post, h_post) = s^0 over nsteps steps.
+        objective: ("surface", wall, weight) or ("section", plane_x, weight).
+        Returns (J, dJ/dtheta[N], dJ/dT_w[nwalls]) (gradients None if not asked)."""
+        kind = 0 if objective[0] == "surface" else 1
+        wall = int(objective[1]) if kind == 0 else 0
+        plane = int(objective[1]) if kind == 1 else 0
+        f_post = np.ascontiguousarray(f_post, dtype=np.float64)
+        h_post = np.ascontiguousarray(h_post, dtype=np.float64)
+        J = C.c_double()
+        dth = np.zeros(self.N) if gradients else None
+        dTw = np.zeros(nwalls) if gradients else None
+        rc = lib().orc_adjoint(self._h, f_post.ctypes.data, h_post.ctypes.data, int(nsteps), int(window[0]),
+                               int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
+                               dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
+        if rc != 0:
+            raise OracleError("orc_adjoint: streaming error")
+        return J.value, dth, dTw

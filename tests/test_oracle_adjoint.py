@@ -1,0 +1,114 @@
+"""Pins of the oracle's adjoint of the h evolution against finite differences.
+
+For the CM kinds the h step is affine in h, theta and the wall temperatures
+(Eq. H_cm_collision, Eq. IABB, App. D), and the objectives are linear
+fluxes, so J(theta, T_w) is affine: central differences in FP64 are exact up
+to rounding, and any mistake in a transpose shows up as an O(1) relative
+error."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_01316_gb300 import inputs as I
+
+
+def _plate_case(qh=27, kind="trt", qb=0.3, qt=0.7, seed=5):
+    w = I.plate_channel(nx=6, ny=9, nz=4, q_bottom=qb, q_top=qt, theta_max=1e-3, seed=seed)
+    N = len(w["rho"])
+    w["u"] = I.uniform(seed + 1, 3 * N, -0.03, 0.03).reshape(3, N)
+    w["T"] = I.uniform(seed + 2, N, 0.2, 1.0)
+    p = O.make_params(nx=6, ny=9, nz=4, qh=qh, hkind=kind, nu=0.05, k=0.01, F=(2e-4, 0.0, 1e-4))
+    return w, p
+
+
+def _channel_case(qh=27, kind="trt", seed=6):
+    w = I.heated_sphere(14, 9, 8, D=4.0, cx=6.0, seed=seed, u_in=0.04, T_in=0.2)
+    nx, ny, nz = w["dims"]
+    p = O.make_params(nx=nx, ny=ny, nz=nz, qh=qh, hkind=kind, periodic_x=False, nu=0.05, k=0.01,
+                      u_in=w["u_in"], T_in=w["T_in"])
+    N = nx * ny * nz
+    w["theta"] = I.uniform(seed + 3, N, 0.0, 1e-3)
+    return w, p
+
+
+def _setup(w, p, Tw):
+    o = O.Oracle(p)
+    o.set_geometry(w["flags"], w["links"], nwalls=w["nwalls"])
+    for i, T in enumerate(Tw):
+        o.set_wall_temperature(i, T)
+    o.set_theta(w["theta"])
+    o.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    fpost, hpost = o.post()
+    return o, fpost, hpost
+
+
+def _J(w, p, Tw, theta, fpost, hpost, nsteps, window, obj):
+    o = O.Oracle(p)
+    o.set_geometry(w["flags"], w["links"], nwalls=w["nwalls"])
+    for i, T in enumerate(Tw):
+        o.set_wall_temperature(i, T)
+    o.set_theta(theta)
+    J, _, _ = o.adjoint(fpost, hpost, nsteps, window, obj, nwalls=w["nwalls"], gradients=False)
+    return J
+
+
+@pytest.mark.parametrize("qh,kind", [(27, "trt"), (27, "srt"), (27, "1st"), (7, "trt")])
+@pytest.mark.parametrize("obj", [("surface", 1, 0.7), ("section", 3, 1.3)])
+def test_plate_adjoint_matches_finite_differences(qh, kind, obj):
+    w, p = _plate_case(qh, kind)
+    Tw = [1.0, 0.1]
+    o, fpost, hpost = _setup(w, p, Tw)
+    nsteps, window = 10, (4, 10)
+    J, dth, dTw = o.adjoint(fpost, hpost, nsteps, window, obj, nwalls=2)
+    theta = w["theta"].copy()
+    rng = np.random.default_rng(7)
+    fluid = np.nonzero(w["flags"] == I.FLUID)[0]
+    for n in rng.choice(fluid, 6, replace=False):
+        eps = 1e-3
+        tp = theta.copy(); tp[n] += eps
+        tm = theta.copy(); tm[n] -= eps
+        fd = (_J(w, p, Tw, tp, fpost, hpost, nsteps, window, obj) -
+              _J(w, p, Tw, tm, fpost, hpost, nsteps, window, obj)) / (2 * eps)
+        assert abs(dth[n] - fd) <= 1e-8 * max(abs(fd), 1e-3), (n, dth[n], fd)
+    for wall in range(2):
+        eps = 1e-3
+        Tp = list(Tw); Tp[wall] += eps
+        Tm = list(Tw); Tm[wall] -= eps
+        fd = (_J(w, p, Tp, theta, fpost, hpost, nsteps, window, obj) -
+              _J(w, p, Tm, theta, fpost, hpost, nsteps, window, obj)) / (2 * eps)
+        assert abs(dTw[wall] - fd) <= 1e-8 * max(abs(fd), 1e-3), (wall, dTw[wall], fd)
+    # solid nodes carry no sensitivity
+    assert np.all(dth[w["flags"] == I.SOLID] == 0.0)
+
+
+@pytest.mark.parametrize("qh", [27, 7])
+def test_channel_adjoint_directional_derivative(qh):
+    # inlet/outlet planes and a sphere with thin gaps: the gradient's
+    # projection on a random direction equals the exact directional change
+    w, p = _channel_case(qh)
+    Tw = [1.0]
+    o, fpost, hpost = _setup(w, p, Tw)
+    nx = w["dims"][0]
+    for obj in (("surface", 0, 1.0), ("section", nx - 2, 1.0)):
+        nsteps, window = 9, (3, 9)
+        J, dth, dTw = o.adjoint(fpost, hpost, nsteps, window, obj, nwalls=1)
+        v = np.random.default_rng(9).uniform(-1, 1, len(dth))
+        eps = 1e-4
+        theta = w["theta"]
+        fd = (_J(w, p, Tw, theta + eps * v, fpost, hpost, nsteps, window, obj) -
+              _J(w, p, Tw, theta - eps * v, fpost, hpost, nsteps, window, obj)) / (2 * eps)
+        assert abs(dth @ v - fd) <= 1e-8 * max(abs(fd), 1e-6)
+        assert np.all(dth[w["flags"] == I.INLET] == 0.0)
+
+
+def test_objective_value_matches_surface_flux():
+    # J over a one-level window at level 0 is the surface flux of Sec. 4.4
+    w, p = _plate_case()
+    o, fpost, hpost = _setup(w, p, [1.0, 0.1])
+    J, _, _ = o.adjoint(fpost, hpost, 0, (0, 0), ("surface", 0, 1.0), nwalls=2, gradients=False)
+    o2 = O.Oracle(p)
+    o2.set_geometry(w["flags"], w["links"], nwalls=2)
+    o2.set_wall_temperature(0, 1.0); o2.set_wall_temperature(1, 0.1)
+    o2.set_theta(w["theta"])
+    o2.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    assert abs(J - o2.surface_flux(0)) < 1e-14
