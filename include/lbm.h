@@ -147,17 +147,66 @@ lbm_status lbm_surface_flux(lbm_ctx* ctx, int wall_id, double* flux);
 lbm_status lbm_nusselt(lbm_ctx* ctx, int wall_id, double length, double area, double dT,
                        double* nu_out);
 
+/* Section heat flux (Sec. 4.4, Eq. heat_flux_section): sum of e_x h over the
+ * non-solid nodes of the plane x = plane_x, from the current post-collision
+ * state, FP64.  Synchronises. */
+lbm_status lbm_section_flux(lbm_ctx* ctx, int plane_x, double* flux);
+
 /* Bytes needed by lbm_save_state. */
 lbm_status lbm_state_size(lbm_ctx* ctx, size_t* bytes);
 
 /* Copy the stored populations (with a header naming the grid, lattice and
- * storage) to host memory of *bytes bytes; *bytes is set to the size used.
- * Synchronises. */
-lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t* bytes);
+ * storage) to a buffer of *bytes bytes, host memory or (is_device = 1) device
+ * memory; *bytes is set to the size used.  Synchronises. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes, int is_device);
 
 /* Restore a state written by lbm_save_state of a context with the same grid,
- * lattice and storage (LBM_ERR_INVALID otherwise). */
-lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
+ * lattice and storage (LBM_ERR_INVALID otherwise); buf in host or
+ * (is_device = 1) device memory. */
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes, int is_device);
+
+/* ---- adjoint of the h evolution -------------------------------------------
+ * One-way coupling (Sec. 2: h does not act on f) makes the h step affine in
+ * the h state, the per-node source Q (App. D) and the wall temperatures
+ * (Eq. IABB), with the velocity field fixed:
+ *     g^{k+1} = P s^k + b(T_w),   s^{k+1} = L(u^{k+1}) g^{k+1} + e(u^{k+1}) Q
+ * (s^k: post-collision h of level k, g: arrivals after streaming and walls,
+ * L, e from Eq. H_cm_collision).  An objective is a linear flux F of s^k
+ * summed with a weight over a window of levels; the adjoint runs the
+ * transposed steps backwards.  Velocity records, adjoint arrays: element type
+ * float, or double for LBM_F64 contexts; SoA [3][N] and [Q_h][N]. */
+typedef enum { LBM_OBJ_SURFACE_FLUX = 0, LBM_OBJ_SECTION_FLUX = 1 } lbm_objective_kind;
+typedef struct {
+    int kind;       /* lbm_objective_kind */
+    int wall_id;    /* SURFACE_FLUX: the wall (lbm_surface_flux's flux) */
+    int plane_x;    /* SECTION_FLUX: the plane (lbm_section_flux's flux) */
+    double weight;  /* J += weight * F(level) */
+} lbm_objective;
+
+/* *J_device (device double) += weight * F(current level); asynchronous. */
+lbm_status lbm_objective_accumulate(lbm_ctx* ctx, const lbm_objective* obj, double* J_device);
+
+/* Advance n steps like lbm_step and record, for each step k = 1..n, the
+ * velocity u used by every node's collision at u_rec + (k-1)*3*N (device).
+ * advance_h = 0 advances f only and leaves h untouched (the velocity
+ * recomputation of the adjoint needs no h). */
+lbm_status lbm_step_record(lbm_ctx* ctx, int n, void* u_rec, int advance_h);
+
+/* One level of the adjoint sweep.  mu_next: adjoint of the arrivals of level
+ * k+1 (zeros at the last level).  Computes lambda^k = P^T mu_next + dJ/ds^k
+ * (obj: the objective term of level k, NULL when level k is outside the
+ * window); then, if u_level (the velocity of level k's collision, from
+ * lbm_step_record) is given, writes mu^k = L(u^k)^T lambda^k to out and adds
+ * e(u^k)^T lambda^k to dJ_dtheta[N] (device double, may be NULL); with
+ * u_level NULL (the initial level) it writes lambda^0 to out.  The dJ/dT_w
+ * terms are accumulated inside the context (lbm_adjoint_wall_gradient).
+ * mu_next and out must not alias.  Asynchronous. */
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_next, void* out,
+                            const lbm_objective* obj, double* dJ_dtheta);
+
+/* dJ/dT_w accumulated by lbm_adjoint_step since the last reset, per wall
+ * (host double[n_walls]); reset = 1 clears the accumulators.  Synchronises. */
+lbm_status lbm_adjoint_wall_gradient(lbm_ctx* ctx, double* dJ_dTwall, int reset);
 
 /* Streaming map used by the step: src[a*N + n] = node whose post-collision
  * population a arrives at node n, -1 where a wall link replaces it, -2 for

@@ -1,0 +1,91 @@
+"""Gradients of a heat-transfer objective with respect to the per-node heat
+source theta and the wall temperatures, through the hand-written adjoint of
+the library (include/lbm.h, "adjoint of the h evolution").
+
+J(theta, T_w) = sum over levels k in [window[0], window[1]] of
+weight * F(s^k), F a linear flux of the post-collision h state (the surface
+heat flux of a wall, Sec. 4.4, or the x-flux through a plane), over nsteps
+steps from a saved state s^0.
+
+Forward: runs the steps, keeping a device checkpoint of the state every
+`every` steps.  Backward: for each segment, last first, restores its
+checkpoint, recomputes the velocity of every level of the segment (f only;
+h is affine and its adjoint needs only u), then runs the adjoint kernel
+level by level.  All arithmetic runs in the CUDA library; this module only
+orders the calls and owns the device buffers (torch tensors).
+"""
+from __future__ import annotations
+
+import torch
+
+from .lbm import Solver
+
+
+class ThermalObjective(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, T_wall, solver: Solver, state0, nsteps: int, window, objective, every: int):
+        if every < 1:
+            raise ValueError("checkpoint interval must be >= 1")
+        dev = state0.device
+        # the solver runs on its own stream: order it after torch's work on
+        # the inputs, and torch's later work after the solver's
+        torch.cuda.synchronize(dev)
+        solver.set_source(theta.detach().to(device=dev, dtype=torch.float32))
+        torch.cuda.synchronize(dev)
+        for w, T in enumerate(T_wall.detach().cpu().tolist()):
+            solver.set_bc(w, T)
+        solver.load_state(state0)
+        J = torch.zeros(1, dtype=torch.float64, device=dev)
+        ckpts = {}
+        for k in range(nsteps + 1):
+            if k % every == 0 and k < nsteps:
+                ckpts[k] = solver.save_state(torch.empty_like(state0))
+            if window[0] <= k <= window[1]:
+                solver.objective_accumulate(objective, J)
+            if k < nsteps:
+                solver.step(1)
+        solver.sync()
+        ctx.solver, ctx.ckpts, ctx.nsteps, ctx.window = solver, ckpts, nsteps, window
+        ctx.objective, ctx.every, ctx.n_walls = objective, every, T_wall.numel()
+        ctx.theta_dtype, ctx.Tw_dtype = theta.dtype, T_wall.dtype
+        ctx.theta_device, ctx.Tw_device = theta.device, T_wall.device
+        return J[0]
+
+    @staticmethod
+    def backward(ctx, gJ):
+        s: Solver = ctx.solver
+        N, qh = s.N, s.qh
+        dev = next(iter(ctx.ckpts.values())).device if ctx.ckpts else torch.device("cuda")
+        rdt = torch.float64 if s.params.storage == 1 else torch.float32
+        mu_next = torch.zeros(qh * N, dtype=rdt, device=dev)
+        mu_out = torch.empty_like(mu_next)
+        dtheta = torch.zeros(N, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)  # zeroed buffers before the solver's stream uses them
+        s.adjoint_wall_gradient(ctx.n_walls, reset=True)
+        lo, hi = ctx.window
+        starts = sorted(ctx.ckpts)
+        for seg_start in reversed(starts):
+            seg_end = min(seg_start + ctx.every, ctx.nsteps)
+            L = seg_end - seg_start
+            s.load_state(ctx.ckpts[seg_start])
+            urec = torch.empty(L * 3 * N, dtype=rdt, device=dev)
+            s.step_record(L, urec, advance_h=False)
+            for k in range(seg_end, seg_start, -1):
+                obj = ctx.objective if lo <= k <= hi else None
+                u_k = urec[(k - seg_start - 1) * 3 * N:(k - seg_start) * 3 * N]
+                s.adjoint_step(u_k, mu_next, mu_out, obj, dtheta)
+                mu_next, mu_out = mu_out, mu_next
+        # level 0: the initial state is given; only its objective and wall terms remain
+        obj0 = ctx.objective if lo <= 0 <= hi else None
+        s.adjoint_step(None, mu_next, mu_out, obj0, None)
+        dTw = s.adjoint_wall_gradient(ctx.n_walls, reset=True)  # synchronises the solver's stream
+        gJ = gJ.to(torch.float64)
+        g_theta = (gJ.to(dtheta.device) * dtheta).to(device=ctx.theta_device, dtype=ctx.theta_dtype)
+        g_Tw = (gJ.cpu() * torch.from_numpy(dTw)).to(device=ctx.Tw_device, dtype=ctx.Tw_dtype)
+        return g_theta, g_Tw, None, None, None, None, None, None
+
+
+def thermal_objective(theta, T_wall, solver, state0, nsteps, window, objective, every=50):
+    """J(theta, T_wall) with gradients by the adjoint (see module docstring).
+    state0: CUDA uint8 tensor from solver.save_state(out=...)."""
+    return ThermalObjective.apply(theta, T_wall, solver, state0, nsteps, window, objective, every)

@@ -24,7 +24,7 @@ struct lbm_ctx {
     int device = 0;
     void* f[2] = {nullptr, nullptr};
     void* h[2] = {nullptr, nullptr};
-    int cur = 0;  // f[cur], h[cur] hold the post-collision state of the current time level
+    int cur_f = 0, cur_h = 0;  // f[cur_f], h[cur_h]: post-collision state of the current level
     uint8_t* d_flags = nullptr;
     int nw = 0;
     int32_t* d_wnode = nullptr;
@@ -34,6 +34,11 @@ struct lbm_ctx {
     int64_t nl = 0;
     float* d_lq = nullptr;
     int32_t* d_lwall = nullptr;
+    int32_t* d_rsegbase = nullptr;  // adjoint: reverse (x_f) link table
+    uint32_t* d_rmask = nullptr;
+    int32_t* d_roff = nullptr;
+    int32_t* d_rlink = nullptr;
+    double* d_dlink = nullptr;      // adjoint: per link dJ/dT_w accumulators
     int n_walls = 1;
     float* d_Twall = nullptr;
     std::vector<float> Twall{0.0f};
@@ -100,10 +105,10 @@ struct DeviceGuard {
 
 Buffers buffers(const lbm_ctx* c) {
     Buffers b{};
-    b.fA = c->f[c->cur];
-    b.fB = c->f[1 - c->cur];
-    b.hA = c->h[c->cur];
-    b.hB = c->h[1 - c->cur];
+    b.fA = c->f[c->cur_f];
+    b.fB = c->f[1 - c->cur_f];
+    b.hA = c->h[c->cur_h];
+    b.hB = c->h[1 - c->cur_h];
     b.flags = c->d_flags;
     b.theta = c->d_theta;
     b.inlet_post = c->d_inlet;
@@ -115,6 +120,12 @@ Buffers buffers(const lbm_ctx* c) {
     b.lwall = c->d_lwall;
     b.Twall = c->d_Twall;
     b.nw = c->nw;
+    b.rseg_base = c->d_rsegbase;
+    b.rmask = c->d_rmask;
+    b.roff = c->d_roff;
+    b.rlink = c->d_rlink;
+    b.dlink = c->d_dlink;
+    b.urec = nullptr;
     return b;
 }
 
@@ -165,6 +176,16 @@ void free_geometry(lbm_ctx* c) {
     cudaFree(c->d_woff);
     cudaFree(c->d_lq);
     cudaFree(c->d_lwall);
+    cudaFree(c->d_rsegbase);
+    cudaFree(c->d_rmask);
+    cudaFree(c->d_roff);
+    cudaFree(c->d_rlink);
+    cudaFree(c->d_dlink);
+    c->d_rsegbase = nullptr;
+    c->d_rmask = nullptr;
+    c->d_roff = nullptr;
+    c->d_rlink = nullptr;
+    c->d_dlink = nullptr;
     c->d_wnode = nullptr;
     c->d_segbase = nullptr;
     c->d_wmask = nullptr;
@@ -395,6 +416,30 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
             return fail(c, LBM_ERR_INVALID, "fluid->solid links of node " + std::to_string(n) + " are not all listed");
         iflags[n] |= lbmd::F_WALL;
     }
+    // adjoint reverse table: node y = x - e_a of each link (x, a) with
+    // q <= 1/2 whose y is fluid or outlet (Eq. IABB reads h*_a(y) there)
+    std::vector<std::pair<int64_t, int32_t>> rev;  // (y*32 + a, link index)
+    for (int64_t i = 0; i < n_links; ++i) {
+        if (!(sq[i] <= 0.5f)) continue;
+        const int a = sd[i];
+        const int yv = nbr(sn[i], -lbmd::EX(a), -lbmd::EY(a), -lbmd::EZ(a));
+        if (yv < 0 || fl[yv] == lbmd::T_SOLID || fl[yv] == lbmd::T_INLET) continue;
+        rev.push_back({(int64_t)yv * 32 + a, (int32_t)i});
+    }
+    std::sort(rev.begin(), rev.end());
+    std::vector<int32_t> rnode, roff, rlink;
+    std::vector<uint32_t> rmask;
+    for (size_t i = 0; i < rev.size(); ++i) {
+        const int yv = (int)(rev[i].first / 32), a = (int)(rev[i].first % 32);
+        if (i == 0 || rnode.back() != yv) {
+            rnode.push_back(yv);
+            roff.push_back((int32_t)i);
+            rmask.push_back(0u);
+        }
+        rmask.back() |= 1u << a;
+        rlink.push_back(rev[i].second);
+        iflags[yv] |= lbmd::F_RWALL;
+    }
     // wall nodes before each 32-node segment (warp) of the step kernel
     const int nseg = (N + 31) / 32;
     std::vector<int32_t> segbase(nseg);
@@ -403,6 +448,14 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         for (int sgm = 0; sgm < nseg; ++sgm) {
             while (k < wnode.size() && wnode[k] < sgm * 32) ++k;
             segbase[sgm] = (int32_t)k;
+        }
+    }
+    std::vector<int32_t> rsegbase(nseg);
+    {
+        size_t k = 0;
+        for (int sgm = 0; sgm < nseg; ++sgm) {
+            while (k < rnode.size() && rnode[k] < sgm * 32) ++k;
+            rsegbase[sgm] = (int32_t)k;
         }
     }
     // upload
@@ -426,6 +479,30 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         CK(cudaMemcpyAsync(c->d_woff, woff.data(), c->nw * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
         CK(cudaMemcpyAsync(c->d_lq, sq.data(), n_links * sizeof(float), cudaMemcpyHostToDevice, c->stream), "link upload");
         CK(cudaMemcpyAsync(c->d_lwall, sw.data(), n_links * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "link upload");
+        if (cudaMalloc(&c->d_dlink, n_links * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->d_rsegbase, nseg * sizeof(int32_t)) != cudaSuccess) {
+            free_geometry(c);
+            return fail(c, LBM_ERR_NOMEM, "adjoint tables: out of device memory");
+        }
+        CK(cudaMemsetAsync(c->d_dlink, 0, n_links * sizeof(double), c->stream), "link accumulators");
+        CK(cudaMemcpyAsync(c->d_rsegbase, rsegbase.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+           "reverse table upload");
+        if (!rnode.empty()) {
+            const size_t nr = rnode.size();
+            if (cudaMalloc(&c->d_rmask, nr * sizeof(uint32_t)) != cudaSuccess ||
+                cudaMalloc(&c->d_roff, nr * sizeof(int32_t)) != cudaSuccess ||
+                cudaMalloc(&c->d_rlink, rlink.size() * sizeof(int32_t)) != cudaSuccess) {
+                free_geometry(c);
+                return fail(c, LBM_ERR_NOMEM, "adjoint tables: out of device memory");
+            }
+            CK(cudaMemcpyAsync(c->d_rmask, rmask.data(), nr * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream),
+               "reverse table upload");
+            CK(cudaMemcpyAsync(c->d_roff, roff.data(), nr * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+               "reverse table upload");
+            CK(cudaMemcpyAsync(c->d_rlink, rlink.data(), rlink.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               c->stream),
+               "reverse table upload");
+        }
     }
     if ((int)c->Twall.size() != n_walls) {
         cudaFree(c->d_Twall);
@@ -522,8 +599,8 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const
         dT = c->d_stage + 4 * N;
     }
     Buffers b = buffers(c);
-    b.fB = c->f[c->cur];  // write the current level in place
-    b.hB = c->h[c->cur];
+    b.fB = c->f[c->cur_f];  // write the current level in place
+    b.hB = c->h[c->cur_h];
     const DevParams p = c->dp;
     cudaStream_t s = c->stream;
     CK(dispatch(c, [&](auto tag) {
@@ -549,7 +626,8 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
             return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
         });
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
-        c->cur = 1 - c->cur;
+        c->cur_f = 1 - c->cur_f;
+        c->cur_h = 1 - c->cur_h;
     }
     return LBM_OK;
 }
@@ -680,7 +758,7 @@ lbm_status lbm_state_size(lbm_ctx* c, size_t* bytes) {
     return LBM_OK;
 }
 
-lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t* bytes) {
+lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t* bytes, int is_device) {
     if (!c || !bytes || !host_buf) return LBM_ERR_INVALID;
     DeviceGuard g(c->device);
     size_t need = 0;
@@ -700,31 +778,39 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t* bytes) {
     hd.fbytes = (uint64_t)27 * c->N * c->ssize;
     hd.hbytes = (uint64_t)c->qh * c->N * c->ssize;
     char* out = (char*)host_buf;
-    std::memcpy(out, &hd, sizeof(hd));
-    CK(cudaMemcpyAsync(out + sizeof(hd), c->f[c->cur], hd.fbytes, cudaMemcpyDeviceToHost, c->stream), "state copy");
-    CK(cudaMemcpyAsync(out + sizeof(hd) + hd.fbytes, c->h[c->cur], hd.hbytes, cudaMemcpyDeviceToHost, c->stream),
-       "state copy");
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (is_device) {
+        CK(cudaMemcpyAsync(out, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->stream), "state copy");
+    } else {
+        std::memcpy(out, &hd, sizeof(hd));
+    }
+    CK(cudaMemcpyAsync(out + sizeof(hd), c->f[c->cur_f], hd.fbytes, kind, c->stream), "state copy");
+    CK(cudaMemcpyAsync(out + sizeof(hd) + hd.fbytes, c->h[c->cur_h], hd.hbytes, kind, c->stream), "state copy");
     CK(cudaStreamSynchronize(c->stream), "state copy");
     *bytes = need;
     return LBM_OK;
 }
 
-lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
+lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes, int is_device) {
     if (!c || !host_buf) return LBM_ERR_INVALID;
     DeviceGuard g(c->device);
     if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
     StateHeader hd{};
     if (bytes < sizeof(hd)) return fail(c, LBM_ERR_INVALID, "state buffer too small");
-    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (is_device) {
+        CK(cudaMemcpy(&hd, host_buf, sizeof(hd), cudaMemcpyDeviceToHost), "state header");
+    } else {
+        std::memcpy(&hd, host_buf, sizeof(hd));
+    }
     if (std::memcmp(hd.magic, "LBMSTATE", 8) != 0 || hd.version != 1 || hd.nx != c->p.nx || hd.ny != c->p.ny ||
         hd.nz != c->p.nz || hd.qh != c->qh || hd.storage != c->p.storage ||
         hd.fbytes != (uint64_t)27 * c->N * c->ssize || hd.hbytes != (uint64_t)c->qh * c->N * c->ssize ||
         bytes < sizeof(hd) + hd.fbytes + hd.hbytes)
         return fail(c, LBM_ERR_INVALID, "state does not match this context");
     const char* in = (const char*)host_buf;
-    CK(cudaMemcpyAsync(c->f[c->cur], in + sizeof(hd), hd.fbytes, cudaMemcpyHostToDevice, c->stream), "state load");
-    CK(cudaMemcpyAsync(c->h[c->cur], in + sizeof(hd) + hd.fbytes, hd.hbytes, cudaMemcpyHostToDevice, c->stream),
-       "state load");
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c->f[c->cur_f], in + sizeof(hd), hd.fbytes, kind, c->stream), "state load");
+    CK(cudaMemcpyAsync(c->h[c->cur_h], in + sizeof(hd) + hd.fbytes, hd.hbytes, kind, c->stream), "state load");
     CK(cudaStreamSynchronize(c->stream), "state load");
     c->initialised = true;
     return LBM_OK;
@@ -759,6 +845,121 @@ lbm_status lbm_get_links(lbm_ctx* c, int64_t* n_links, int32_t* node, int32_t* d
         if (wall) wall[i] = c->h_lwall[i];
     }
     *n_links = total;
+    return LBM_OK;
+}
+
+static lbmd::AdjObjective to_adj(const lbm_objective* o) {
+    lbmd::AdjObjective a{};
+    a.kind = o ? o->kind : 0;
+    a.wall = o ? o->wall_id : -1;
+    a.plane = o ? o->plane_x : -1;
+    a.weight = o ? o->weight : 0.0;
+    if (!o) a.kind = 0, a.wall = -1;
+    return a;
+}
+
+static lbm_status check_objective(lbm_ctx* c, const lbm_objective* o) {
+    if (!o) return LBM_OK;
+    if (o->kind == LBM_OBJ_SURFACE_FLUX) {
+        if (o->wall_id < 0 || o->wall_id >= c->n_walls) return fail(c, LBM_ERR_INVALID, "objective wall id out of range");
+    } else if (o->kind == LBM_OBJ_SECTION_FLUX) {
+        if (o->plane_x < 0 || o->plane_x >= c->p.nx) return fail(c, LBM_ERR_INVALID, "objective plane out of range");
+    } else {
+        return fail(c, LBM_ERR_INVALID, "unknown objective kind");
+    }
+    if (!std::isfinite(o->weight)) return fail(c, LBM_ERR_INVALID, "objective weight not finite");
+    return LBM_OK;
+}
+
+lbm_status lbm_step_record(lbm_ctx* c, int n, void* u_rec, int advance_h) {
+    if (!c) return LBM_ERR_INVALID;
+    if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
+    if (n > 0 && !u_rec) return fail(c, LBM_ERR_INVALID, "null velocity record");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    DeviceGuard g(c->device);
+    const DevParams p = c->dp;
+    const size_t rsize = c->p.storage == LBM_F64 ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < n; ++i) {
+        Buffers b = buffers(c);
+        b.urec = (char*)u_rec + (size_t)i * 3 * c->N * rsize;
+        cudaError_t e = dispatch(c, [&](auto tag) {
+            using Tg = decltype(tag);
+            return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream, advance_h != 0);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c->cur_f = 1 - c->cur_f;
+        if (advance_h) c->cur_h = 1 - c->cur_h;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next, void* out,
+                            const lbm_objective* obj, double* dJ_dtheta) {
+    if (!c || !mu_next || !out) return LBM_ERR_INVALID;
+    if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    lbm_status st = check_objective(c, obj);
+    if (st != LBM_OK) return st;
+    DeviceGuard g(c->device);
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    const lbmd::AdjObjective a = to_adj(obj);
+    cudaError_t e;
+    if (c->p.storage == LBM_F64) {
+        e = c->qh == 27 ? lbmd::launch_adjoint<double, 27>(b, p, (const double*)u_level, (const double*)mu_next,
+                                                          (double*)out, a, dJ_dtheta, c->stream)
+                        : lbmd::launch_adjoint<double, 7>(b, p, (const double*)u_level, (const double*)mu_next,
+                                                         (double*)out, a, dJ_dtheta, c->stream);
+    } else {
+        e = c->qh == 27 ? lbmd::launch_adjoint<float, 27>(b, p, (const float*)u_level, (const float*)mu_next,
+                                                         (float*)out, a, dJ_dtheta, c->stream)
+                        : lbmd::launch_adjoint<float, 7>(b, p, (const float*)u_level, (const float*)mu_next,
+                                                        (float*)out, a, dJ_dtheta, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_wall_gradient(lbm_ctx* c, double* dJ_dTwall, int reset) {
+    if (!c || !dJ_dTwall) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    for (int w = 0; w < c->n_walls; ++w) dJ_dTwall[w] = 0.0;
+    if (c->nl == 0) return LBM_OK;
+    std::vector<double> acc((size_t)c->nl);
+    CK(cudaMemcpyAsync(acc.data(), c->d_dlink, c->nl * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "link gradient copy");
+    if (reset) CK(cudaMemsetAsync(c->d_dlink, 0, c->nl * sizeof(double), c->stream), "link gradient reset");
+    CK(cudaStreamSynchronize(c->stream), "link gradient");
+    for (int64_t l = 0; l < c->nl; ++l) dJ_dTwall[c->h_lwall[l]] += acc[l];
+    return LBM_OK;
+}
+
+lbm_status lbm_objective_accumulate(lbm_ctx* c, const lbm_objective* obj, double* J_device) {
+    if (!c || !obj || !J_device) return LBM_ERR_INVALID;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    lbm_status st = check_objective(c, obj);
+    if (st != LBM_OK) return st;
+    DeviceGuard g(c->device);
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    const lbmd::AdjObjective a = to_adj(obj);
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_objective<typename Tg::S, Tg::Q>(b, p, a, c->d_scratch, J_device, c->stream);
+       }),
+       "objective launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_section_flux(lbm_ctx* c, int plane_x, double* flux) {
+    if (!c || !flux) return LBM_ERR_INVALID;
+    lbm_objective o{LBM_OBJ_SECTION_FLUX, 0, plane_x, 1.0};
+    double* acc = c->d_scratch + 3 * lbmd::kRedBlocks + 3;
+    DeviceGuard g(c->device);
+    CK(cudaMemsetAsync(acc, 0, sizeof(double), c->stream), "section flux");
+    lbm_status st = lbm_objective_accumulate(c, &o, acc);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(flux, acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "section flux copy");
+    CK(cudaStreamSynchronize(c->stream), "section flux");
     return LBM_OK;
 }
 

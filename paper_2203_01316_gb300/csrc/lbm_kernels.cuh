@@ -7,8 +7,9 @@
 
 namespace lbmd {
 
-// internal node flags: bits 0-1 type, bit 2 = has at least one wall link
-enum : uint8_t { T_FLUID = 0, T_SOLID = 1, T_INLET = 2, T_OUTLET = 3, F_WALL = 4 };
+// internal node flags: bits 0-1 type, bit 2 = has at least one wall link,
+// bit 3 = is x_f (= x - e_a) of a wall link (x, a) with q <= 1/2
+enum : uint8_t { T_FLUID = 0, T_SOLID = 1, T_INLET = 2, T_OUTLET = 3, F_WALL = 4, F_RWALL = 8 };
 
 struct Buffers {
     const void* fA;  // post-collision state, time t
@@ -26,13 +27,38 @@ struct Buffers {
     const int32_t* lwall;     // per link wall id
     const float* Twall;       // per wall temperature
     int nw;                   // number of wall nodes
+    // adjoint: nodes y that are x_f = x - e_a of a link (x, a) with q <= 1/2
+    const int32_t* rseg_base; // such nodes before each 32-node segment
+    const uint32_t* rmask;    // bit a set: y + e_a has link a with q <= 1/2
+    const int32_t* roff;      // first entry in rlink
+    const int32_t* rlink;     // link index (into lq / lwall) of each entry
+    double* dlink;            // per link accumulator of dJ/dT_w terms
+    void* urec;               // recorded velocities of a step (3N, R) or nullptr
+};
+
+// objective of the adjoint: a linear flux of the post-collision h state
+struct AdjObjective {
+    int kind;       // 0: surface heat flux of `wall`; 1: sum e_x h over the plane x = plane
+    int wall, plane;
+    double weight;  // 0: no objective term at this level
 };
 
 constexpr int kBlock = 128;
 constexpr int kRedBlocks = 1216;  // 8 x 152 SMs, partial sums of the reductions
 constexpr int kRedThreads = 256;
 
-template <typename S, int QH> cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s);
+// advance_h = false advances f only (velocity recomputation for the adjoint);
+// b.urec non-null records the velocity u used by each node's collision
+template <typename S, int QH>
+cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h = true);
+// adjoint of one level of the h evolution (R = float, or double for FP64 storage)
+template <typename R, int QH>
+cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* mu_next, R* mu_out,
+                           AdjObjective obj, double* dtheta, cudaStream_t s);
+// *acc += weight * F(current level) (F: surface flux of a wall or section flux of a plane)
+template <typename S, int QH>
+cudaError_t launch_objective(const Buffers& b, const DevParams& p, AdjObjective obj, double* scratch, double* acc,
+                             cudaStream_t s);
 template <typename S, int QH>
 cudaError_t launch_init(const Buffers& b, const DevParams& p, const double* rho, const double* u, const double* T,
                         cudaStream_t s);
@@ -125,8 +151,11 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 5
 #endif
-template <typename S, int QH>
-__global__ void __launch_bounds__(kBlock, LBM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ fA, S* __restrict__ fB,
+// FP64 arithmetic needs twice the registers: 2 blocks per SM
+template <typename S> constexpr int step_min_blocks() { return sizeof(typename Acc<S>::R) == 8 ? 2 : LBM_STEP_MIN_BLOCKS; }
+
+template <typename S, int QH, bool DO_H, bool REC>
+__global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* __restrict__ fA, S* __restrict__ fB,
                                                   const S* __restrict__ hA, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags,
                                                   const float* __restrict__ theta,
@@ -136,7 +165,8 @@ __global__ void __launch_bounds__(kBlock, LBM_STEP_MIN_BLOCKS) k_step(const S* _
                                                   const int32_t* __restrict__ woff,
                                                   const float* __restrict__ lq,
                                                   const int32_t* __restrict__ lwall,
-                                                  const float* __restrict__ Twall, const DevParams p) {
+                                                  const float* __restrict__ Twall,
+                                                  typename Acc<S>::R* __restrict__ urec, const DevParams p) {
     using R = typename Acc<S>::R;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in_range = n < p.N;
@@ -150,8 +180,15 @@ __global__ void __launch_bounds__(kBlock, LBM_STEP_MIN_BLOCKS) k_step(const S* _
     if (type == T_INLET) {
 #pragma unroll
         for (int a = 0; a < 27; ++a) st(fB + a * N + n, inlet[a]);
+        if (DO_H) {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
+            for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
+        }
+        if (REC) {
+            urec[n] = (R)p.uin[0];
+            urec[N + n] = (R)p.uin[1];
+            urec[2 * N + n] = (R)p.uin[2];
+        }
         return;
     }
     uint32_t mask = 0;
@@ -188,6 +225,12 @@ __global__ void __launch_bounds__(kBlock, LBM_STEP_MIN_BLOCKS) k_step(const S* _
     }
     R ux, uy, uz;
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
+    if (REC) {
+        urec[n] = ux;
+        urec[N + n] = uy;
+        urec[2 * N + n] = uz;
+    }
+    if constexpr (DO_H) {
     R hd[QH];
 #pragma unroll
     for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + i * N + src_of(nb, HDIR<QH>(i)));
@@ -215,14 +258,22 @@ __global__ void __launch_bounds__(kBlock, LBM_STEP_MIN_BLOCKS) k_step(const S* _
     }
     const R Q = theta ? (R)__ldg(theta + n) : R(0);
     collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+    }
 }
 
-template <typename S, int QH> cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s) {
+template <typename S, int QH>
+cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h) {
     using R = typename Acc<S>::R;
     const int grid = (p.N + kBlock - 1) / kBlock;
-    k_step<S, QH><<<grid, kBlock, 0, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta,
-                                          (const R*)b.inlet_post, b.seg_base, b.wmask, b.woff, b.lq, b.lwall,
-                                          b.Twall, p);
+    R* urec = (R*)b.urec;
+#define LBM_STEP_ARGS                                                                                            \
+    (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, b.seg_base, \
+        b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, p
+    if (advance_h && !urec) k_step<S, QH, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+    else if (advance_h) k_step<S, QH, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+    else if (urec) k_step<S, QH, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+    else k_step<S, QH, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+#undef LBM_STEP_ARGS
     return cudaGetLastError();
 }
 
@@ -485,6 +536,298 @@ cudaError_t launch_surface_flux(const Buffers& b, const DevParams& p, int wall, 
     k_surface_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.wnode, b.wmask, b.woff, b.lq, b.lwall,
                                                             b.Twall, b.nw, wall, scratch, p);
     k_reduce_partials<1><<<1, 1024, 0, s>>>(scratch, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+// ---- adjoint of the h evolution --------------------------------------------
+// With u fixed (one-way coupling), one step is g^{k+1} = P s^k + b(T_w) and
+// s^{k+1} = L(u^{k+1}) g^{k+1} + e(u^{k+1}) theta, with
+// L = T^-1 (1 - S) T + T^-1 S E 1^T and e = T^-1 E (Eq. H_cm_collision and
+// the App. D source).  One call computes, per node y,
+//   lambda^k(y) = (P^T mu^{k+1})(y) + dJ_k/ds^k(y)           (gather)
+//   mu^k(y)     = L(u^k)^T lambda^k = T^T (1-S) z + 1 (E^T S z),  z = T^-T lambda
+//   dJ/dtheta(y) += E^T z,   dJ/dT_w(link) += (db/dT_w) mu^{k+1}
+// P^T is a pull from y + e_a (the transpose of the forward pull), plus the
+// Eq. IABB partials of the wall links that read y.
+
+// transposes of the 3-point maps fwd3 / inv3 (same slot conventions)
+template <typename R> __device__ __forceinline__ void fwd3T(R& a, R& b, R& c, R v) {
+    const R m0 = a - v * b + v * v * c;
+    const R m1 = b - R(2) * v * c;
+    const R m2 = c;
+    a = m0 - m1 + m2;
+    b = m0;
+    c = m0 + m1 + m2;
+}
+template <typename R> __device__ __forceinline__ void inv3T(R& a, R& b, R& c, R v) {
+    const R m2 = R(0.5) * (a + c) - b;
+    const R m1 = R(0.5) * (c - a);
+    const R m0 = b;
+    a = m0 + v * m1 + v * v * m2;
+    b = m1 + R(2) * v * m2;
+    c = m2;
+}
+
+// partial derivatives of one Eq. IABB arrival with respect to h*_a(x_b),
+// h*_abar(x_b) and T_w (the latter per unit weight w_a)
+template <typename R>
+__device__ __forceinline__ void iabb_partials(float q, bool thin, R& d_ab, R& d_abb, R& d_T) {
+    if (q <= 0.5f && !thin) {
+        d_ab = -R(2) * (R)q; d_abb = R(0); d_T = R(2);
+    } else {
+        const R qq = (R)fmaxf(q, 0.5f);
+        d_ab = -R(1) / (R(2) * qq); d_abb = (R(2) * qq - R(1)) / (R(2) * qq); d_T = R(2) / (R(2) * qq);
+    }
+}
+
+template <typename R, int QH>
+__global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_next, R* __restrict__ out,
+                                                     const R* __restrict__ uk, double* __restrict__ dtheta,
+                                                     const uint8_t* __restrict__ flags,
+                                                     const int32_t* __restrict__ seg_base,
+                                                     const uint32_t* __restrict__ wmask,
+                                                     const int32_t* __restrict__ woff, const float* __restrict__ lq,
+                                                     const int32_t* __restrict__ lwall,
+                                                     const int32_t* __restrict__ rseg_base,
+                                                     const uint32_t* __restrict__ rmask,
+                                                     const int32_t* __restrict__ roff,
+                                                     const int32_t* __restrict__ rlink, double* __restrict__ dlink,
+                                                     const AdjObjective obj, const DevParams p) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = n < p.N;
+    const uint8_t fl = in_range ? flags[n] : (uint8_t)T_SOLID;
+    const bool is_wall = (fl & F_WALL) != 0, is_rw = (fl & F_RWALL) != 0;
+    const uint32_t bal_w = __ballot_sync(0xffffffffu, is_wall);
+    const uint32_t bal_r = __ballot_sync(0xffffffffu, is_rw);
+    if (!in_range) return;
+    const int N = p.N;
+    const int type = fl & 3;
+    if (type == T_SOLID || type == T_INLET) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) out[i * N + n] = R(0);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int x, y, z;
+    node_xyz(n, p, x, y, z);
+    // push neighbours: index 0 <-> e = -1, 2 <-> e = +1; -1 when outside a bounded x
+    int xt[3] = {x - 1, x, x + 1};
+    if (p.periodic_x) {
+        if (xt[0] < 0) xt[0] += p.nx;
+        if (xt[2] >= p.nx) xt[2] -= p.nx;
+    } else {
+        if (xt[0] < 0) xt[0] = -1;
+        if (xt[2] >= p.nx) xt[2] = -1;
+    }
+    const int yt[3] = {((y == 0) ? p.ny - 1 : y - 1) * p.nx, y * p.nx, ((y == p.ny - 1) ? 0 : y + 1) * p.nx};
+    const int pl = p.nx * p.ny;
+    const int zt[3] = {((z == 0) ? p.nz - 1 : z - 1) * pl, z * pl, ((z == p.nz - 1) ? 0 : z + 1) * pl};
+    const R wsurf = (obj.kind == 0) ? (R)obj.weight : R(0);
+    R lam[QH];
+#pragma unroll
+    for (int i = 0; i < QH; ++i) {
+        const int a = HDIR<QH>(i);
+        lam[i] = R(0);
+        const int xx = xt[EX(a) + 1];
+        if (xx < 0) continue;
+        const int t = xx + yt[EY(a) + 1] + zt[EZ(a) + 1];
+        const int tt = flags[t] & 3;
+        if (tt != T_SOLID && tt != T_INLET) lam[i] = mu_next[i * N + t];
+    }
+    if (!p.periodic_x && x == p.nx - 1) {
+        // outlet plane: its incoming e_x < 0 populations copy this node's value
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            if (EX(a) != -1) continue;
+            const int t = x + yt[EY(a) + 1] + zt[EZ(a) + 1];
+            lam[i] += mu_next[i * N + t];
+        }
+    }
+    if (is_rw) {
+        // this node is x_f of links (t = y + e_a, a) with q <= 1/2
+        const int idx = __ldg(rseg_base + (n >> 5)) + __popc(bal_r & lt);
+        const uint32_t rm = __ldg(rmask + idx);
+        const int ro = __ldg(roff + idx);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            if (!(rm & (1u << a))) continue;
+            const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
+            const float q = __ldg(lq + l);
+            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+            const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
+            lam[i] -= (R(1) - R(2) * (R)q) * (mu_next[HOPP<QH>(i) * N + t] + cw);
+        }
+    }
+    if (is_wall) {
+        const int idx = __ldg(seg_base + (n >> 5)) + __popc(bal_w & lt);
+        const uint32_t mask = __ldg(wmask + idx);
+        const int off = __ldg(woff + idx);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int b = HDIR<QH>(i);
+            if (!(mask & (1u << b))) continue;
+            const int ib = HOPP<QH>(i);
+            const int l = off + __popc(mask & ((1u << b) - 1u));
+            const float q = __ldg(lq + l);
+            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+            const bool thin = (mask >> HDIR<QH>(ib)) & 1u;
+            R d_ab, d_abb, d_T;
+            iabb_partials<R>(q, thin, d_ab, d_abb, d_T);
+            const R m = mu_next[ib * N + n] + cw;
+            lam[i] += d_ab * m - cw;
+            lam[ib] += d_abb * m;
+            dlink[l] += (double)d_T * HW<QH>(i) * (double)m;
+        }
+    }
+    if (obj.kind == 1 && x == obj.plane) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) lam[i] += (R)obj.weight * (R)EX(HDIR<QH>(i));
+    }
+    if (!uk) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) out[i * N + n] = lam[i];
+        return;
+    }
+    const R ux = uk[n], uy = uk[N + n], uz = uk[2 * N + n];
+    double dth = 0.0;
+    if constexpr (QH == 27) {
+        R cb[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) cb[CUBE(a)] = lam[a];
+        // z = T^-T lambda
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+        for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+            for (int xx = 0; xx < 3; ++xx) inv3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+        R rank = R(0);
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int nn = 0; nn < 3; ++nn)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const R E = Eq<R>(m, nn, o);
+                    const R sr = (R)p.sh[m + nn + o];
+                    R& v = cb[MIDX(m, nn, o)];
+                    if (E != R(0)) {
+                        dth += (double)(E * v);
+                        rank += E * sr * v;
+                    }
+                    v *= (R(1) - sr);
+                }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+        for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+            for (int xx = 0; xx < 3; ++xx) fwd3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+#pragma unroll
+        for (int a = 0; a < 27; ++a) out[a * N + n] = cb[CUBE(a)] + rank;
+    } else {
+        // D3Q7: moments 000, 100/010/001, 200/020/002
+        const R u[3] = {ux, uy, uz};
+        const R c = cs2<R>();
+        // z = T^-T lambda (transpose of the D3Q7 inverse transform of collide_h7)
+        R z0 = lam[0], z1[3], z2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R mb2 = R(0.5) * (lam[1 + d] + lam[4 + d]) - lam[0];
+            const R mb1 = R(0.5) * (lam[1 + d] - lam[4 + d]);
+            z2[d] = mb2;
+            z1[d] = mb1 + R(2) * u[d] * mb2;
+            z0 += u[d] * mb1 + u[d] * u[d] * mb2;
+        }
+        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+        dth = (double)z0 + (double)(c * (z2[0] + z2[1] + z2[2]));
+        const R rank = s0 * z0 + s2 * c * (z2[0] + z2[1] + z2[2]);
+        z0 *= (R(1) - s0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            z1[d] *= (R(1) - s1);
+            z2[d] *= (R(1) - s2);
+        }
+        // T^T z: population i gets z0 + sum_d (e_id - u_d) z1_d + (e_id - u_d)^2 z2_d
+        R base = z0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) base += -u[d] * z1[d] + u[d] * u[d] * z2[d];
+        out[n] = base + rank;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R rest_d = -u[d] * z1[d] + u[d] * u[d] * z2[d];
+            const R plus = (R(1) - u[d]) * z1[d] + (R(1) - u[d]) * (R(1) - u[d]) * z2[d];
+            const R minus = (R(-1) - u[d]) * z1[d] + (R(1) + u[d]) * (R(1) + u[d]) * z2[d];
+            out[(1 + d) * N + n] = base - rest_d + plus + rank;
+            out[(4 + d) * N + n] = base - rest_d + minus + rank;
+        }
+    }
+    if (dtheta) dtheta[n] += dth;
+}
+
+template <typename R, int QH>
+cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* mu_next, R* mu_out,
+                           AdjObjective obj, double* dtheta, cudaStream_t s) {
+    const int grid = (p.N + kBlock - 1) / kBlock;
+    k_adjoint<R, QH><<<grid, kBlock, 0, s>>>(mu_next, mu_out, u_level, dtheta, b.flags, b.seg_base, b.wmask, b.woff,
+                                             b.lq, b.lwall, b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p);
+    return cudaGetLastError();
+}
+
+template <int NV>
+__global__ void k_reduce_accumulate(const double* __restrict__ part, int nparts, double weight,
+                                    double* __restrict__ acc) {
+    __shared__ double sh[32 * NV];
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += part[i * NV + k];
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) acc[0] += weight * v[0];
+}
+
+// x-flux sum e_x h through the plane x = plane (Sec. 4.4 section flux; the
+// shift w T_ref carries no x-flux)
+template <typename S, int QH>
+__global__ void __launch_bounds__(kRedThreads) k_section_flux(const S* __restrict__ hA,
+                                                              const uint8_t* __restrict__ flags, int plane,
+                                                              double* __restrict__ part, const DevParams p) {
+    using R = typename Acc<S>::R;
+    __shared__ double sh[32];
+    double v[1] = {0.0};
+    const size_t N = (size_t)p.N;
+    const int nrow = p.ny * p.nz;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrow; r += gridDim.x * blockDim.x) {
+        const int n = plane + p.nx * r;
+        if ((flags[n] & 3) == T_SOLID) continue;
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int ex = EX(HDIR<QH>(i));
+            if (ex != 0) v[0] += (double)ex * (double)ld<R>(hA + i * N + n);
+        }
+    }
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+template <typename S, int QH>
+cudaError_t launch_objective(const Buffers& b, const DevParams& p, AdjObjective obj, double* scratch, double* acc,
+                             cudaStream_t s) {
+    if (obj.kind == 0)
+        k_surface_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.wnode, b.wmask, b.woff, b.lq,
+                                                                b.lwall, b.Twall, b.nw, obj.wall, scratch, p);
+    else
+        k_section_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.flags, obj.plane, scratch, p);
+    k_reduce_accumulate<1><<<1, 1024, 0, s>>>(scratch, kRedBlocks, obj.weight, acc);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,9 @@
 
 namespace lbmd {
 #define LBM_INST(Q)                                                                                              \
-    template cudaError_t launch_step<__nv_bfloat16, Q>(const Buffers&, const DevParams&, cudaStream_t);                    \
+    template cudaError_t launch_step<__nv_bfloat16, Q>(const Buffers&, const DevParams&, cudaStream_t, bool);              \
+    template cudaError_t launch_objective<__nv_bfloat16, Q>(const Buffers&, const DevParams&, AdjObjective, double*, double*, \
+                                                  cudaStream_t);                                                 \
     template cudaError_t launch_init<__nv_bfloat16, Q>(const Buffers&, const DevParams&, const double*, const double*,     \
                                              const double*, cudaStream_t);                                       \
     template cudaError_t launch_macros<__nv_bfloat16, Q>(const Buffers&, const DevParams&, double*, double*, double*,      \

@@ -4,7 +4,9 @@
 
 namespace lbmd {
 #define LBM_INST(Q)                                                                                              \
-    template cudaError_t launch_step<float, Q>(const Buffers&, const DevParams&, cudaStream_t);                    \
+    template cudaError_t launch_step<float, Q>(const Buffers&, const DevParams&, cudaStream_t, bool);              \
+    template cudaError_t launch_objective<float, Q>(const Buffers&, const DevParams&, AdjObjective, double*, double*, \
+                                                  cudaStream_t);                                                 \
     template cudaError_t launch_init<float, Q>(const Buffers&, const DevParams&, const double*, const double*,     \
                                              const double*, cudaStream_t);                                       \
     template cudaError_t launch_macros<float, Q>(const Buffers&, const DevParams&, double*, double*, double*,      \
@@ -17,6 +19,10 @@ namespace lbmd {
                                                      cudaStream_t);
 LBM_INST(27)
 LBM_INST(7)
+template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&, const float*, const float*, float*,
+                                            AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*, float*,
+                                           AdjObjective, double*, cudaStream_t);
 
 // streaming map of the step kernels (storage independent)
 __global__ void k_stream_map(const uint8_t* __restrict__ flags, const int32_t* __restrict__ wnode,

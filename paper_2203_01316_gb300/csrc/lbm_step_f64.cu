@@ -4,7 +4,9 @@
 
 namespace lbmd {
 #define LBM_INST(Q)                                                                                              \
-    template cudaError_t launch_step<double, Q>(const Buffers&, const DevParams&, cudaStream_t);                    \
+    template cudaError_t launch_step<double, Q>(const Buffers&, const DevParams&, cudaStream_t, bool);              \
+    template cudaError_t launch_objective<double, Q>(const Buffers&, const DevParams&, AdjObjective, double*, double*, \
+                                                  cudaStream_t);                                                 \
     template cudaError_t launch_init<double, Q>(const Buffers&, const DevParams&, const double*, const double*,     \
                                              const double*, cudaStream_t);                                       \
     template cudaError_t launch_macros<double, Q>(const Buffers&, const DevParams&, double*, double*, double*,      \
@@ -17,4 +19,8 @@ namespace lbmd {
                                                      cudaStream_t);
 LBM_INST(27)
 LBM_INST(7)
+template cudaError_t launch_adjoint<double, 27>(const Buffers&, const DevParams&, const double*, const double*, double*,
+                                            AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<double, 7>(const Buffers&, const DevParams&, const double*, const double*, double*,
+                                           AdjObjective, double*, cudaStream_t);
 }  // namespace lbmd

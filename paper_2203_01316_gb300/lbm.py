@@ -23,7 +23,16 @@ STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
 SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_set_inlet", "lbm_set_force",
            "lbm_set_source", "lbm_init_fields", "lbm_step", "lbm_macros", "lbm_get_populations", "lbm_balances",
            "lbm_surface_flux", "lbm_nusselt", "lbm_state_size", "lbm_save_state", "lbm_load_state",
-           "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc"]
+           "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
+           "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
+           "lbm_adjoint_wall_gradient"]
+OBJ_SURFACE, OBJ_SECTION = 0, 1
+
+
+class Objective(C.Structure):
+    """lbm_objective: J += weight * F(level), F the surface flux of a wall or
+    the section flux of a plane."""
+    _fields_ = [("kind", C.c_int), ("wall_id", C.c_int), ("plane_x", C.c_int), ("weight", C.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -71,8 +80,13 @@ def lib():
         "lbm_surface_flux": [vp, i32, C.POINTER(dbl)],
         "lbm_nusselt": [vp, i32, dbl, dbl, dbl, C.POINTER(dbl)],
         "lbm_state_size": [vp, C.POINTER(C.c_size_t)],
-        "lbm_save_state": [vp, vp, C.POINTER(C.c_size_t)],
-        "lbm_load_state": [vp, vp, C.c_size_t],
+        "lbm_save_state": [vp, vp, C.POINTER(C.c_size_t), i32],
+        "lbm_load_state": [vp, vp, C.c_size_t, i32],
+        "lbm_section_flux": [vp, i32, C.POINTER(dbl)],
+        "lbm_objective_accumulate": [vp, C.POINTER(Objective), vp],
+        "lbm_step_record": [vp, i32, vp, i32],
+        "lbm_adjoint_step": [vp, vp, vp, vp, C.POINTER(Objective), vp],
+        "lbm_adjoint_wall_gradient": [vp, C.POINTER(dbl), i32],
         "lbm_stream_map": [vp, vp, i32],
         "lbm_get_links": [vp, C.POINTER(i64), vp, vp, vp, vp],
         "lbm_sync": [vp],
@@ -233,15 +247,60 @@ class Solver:
         self._check(self.L.lbm_nusselt(self._h, int(wall), float(length), float(area), float(dT), C.byref(v)))
         return v.value
 
-    def save_state(self) -> bytes:
+    def state_size(self) -> int:
         n = C.c_size_t()
         self._check(self.L.lbm_state_size(self._h, C.byref(n)))
+        return n.value
+
+    def save_state(self, out=None):
+        """bytes (host) or, with `out` a CUDA uint8 tensor of state_size()
+        bytes, a device copy written into `out`."""
+        n = C.c_size_t(self.state_size())
+        if out is not None:
+            self._check(self.L.lbm_save_state(self._h, out.data_ptr(), C.byref(n), 1))
+            return out
         buf = C.create_string_buffer(n.value)
-        self._check(self.L.lbm_save_state(self._h, buf, C.byref(n)))
+        self._check(self.L.lbm_save_state(self._h, buf, C.byref(n), 0))
         return buf.raw[: n.value]
 
-    def load_state(self, data: bytes):
-        self._check(self.L.lbm_load_state(self._h, data, len(data)))
+    def load_state(self, data):
+        if _is_torch(data):
+            self._check(self.L.lbm_load_state(self._h, data.data_ptr(), data.numel(), 1 if data.is_cuda else 0))
+        else:
+            self._check(self.L.lbm_load_state(self._h, data, len(data), 0))
+
+    def section_flux(self, plane_x):
+        q = C.c_double()
+        self._check(self.L.lbm_section_flux(self._h, int(plane_x), C.byref(q)))
+        return q.value
+
+    # -- adjoint (device tensors; see include/lbm.h) --
+    @staticmethod
+    def objective(kind, index, weight=1.0):
+        o = Objective()
+        o.kind = OBJ_SURFACE if kind == "surface" else OBJ_SECTION
+        o.wall_id = int(index) if o.kind == OBJ_SURFACE else 0
+        o.plane_x = int(index) if o.kind == OBJ_SECTION else 0
+        o.weight = float(weight)
+        return o
+
+    def objective_accumulate(self, obj, J_device):
+        self._check(self.L.lbm_objective_accumulate(self._h, C.byref(obj), J_device.data_ptr()))
+
+    def step_record(self, n, u_rec, advance_h=True):
+        self._check(self.L.lbm_step_record(self._h, int(n), u_rec.data_ptr() if n > 0 else None,
+                                           1 if advance_h else 0))
+
+    def adjoint_step(self, u_level, mu_next, out, obj=None, dtheta=None):
+        self._check(self.L.lbm_adjoint_step(self._h, u_level.data_ptr() if u_level is not None else None,
+                                            mu_next.data_ptr(), out.data_ptr(),
+                                            C.byref(obj) if obj is not None else None,
+                                            dtheta.data_ptr() if dtheta is not None else None))
+
+    def adjoint_wall_gradient(self, n_walls, reset=True):
+        g = (C.c_double * n_walls)()
+        self._check(self.L.lbm_adjoint_wall_gradient(self._h, g, 1 if reset else 0))
+        return np.array(g[:], dtype=np.float64)
 
     def stream_map(self):
         src = np.empty((27, self.N), np.int32)
