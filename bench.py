@@ -1,5 +1,6 @@
 """Benchmark of the coupled f+h stream+collide step (MLUPS and fraction of the
-HBM roofline) on synthetic inputs.
+HBM roofline) and of its adjoint (adjoint/forward time ratio) on synthetic
+inputs.
 
 Workload (default): heated sphere in a channel, 384 x 128 x 128 nodes, sphere
 diameter 32 at x = 96 (seeded sub-lattice offset), inlet u = 0.02 / T = 0,
@@ -266,6 +267,42 @@ def _config(w=None, storage="f32"):
             "l2": f"inputs larger than L2 ({traffic:.2f} GB population traffic per step)"}
 
 
+def measure_adjoint(w, stream, fwd_ms, steps=200, every=50):
+    """Adjoint/forward time ratio: J = surface heat flux of the sphere summed
+    over the last fifth of `steps` steps; backward = restore the checkpoint
+    of each segment, recompute its velocities (f only), run the adjoint
+    kernel level by level (paper_2203_01316_gb300.autograd)."""
+    import torch
+    from paper_2203_01316_gb300.autograd import thermal_objective
+    s = make_solver(w, "f32", stream=stream.cuda_stream)
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    N = w["flags"].size
+    state0 = s.save_state(torch.empty(s.state_size(), dtype=torch.uint8, device="cuda"))
+    theta = torch.zeros(N, dtype=torch.float64, device="cuda", requires_grad=True)
+    Tw = torch.tensor([WORKLOAD["T_wall"]], dtype=torch.float64, requires_grad=True)
+    obj = s.objective("surface", 0, 1.0)
+    window = (steps - steps // 5, steps)
+    # one untimed pass: device buffers and kernel modules come up here
+    Jw = thermal_objective(theta, Tw, s, state0, steps, window, obj, every=every)
+    Jw.backward()
+    theta.grad = None
+    Tw.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = thermal_objective(theta, Tw, s, state0, steps, window, obj, every=every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    bwd = (t2 - t1) / steps * 1e3
+    return {"steps": steps, "checkpoint_every": every, "objective": "sphere surface heat flux, last 20% of steps",
+            "forward_with_checkpoints_ms_per_step": (t1 - t0) / steps * 1e3,
+            "backward_ms_per_step": bwd, "forward_ms_per_step": fwd_ms, "ratio": bwd / fwd_ms,
+            "dJ_dTwall": float(Tw.grad[0]), "grad_theta_norm": float(theta.grad.norm())}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -348,6 +385,7 @@ def run_ours(args):
 
     line["e2e"] = e2e
     line["storage_variants"] = variants
+    line["adjoint"] = measure_adjoint(w, stream, ms, steps=args.adjoint_steps)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
@@ -370,6 +408,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0,
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end run and the storage variants")
     args = ap.parse_args()

@@ -200,7 +200,9 @@ lbm_status lbm_step_record(lbm_ctx* ctx, int n, void* u_rec, int advance_h);
  * e(u^k)^T lambda^k to dJ_dtheta[N] (device double, may be NULL); with
  * u_level NULL (the initial level) it writes lambda^0 to out.  The dJ/dT_w
  * terms are accumulated inside the context (lbm_adjoint_wall_gradient).
- * mu_next and out must not alias.  Asynchronous. */
+ * mu_next must be zero at solid and inlet nodes (true of zero-filled arrays
+ * and of every out this call writes); mu_next and out must not alias.
+ * Asynchronous. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_next, void* out,
                             const lbm_objective* obj, double* dJ_dtheta);
 

@@ -624,16 +624,14 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     const int pl = p.nx * p.ny;
     const int zt[3] = {((z == 0) ? p.nz - 1 : z - 1) * pl, z * pl, ((z == p.nz - 1) ? 0 : z + 1) * pl};
     const R wsurf = (obj.kind == 0) ? (R)obj.weight : R(0);
+    // mu_next is zero at solid and inlet nodes (this kernel writes zeros
+    // there), which are exactly the nodes that pull nothing: no flag test
     R lam[QH];
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
         const int a = HDIR<QH>(i);
-        lam[i] = R(0);
         const int xx = xt[EX(a) + 1];
-        if (xx < 0) continue;
-        const int t = xx + yt[EY(a) + 1] + zt[EZ(a) + 1];
-        const int tt = flags[t] & 3;
-        if (tt != T_SOLID && tt != T_INLET) lam[i] = mu_next[i * N + t];
+        lam[i] = (xx < 0) ? R(0) : __ldg(mu_next + i * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]);
     }
     if (!p.periodic_x && x == p.nx - 1) {
         // outlet plane: its incoming e_x < 0 populations copy this node's value
