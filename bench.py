@@ -303,6 +303,86 @@ def measure_adjoint(w, stream, fwd_ms, steps=200, every=50):
             "dJ_dTwall": float(Tw.grad[0]), "grad_theta_norm": float(theta.grad.norm())}
 
 
+def precision_study(args):
+    """Precision form of the heated sphere (Pr = 1000): populations stored
+    in FP16 / BF16 (stochastic and nearest rounding) / FP32 with FP32
+    arithmetic against the FP64 path, after
+    `steps` steps: relative L2 error of u and T over the fluid nodes and the
+    relative error of the sphere's Nusselt number averaged over the last 10%
+    of the steps.  scale 1: 384x128x128 (D = 32) against the FP64 GPU path;
+    --precision-crop: 96x32x32 (D = 8) against the FP64 oracle."""
+    import torch
+    from paper_2203_01316_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream()
+    scale = 0.25 if args.precision_crop else args.scale
+    w = make_workload(scale)
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    D = w["D"]
+    fluid = np.asarray(w["flags"]) == 0
+    steps = args.steps
+    win = max(1, steps // 10)
+    k = WORKLOAD["nu"] * scale / WORKLOAD["Pr"]   # nu = U D / Re scales with D
+    nu = WORKLOAD["nu"] * scale
+    area = math.pi * D * D
+    out = {}
+
+    def run(storage, round_nearest=False):
+        from paper_2203_01316_gb300 import Solver
+        s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind="trt", storage=storage, periodic_x=False,
+                   rho0=1.0, T_ref=0.5, stream=stream.cuda_stream, round_nearest=round_nearest)
+        s.set_geometry(w["flags"], w["links"], n_walls=1)
+        s.set_bc(0, WORKLOAD["T_wall"])
+        s.set_inlet(w["u_in"], w["T_in"])
+        s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        J = torch.zeros(1, dtype=torch.float64, device="cuda")
+        obj = s.objective("surface", 0, D / (k * area * (WORKLOAD["T_wall"] - WORKLOAD["T_in"])) / win)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps - win)
+        for _ in range(win):
+            s.objective_accumulate(obj, J)
+            s.step(1)
+        rho, u, T = s.macros()
+        dt = time.perf_counter() - t0
+        Nu = float(J.item())
+        s.close()
+        return u, T, Nu, dt
+
+    if args.precision_crop:
+        from oracle import oracle as O
+        O.build()
+        p = O.make_params(nx=nx, ny=ny, nz=nz, qh=27, hkind="trt", periodic_x=False, nu=nu, k=k,
+                          u_in=w["u_in"], T_in=w["T_in"])
+        o = O.Oracle(p)
+        o.set_geometry(w["flags"], w["links"], nwalls=1)
+        o.set_wall_temperature(0, WORKLOAD["T_wall"])
+        o.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        # the GPU stores post-collision states; the oracle's level t is its
+        # state after t steps, collided once more for the flux of t -> t+1
+        o.step(steps - win)
+        Nu_ref = 0.0
+        for _ in range(win):
+            Nu_ref += o.surface_flux(0) * D / (k * area * (WORKLOAD["T_wall"] - WORKLOAD["T_in"])) / win
+            o.step(1)
+        _, u_ref, T_ref = o.macros()
+        ref = "FP64 oracle"
+    else:
+        u_ref, T_ref, Nu_ref, _ = run("f64")
+        ref = "FP64 GPU path"
+    for name, storage, rn in (("f32", "f32", False), ("f16", "f16", False), ("f16_round_nearest", "f16", True),
+                              ("bf16", "bf16", False), ("bf16_round_nearest", "bf16", True)):
+        u, T, Nu, dt = run(storage, rn)
+        out[name] = {
+            "rel_l2_u": float(np.sqrt(np.sum((u[:, fluid] - u_ref[:, fluid]) ** 2) / np.sum(u_ref[:, fluid] ** 2))),
+            "rel_l2_T": float(np.sqrt(np.sum((T[fluid] - T_ref[fluid]) ** 2) / np.sum(T_ref[fluid] ** 2))),
+            "Nu": Nu, "Nu_rel_err": abs(Nu - Nu_ref) / abs(Nu_ref)}
+    line = {"precision_study": f"heated sphere {nx}x{ny}x{nz}, D={D:g}, Pr={WORKLOAD['Pr']:g}, {steps} steps",
+            "reference": ref, "Nu_ref": Nu_ref, "Nu_window_steps": win, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -409,12 +489,18 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--precision", action="store_true",
+                    help="FP16/BF16/FP32 storage against FP64 (see precision_study)")
+    ap.add_argument("--precision-crop", action="store_true",
+                    help="with --precision: the 96x32x32 crop against the FP64 oracle")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end run and the storage variants")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.precision:
+        precision_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -55,7 +55,8 @@ typedef enum { LBM_D3Q27 = 27, LBM_D3Q7 = 7 } lbm_lattice;
 typedef enum { LBM_H_CM_TRT = 0, LBM_H_CM_SRT = 1, LBM_H_CM_1ST = 2 } lbm_hkind;
 
 /* Storage of populations in HBM.  Every type stores the shifted values
- * f - w*rho0 and h - w*T_ref; arithmetic is FP32 (FP64 for LBM_F64). */
+ * f - w*rho0 and h - w*T_ref; arithmetic is FP32 (FP64 for LBM_F64).  The
+ * 16-bit types round stochastically by default (lbm_params.round_nearest). */
 typedef enum { LBM_F32 = 0, LBM_F64 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_storage;
 
 typedef struct {
@@ -72,6 +73,9 @@ typedef struct {
                             cumulants (0 < omega_bulk < 2); 1 sets it to equilibrium */
     double rho0, T_ref;  /* shift references of the stored populations */
     void* cuda_stream;   /* cudaStream_t to run on; NULL = the library creates one */
+    int round_nearest;   /* 16-bit storage: 0 = stochastic rounding (unbiased, reproducible:
+                            random bits hashed from node, population and time level),
+                            1 = round to nearest even */
 } lbm_params;
 
 /* Create a context and allocate its device state.  The populations are zero

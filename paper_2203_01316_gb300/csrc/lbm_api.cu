@@ -293,6 +293,8 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     }
     d.rho0 = p.rho0;
     d.Tref = p.T_ref;
+    d.stochastic = p.round_nearest ? 0 : 1;
+    d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;
     lbm_status s = upload_inlet(c);
@@ -601,6 +603,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const
     Buffers b = buffers(c);
     b.fB = c->f[c->cur_f];  // write the current level in place
     b.hB = c->h[c->cur_h];
+    c->dp.step = 0;
     const DevParams p = c->dp;
     cudaStream_t s = c->stream;
     CK(dispatch(c, [&](auto tag) {
@@ -618,9 +621,10 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
     DeviceGuard g(c->device);
-    const DevParams p = c->dp;
     for (int i = 0; i < n; ++i) {
         const Buffers b = buffers(c);
+        c->dp.step += 1;
+        const DevParams p = c->dp;
         cudaError_t e = dispatch(c, [&](auto tag) {
             using Tg = decltype(tag);
             return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
@@ -750,6 +754,7 @@ struct StateHeader {
     uint32_t version;
     int32_t nx, ny, nz, qh, storage;
     uint64_t fbytes, hbytes;
+    uint64_t step;  // time level (random stream of the 16-bit stochastic rounding)
 };
 
 lbm_status lbm_state_size(lbm_ctx* c, size_t* bytes) {
@@ -769,7 +774,8 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t* bytes, int is_devi
     }
     StateHeader hd{};
     std::memcpy(hd.magic, "LBMSTATE", 8);
-    hd.version = 1;
+    hd.version = 2;
+    hd.step = c->dp.step;
     hd.nx = c->p.nx;
     hd.ny = c->p.ny;
     hd.nz = c->p.nz;
@@ -802,7 +808,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes, int is
     } else {
         std::memcpy(&hd, host_buf, sizeof(hd));
     }
-    if (std::memcmp(hd.magic, "LBMSTATE", 8) != 0 || hd.version != 1 || hd.nx != c->p.nx || hd.ny != c->p.ny ||
+    if (std::memcmp(hd.magic, "LBMSTATE", 8) != 0 || hd.version != 2 || hd.nx != c->p.nx || hd.ny != c->p.ny ||
         hd.nz != c->p.nz || hd.qh != c->qh || hd.storage != c->p.storage ||
         hd.fbytes != (uint64_t)27 * c->N * c->ssize || hd.hbytes != (uint64_t)c->qh * c->N * c->ssize ||
         bytes < sizeof(hd) + hd.fbytes + hd.hbytes)
@@ -812,6 +818,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes, int is
     CK(cudaMemcpyAsync(c->f[c->cur_f], in + sizeof(hd), hd.fbytes, kind, c->stream), "state load");
     CK(cudaMemcpyAsync(c->h[c->cur_h], in + sizeof(hd) + hd.fbytes, hd.hbytes, kind, c->stream), "state load");
     CK(cudaStreamSynchronize(c->stream), "state load");
+    c->dp.step = (uint32_t)hd.step;
     c->initialised = true;
     return LBM_OK;
 }
@@ -877,10 +884,11 @@ lbm_status lbm_step_record(lbm_ctx* c, int n, void* u_rec, int advance_h) {
     if (n > 0 && !u_rec) return fail(c, LBM_ERR_INVALID, "null velocity record");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
     DeviceGuard g(c->device);
-    const DevParams p = c->dp;
     const size_t rsize = c->p.storage == LBM_F64 ? sizeof(double) : sizeof(float);
     for (int i = 0; i < n; ++i) {
         Buffers b = buffers(c);
+        c->dp.step += 1;
+        const DevParams p = c->dp;
         b.urec = (char*)u_rec + (size_t)i * 3 * c->N * rsize;
         cudaError_t e = dispatch(c, [&](auto tag) {
             using Tg = decltype(tag);

@@ -77,6 +77,43 @@ __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
+// Stochastic rounding of the 16-bit stores: the value is rounded up in
+// magnitude with probability equal to the discarded fraction, so rounding
+// errors have zero mean and do not accumulate into a drift over many steps.
+// Implemented by adding a uniform random integer below the last kept bit to
+// the FP32 bit pattern and truncating (FP32 -> FP16 drops 13 mantissa bits,
+// -> BF16 drops 16).  FP16 subnormals, overflow and non-finite values use
+// round-to-nearest.
+__device__ __forceinline__ void st_sr(float* p, float v, uint32_t) { *p = v; }
+__device__ __forceinline__ void st_sr(double* p, double v, uint32_t) { *p = v; }
+__device__ __forceinline__ void st_sr(__half* p, float v, uint32_t r) {
+    const float a = fabsf(v);
+    if (!(a >= 6.103515625e-05f && a < 65504.0f)) {
+        *p = __float2half_rn(v);
+        return;
+    }
+    *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+}
+__device__ __forceinline__ void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
+    if (!isfinite(v)) {
+        *p = __float2bfloat16_rn(v);
+        return;
+    }
+    *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xFFFFu)));
+}
+
+// counter-based 32-bit hash (the "lowbias32" integer mixer of C. Wellons) of
+// (node, population slot, step): reproducible random bits for st_sr
+__device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t step) {
+    uint32_t x = key ^ (step * 0x9E3779B9u);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 // ---- moment algebra --------------------------------------------------------
 template <typename R> __device__ __forceinline__ constexpr R cs2() { return R(1) / R(3); }
 
@@ -165,6 +202,8 @@ template <typename R> __device__ __forceinline__ void inverse_cube(R* c, R vx, R
 // ---- parameters -------------------------------------------------------------
 struct DevParams {
     int nx, ny, nz, N, periodic_x;
+    int stochastic;      // 16-bit storage: 1 stochastic rounding, 0 round to nearest
+    uint32_t step;       // time level being written (random stream of st_sr)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6
     double rho0, Tref;

@@ -124,8 +124,13 @@ __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __res
     using R = typename Acc<S>::R;
     R rho;
     collide_f<R>(fd, p, ux, uy, uz, rho);
+    if (sizeof(S) == 2 && p.stochastic) {
 #pragma unroll
-    for (int a = 0; a < 27; ++a) st(fB + a * p.N + n, fd[a]);
+        for (int a = 0; a < 27; ++a) st_sr(fB + a * p.N + n, fd[a], sr_bits(((uint32_t)n << 6) | a, p.step));
+    } else {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) st(fB + a * p.N + n, fd[a]);
+    }
 }
 
 template <typename S, int QH>
@@ -135,8 +140,14 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
                                                 typename Acc<S>::R Q) {
     using R = typename Acc<S>::R;
     collide_h<R, QH>(hd, ux, uy, uz, Q, p);
+    if (sizeof(S) == 2 && p.stochastic) {
 #pragma unroll
-    for (int i = 0; i < QH; ++i) st(hB + i * p.N + n, hd[i]);
+        for (int i = 0; i < QH; ++i)
+            st_sr(hB + i * p.N + n, hd[i], sr_bits(((uint32_t)n << 6) | 32u | i, p.step));
+    } else {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) st(hB + i * p.N + n, hd[i]);
+    }
 }
 
 // ---- the step: pull streaming, Eq. IBB / Eq. IABB on wall links, planes,

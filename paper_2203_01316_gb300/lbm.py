@@ -45,7 +45,7 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lat_h", C.c_int), ("hkind", C.c_int),
                 ("storage", C.c_int), ("periodic_x", C.c_int), ("nu", C.c_double), ("k", C.c_double),
                 ("Pr", C.c_double), ("omega_bulk", C.c_double), ("rho0", C.c_double), ("T_ref", C.c_double),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int)]
 
 
 _lib = None
@@ -129,10 +129,11 @@ class Solver:
     number; lat_h: 27 or 7; hkind: 'trt' | 'srt' | '1st'; storage:
     'f32' | 'f64' | 'f16' | 'bf16'; periodic_x: True, or False for an
     inlet/outlet channel; stream: a torch.cuda.Stream or raw handle, or None
-    for a library-owned stream."""
+    for a library-owned stream; round_nearest: 16-bit storage rounds to
+    nearest instead of stochastically."""
 
     def __init__(self, nx, ny, nz, nu, k=0.0, Pr=0.0, lat_h=27, hkind="trt", storage="f32", periodic_x=True,
-                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None):
+                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False):
         self.L = lib()
         p = Params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -145,6 +146,7 @@ class Solver:
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
         p.cuda_stream = stream
+        p.round_nearest = 1 if round_nearest else 0
         self.params = p
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.N = p.nx * p.ny * p.nz

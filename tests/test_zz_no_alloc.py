@@ -23,9 +23,9 @@ REL_TOL = 1e-9  # the tolerance of the balance checks in the parity tests
 def _state_arrays(s):
     """The context's stored FP32 populations (deviation form) as host arrays."""
     blob = s.save_state()
-    magic, version, nx, ny, nz, qh, storage, fbytes, hbytes = struct.unpack_from("<8sI5iQQ", blob, 0)
+    magic, version, nx, ny, nz, qh, storage, fbytes, hbytes, step = struct.unpack_from("<8sI5iQQQ", blob, 0)
     assert magic == b"LBMSTATE" and storage == 0
-    off = struct.calcsize("<8sI5iQQ")
+    off = struct.calcsize("<8sI5iQQQ")
     f = np.frombuffer(blob, dtype=np.float32, count=fbytes // 4, offset=off)
     h = np.frombuffer(blob, dtype=np.float32, count=hbytes // 4, offset=off + fbytes)
     return f, h, qh
