@@ -383,6 +383,70 @@ def precision_study(args):
     print(json.dumps(line), flush=True)
 
 
+def porous_study(args):
+    """Porous bed: 512x256x256 (33.5M nodes), 200 spheres with D uniform in
+    [12, 24], IBB/IABB with T_w = 1, inlet u = 0.01, Pr = 1000, D3Q27
+    cumulant f + D3Q7 CM-TRT h, FP32 and FP16 storage.  MLUPS and roofline
+    fraction of the step; then `spin` forward steps and a 1000-step adjoint of
+    the heat flux through the plane x = nx-2 (summed over the last 100
+    levels) with respect to theta, checkpoints every 50 steps."""
+    import torch
+    from paper_2203_01316_gb300 import Solver, build, inputs as I
+    from paper_2203_01316_gb300.autograd import thermal_objective
+    build.build()
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    w = I.porous_bed(seed=WORKLOAD["seed"])
+    t_geom = time.perf_counter() - t0
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    n_active = int(np.count_nonzero(np.asarray(w["flags"]) != 1))
+    nu, Pr = 0.01, 1000.0
+    hbm, src = peaks()
+    out = {"workload": f"porous bed {nx}x{ny}x{nz}, {len(w['radii'])} spheres D in [12,24], D3Q27 f + "
+                       f"D3Q7 CM-TRT h, IBB/IABB, Pr={Pr:g}", "nodes": N, "solid_fraction": 1 - n_active / N,
+           "wall_links": int(len(w["links"]["node"])), "geometry_build_s": t_geom}
+    for storage in ("f32", "f16"):
+        s = Solver(nx, ny, nz, nu=nu, Pr=Pr, lat_h=7, hkind="trt", storage=storage, periodic_x=False,
+                   T_ref=0.5, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        s.set_geometry(w["flags"], w["links"], n_walls=1)
+        t_set = time.perf_counter() - t0
+        s.set_bc(0, 1.0)
+        s.set_inlet(w["u_in"], w["T_in"])
+        s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        dt = time_steps(s, args.steps, args.warmup, stream)
+        alg = n_active * 2 * (27 + 7) * BYTES_PER_VALUE[storage]
+        ach = alg / (dt / args.steps) / 1e9
+        r = {"MLUPS": N * args.steps / dt / 1e6, "ms_per_step": dt / args.steps * 1e3, "achieved_GBs": ach,
+             "frac": ach / hbm, "set_geometry_s": t_set}
+        if storage == "f32" and args.adjoint_steps > 0:
+            s.step(args.spin)
+            torch.cuda.synchronize()
+            state0 = s.save_state(torch.empty(s.state_size(), dtype=torch.uint8, device="cuda"))
+            theta = torch.zeros(N, dtype=torch.float64, device="cuda", requires_grad=True)
+            Tw = torch.tensor([1.0], dtype=torch.float64, requires_grad=True)
+            obj = s.objective("section", nx - 2, 1.0)
+            n = args.adjoint_steps
+            tf = time.perf_counter()
+            J = thermal_objective(theta, Tw, s, state0, n, (n - 99, n), obj, every=50)
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
+            J.backward()
+            torch.cuda.synchronize()
+            te = time.perf_counter()
+            free, total = torch.cuda.mem_get_info()
+            r["adjoint"] = {"steps": n, "checkpoint_every": 50, "spin_up_steps": args.spin,
+                            "objective": "heat flux through x = nx-2, last 100 levels",
+                            "forward_ms_per_step": (tb - tf) / n * 1e3, "backward_ms_per_step": (te - tb) / n * 1e3,
+                            "ratio": (te - tb) / n * 1e3 / r["ms_per_step"], "J": float(J.item()),
+                            "grad_theta_norm": float(theta.grad.norm()), "device_mem_used_GB": (total - free) / 1e9,
+                            "note": "first (cold) adjoint call: includes allocation of checkpoint buffers"}
+        out[storage] = r
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -489,6 +553,9 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--workload", choices=["sphere", "porous"], default="sphere",
+                    help="porous: the 512x256x256 porous bed (see porous_study)")
+    ap.add_argument("--spin", type=int, default=2000, help="porous: forward steps before the adjoint")
     ap.add_argument("--precision", action="store_true",
                     help="FP16/BF16/FP32 storage against FP64 (see precision_study)")
     ap.add_argument("--precision-crop", action="store_true",
@@ -500,6 +567,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.precision:
         precision_study(args)
+    elif args.workload == "porous":
+        porous_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -401,22 +401,40 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         }
         wmask.back() |= 1u << sd[i];
     }
-    // completeness: every fluid->solid link listed; outlet nodes see no solid
+    // completeness: every fluid->solid link listed; outlet nodes see no solid.
+    // Nested loops with per-row neighbour offsets (y, z periodic).
     std::vector<uint8_t> iflags(fl);
     size_t wi = 0;
-    for (int n = 0; n < N; ++n) {
-        if (fl[n] == lbmd::T_SOLID || fl[n] == lbmd::T_INLET) continue;
-        uint32_t m = 0;
-        for (int a = 1; a < 27; ++a) {
-            const int t = nbr(n, lbmd::EX(a), lbmd::EY(a), lbmd::EZ(a));
-            if (t >= 0 && fl[t] == lbmd::T_SOLID) m |= 1u << a;
+    const int64_t plane = (int64_t)nx * ny;
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            int64_t rowoff[27];  // index offset of the neighbour row of direction a
+            for (int a = 0; a < 27; ++a) {
+                const int yy = (y + lbmd::EY(a) + ny) % ny, zz = (z + lbmd::EZ(a) + nz) % nz;
+                rowoff[a] = (int64_t)zz * plane + (int64_t)yy * nx;
+            }
+            const int64_t row = (int64_t)z * plane + (int64_t)y * nx;
+            for (int x = 0; x < nx; ++x) {
+                const int n = (int)(row + x);
+                if (fl[n] == lbmd::T_SOLID || fl[n] == lbmd::T_INLET) continue;
+                uint32_t m = 0;
+                for (int a = 1; a < 27; ++a) {
+                    int xx = x + lbmd::EX(a);
+                    if (xx < 0 || xx >= nx) {
+                        if (!c->p.periodic_x) continue;
+                        xx = (xx + nx) % nx;
+                    }
+                    if (fl[rowoff[a] + xx] == lbmd::T_SOLID) m |= 1u << a;
+                }
+                if (!m) continue;
+                if (fl[n] == lbmd::T_OUTLET) return fail(c, LBM_ERR_INVALID, "outlet node next to a solid");
+                while (wi < wnode.size() && wnode[wi] < n) ++wi;
+                if (wi >= wnode.size() || wnode[wi] != n || wmask[wi] != m)
+                    return fail(c, LBM_ERR_INVALID,
+                                "fluid->solid links of node " + std::to_string(n) + " are not all listed");
+                iflags[n] |= lbmd::F_WALL;
+            }
         }
-        if (!m) continue;
-        if (fl[n] == lbmd::T_OUTLET) return fail(c, LBM_ERR_INVALID, "outlet node next to a solid");
-        while (wi < wnode.size() && wnode[wi] < n) ++wi;
-        if (wi >= wnode.size() || wnode[wi] != n || wmask[wi] != m)
-            return fail(c, LBM_ERR_INVALID, "fluid->solid links of node " + std::to_string(n) + " are not all listed");
-        iflags[n] |= lbmd::F_WALL;
     }
     // adjoint reverse table: node y = x - e_a of each link (x, a) with
     // q <= 1/2 whose y is fluid or outlet (Eq. IABB reads h*_a(y) there)
