@@ -76,7 +76,17 @@ typedef struct {
     int round_nearest;   /* 16-bit storage: 0 = stochastic rounding (unbiased, reproducible:
                             random bits hashed from node, population and time level),
                             1 = round to nearest even */
+    int step_kernel;     /* lbm_step_kernel: implementation of lbm_step (same results) */
 } lbm_params;
+
+/* LBM_STEP_AUTO and LBM_STEP_CLASSIC run the classic kernel, which loads
+ * each population directly (the faster one on GB300: the step is close to
+ * the SM issue limit, and the classic kernel keeps 20 warps per SM).
+ * LBM_STEP_STAGED (FP32/FP16/BF16 storage, nx a multiple of 32;
+ * LBM_ERR_INVALID otherwise) copies the rows of the pull into shared memory
+ * with asynchronous bulk copies three tiles ahead; it computes bit-identical
+ * results. */
+typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1, LBM_STEP_STAGED = 2 } lbm_step_kernel;
 
 /* Create a context and allocate its device state.  The populations are zero
  * until lbm_init_fields.  Errors: LBM_ERR_INVALID (parameters), NOMEM, CUDA. */

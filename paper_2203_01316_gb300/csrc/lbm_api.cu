@@ -22,8 +22,13 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    void* f[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};  // population arrays (inside guarded allocations)
     void* h[2] = {nullptr, nullptr};
+    void* f_alloc[2] = {nullptr, nullptr};
+    void* h_alloc[2] = {nullptr, nullptr};
+    int* d_err = nullptr;  // set by the staged step kernel when a pipeline wait times out
+    int num_sms = 1;
+    bool staged = false;   // step with k_step_staged
     int cur_f = 0, cur_h = 0;  // f[cur_f], h[cur_h]: post-collision state of the current level
     uint8_t* d_flags = nullptr;
     int nw = 0;
@@ -224,6 +229,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (p.lat_h != 27 && p.lat_h != 7) return fail(nullptr, LBM_ERR_INVALID, "lat_h must be 27 or 7");
     if (p.hkind < 0 || p.hkind > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown hkind");
     if (p.storage < 0 || p.storage > 3) return fail(nullptr, LBM_ERR_INVALID, "unknown storage");
+    if (p.step_kernel < 0 || p.step_kernel > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown step_kernel");
     if (!(p.nu > 0.0) || !std::isfinite(p.nu)) return fail(nullptr, LBM_ERR_INVALID, "nu must be > 0");
     double k = p.k, Pr = p.Pr;
     if (k > 0.0 && Pr > 0.0) {
@@ -260,12 +266,27 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "stream create"));
         c->own_stream = true;
     }
-    const size_t fb = (size_t)27 * N * c->ssize, hb = (size_t)c->qh * N * c->ssize;
+    // each population array has lbmd::kGuard elements of slack on both sides
+    // (the staged step copies whole rows including a few elements beyond them)
+    const size_t guard = (size_t)lbmd::kGuard * c->ssize;
+    const size_t fb = (size_t)27 * N * c->ssize + 2 * guard, hb = (size_t)c->qh * N * c->ssize + 2 * guard;
     for (int i = 0; i < 2; ++i) {
-        if (cudaMalloc(&c->f[i], fb) != cudaSuccess || cudaMalloc(&c->h[i], hb) != cudaSuccess)
+        if (cudaMalloc(&c->f_alloc[i], fb) != cudaSuccess || cudaMalloc(&c->h_alloc[i], hb) != cudaSuccess)
             return bail(fail(c, LBM_ERR_NOMEM, "population arrays: out of device memory"));
-        cudaMemsetAsync(c->f[i], 0, fb, c->stream);
-        cudaMemsetAsync(c->h[i], 0, hb, c->stream);
+        cudaMemsetAsync(c->f_alloc[i], 0, fb, c->stream);
+        cudaMemsetAsync(c->h_alloc[i], 0, hb, c->stream);
+        c->f[i] = (char*)c->f_alloc[i] + guard;
+        c->h[i] = (char*)c->h_alloc[i] + guard;
+    }
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
+        return bail(fail(c, LBM_ERR_NOMEM, "error flag: out of device memory"));
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    {
+        const bool eligible = p.storage != LBM_F64 && p.nx % 32 == 0;
+        if (p.step_kernel == LBM_STEP_STAGED && !eligible)
+            return bail(fail(c, LBM_ERR_INVALID, "the staged step needs 32/16-bit storage and nx % 32 == 0"));
+        c->staged = eligible && p.step_kernel == LBM_STEP_STAGED;
     }
     if (cudaMalloc(&c->d_flags, N) != cudaSuccess ||
         cudaMalloc(&c->d_inlet, (27 + 27) * sizeof(double)) != cudaSuccess ||
@@ -310,9 +331,10 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2; ++i) {
-        cudaFree(c->f[i]);
-        cudaFree(c->h[i]);
+        cudaFree(c->f_alloc[i]);
+        cudaFree(c->h_alloc[i]);
     }
+    cudaFree(c->d_err);
     free_geometry(c);
     cudaFree(c->d_flags);
     cudaFree(c->d_inlet);
@@ -595,6 +617,14 @@ lbm_status lbm_set_source(lbm_ctx* c, const float* theta, int is_device) {
     return LBM_OK;
 }
 
+// the staged step's pipeline-timeout flag (read after the stream is idle)
+static lbm_status check_pipeline(lbm_ctx* c) {
+    int e = 0;
+    CK(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (e) return fail(c, LBM_ERR_CUDA, "a staged step timed out waiting for its bulk copies");
+    return LBM_OK;
+}
+
 static lbm_status ensure_stage(lbm_ctx* c) {
     if (!c->d_stage && cudaMalloc(&c->d_stage, (size_t)5 * c->N * sizeof(double)) != cudaSuccess)
         return fail(c, LBM_ERR_NOMEM, "staging buffer: out of device memory");
@@ -643,10 +673,28 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
         const Buffers b = buffers(c);
         c->dp.step += 1;
         const DevParams p = c->dp;
-        cudaError_t e = dispatch(c, [&](auto tag) {
-            using Tg = decltype(tag);
-            return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
-        });
+        cudaError_t e;
+        if (c->staged) {
+            switch (c->p.storage) {
+                case LBM_F32:
+                    e = c->qh == 27 ? lbmd::launch_step_staged<float, 27>(b, p, c->d_err, c->num_sms, c->stream)
+                                    : lbmd::launch_step_staged<float, 7>(b, p, c->d_err, c->num_sms, c->stream);
+                    break;
+                case LBM_F16_SHIFTED:
+                    e = c->qh == 27 ? lbmd::launch_step_staged<__half, 27>(b, p, c->d_err, c->num_sms, c->stream)
+                                    : lbmd::launch_step_staged<__half, 7>(b, p, c->d_err, c->num_sms, c->stream);
+                    break;
+                default:
+                    e = c->qh == 27
+                            ? lbmd::launch_step_staged<__nv_bfloat16, 27>(b, p, c->d_err, c->num_sms, c->stream)
+                            : lbmd::launch_step_staged<__nv_bfloat16, 7>(b, p, c->d_err, c->num_sms, c->stream);
+            }
+        } else {
+            e = dispatch(c, [&](auto tag) {
+                using Tg = decltype(tag);
+                return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
+            });
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
         c->cur_f = 1 - c->cur_f;
         c->cur_h = 1 - c->cur_h;
@@ -733,6 +781,7 @@ lbm_status lbm_balances(lbm_ctx* c, double* mass, double* energy) {
     double r[3];
     CK(cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, c->stream), "balances copy");
     CK(cudaStreamSynchronize(c->stream), "balances");
+    if (check_pipeline(c) != LBM_OK) return LBM_ERR_CUDA;
     if (mass) *mass = r[0] + c->dp.rho0 * (double)c->n_fluid_like;
     if (energy) *energy = r[1] + c->dp.Tref * (double)c->n_fluid_like;
     if (r[2] != 0.0) return fail(c, LBM_ERR_DIVERGED, std::to_string((long long)r[2]) + " nodes hold non-finite populations");
@@ -994,7 +1043,7 @@ lbm_status lbm_sync(lbm_ctx* c) {
     DeviceGuard g(c->device);
     CK(cudaStreamSynchronize(c->stream), "sync");
     CK(cudaGetLastError(), "sync");
-    return LBM_OK;
+    return check_pipeline(c);
 }
 
 const char* lbm_last_error(lbm_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }

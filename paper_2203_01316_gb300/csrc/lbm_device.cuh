@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 namespace lbmd {
 
 // ---- D3Q27 velocity list of Sec. 2.1 ------------------------------------
@@ -71,6 +73,12 @@ template <typename R> __device__ __forceinline__ R ld(const float* p) { return (
 template <typename R> __device__ __forceinline__ R ld(const double* p) { return (R)__ldg(p); }
 template <typename R> __device__ __forceinline__ R ld(const __half* p) { return (R)__half2float(__ldg(p)); }
 template <typename R> __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return (R)__bfloat162float(__ldg(p)); }
+
+// a stored value as arithmetic type (shared-memory reads of staged rows)
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(double* p, double v) { *p = v; }

@@ -47,6 +47,22 @@ constexpr int kBlock = 128;
 constexpr int kRedBlocks = 1216;  // 8 x 152 SMs, partial sums of the reductions
 constexpr int kRedThreads = 256;
 
+// Staged variant of the step (FP32 / FP16 / BF16 storage, nx % 32 == 0, the
+// population arrays carrying kGuard elements of slack on both sides): rows
+// of the pull are copied into shared memory by asynchronous bulk copies.
+constexpr int kTile = 128;     // nodes (= threads) per tile, one x-row segment
+constexpr int kStages = 3;     // tiles in flight per CTA
+constexpr int kGuard = 256;    // elements of slack around each population array
+template <typename S> constexpr int stage_pad() { return 16 / (int)sizeof(S); }
+template <typename S, int QH> constexpr int stage_bytes() {
+    return (27 + QH) * (kTile + 2 * stage_pad<S>()) * (int)sizeof(S);
+}
+template <typename S, int QH>
+cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s);
+template <typename S, int QH> bool staged_eligible(const DevParams& p) {
+    return sizeof(S) <= 4 && p.nx % 32 == 0;
+}
+
 // advance_h = false advances f only (velocity recomputation for the adjoint);
 // b.urec non-null records the velocity u used by each node's collision
 template <typename S, int QH>
@@ -270,6 +286,235 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
     const R Q = theta ? (R)__ldg(theta + n) : R(0);
     collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
     }
+}
+
+// ---- staged step ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// bounded wait for the phase of parity `parity` to complete; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// issue the bulk copies of tile `tile` into stage buffer `buf` (thread 0 only)
+template <typename S, int QH>
+__device__ __forceinline__ void stage_issue(const S* __restrict__ fA, const S* __restrict__ hA, int tile,
+                                            int tiles_per_row, S* buf, uint32_t bar, const DevParams& p) {
+    constexpr int PAD = stage_pad<S>();
+    constexpr int ROW = kTile + 2 * PAD;
+    const int row = tile / tiles_per_row;
+    const int x0 = (tile - row * tiles_per_row) * kTile;
+    const int y = row % p.ny, z = row / p.ny;
+    mbar_expect_tx(bar, (uint32_t)stage_bytes<S, QH>());
+    const int ym = (y == 0) ? p.ny - 1 : y - 1, yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int zm = (z == 0) ? p.nz - 1 : z - 1, zp = (z == p.nz - 1) ? 0 : z + 1;
+    const int ys[3] = {yp, y, ym}, zs[3] = {zp, z, zm};  // source row of e = -1, 0, +1
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const S* src = fA + (size_t)a * p.N + ((size_t)zs[EZ(a) + 1] * p.ny + ys[EY(a) + 1]) * p.nx + x0 - PAD;
+        bulk_g2s(smem_addr(buf + a * ROW), src, ROW * sizeof(S), bar);
+    }
+#pragma unroll
+    for (int i = 0; i < QH; ++i) {
+        const int a = HDIR<QH>(i);
+        const S* src = hA + (size_t)i * p.N + ((size_t)zs[EZ(a) + 1] * p.ny + ys[EY(a) + 1]) * p.nx + x0 - PAD;
+        bulk_g2s(smem_addr(buf + (27 + i) * ROW), src, ROW * sizeof(S), bar);
+    }
+}
+
+template <typename S, int QH>
+__global__ void __launch_bounds__(kTile) k_step_staged(const S* __restrict__ fA, S* __restrict__ fB,
+                                                        const S* __restrict__ hA, S* __restrict__ hB,
+                                                        const uint8_t* __restrict__ flags,
+                                                        const float* __restrict__ theta,
+                                                        const typename Acc<S>::R* __restrict__ inlet,
+                                                        const int32_t* __restrict__ seg_base,
+                                                        const uint32_t* __restrict__ wmask,
+                                                        const int32_t* __restrict__ woff,
+                                                        const float* __restrict__ lq,
+                                                        const int32_t* __restrict__ lwall,
+                                                        const float* __restrict__ Twall, int* __restrict__ err,
+                                                        const DevParams p) {
+    using R = typename Acc<S>::R;
+    constexpr int PAD = stage_pad<S>();
+    constexpr int ROW = kTile + 2 * PAD;
+    constexpr int SELEMS = (27 + QH) * ROW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S* stage = reinterpret_cast<S*>(smem_raw);
+    __shared__ __align__(8) uint64_t bars[kStages];
+    const int N = p.N;
+    const int tiles_per_row = (p.nx + kTile - 1) / kTile;
+    const int ntiles = tiles_per_row * p.ny * p.nz;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: tiles of the first kStages-1 iterations
+    if (tid == 0) {
+        for (int s = 0; s < kStages - 1; ++s) {
+            const int t = blockIdx.x + s * gridDim.x;
+            if (t < ntiles) stage_issue<S, QH>(fA, hA, t, tiles_per_row, stage + s * SELEMS, smem_addr(&bars[s]), p);
+        }
+    }
+    for (int it = 0;; ++it) {
+        const int tile = blockIdx.x + it * gridDim.x;
+        if (tile >= ntiles) break;
+        const int sidx = it % kStages;
+        if (tid == 0) {
+            const int nxt = tile + (kStages - 1) * gridDim.x;
+            const int ns = (it + kStages - 1) % kStages;
+            if (nxt < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                stage_issue<S, QH>(fA, hA, nxt, tiles_per_row, stage + ns * SELEMS, smem_addr(&bars[ns]), p);
+            }
+        }
+        const bool ok = mbar_wait(smem_addr(&bars[sidx]), (uint32_t)((it / kStages) & 1));
+        if (__syncthreads_or(!ok)) {
+            // record the failure, give the copies of this stage one more
+            // bounded wait, and leave together
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(smem_addr(&bars[sidx]), (uint32_t)((it / kStages) & 1));
+            }
+            return;
+        }
+        const S* buf = stage + sidx * SELEMS;
+        const int row = tile / tiles_per_row;
+        const int x0 = (tile - row * tiles_per_row) * kTile;
+        const int x = x0 + tid;
+        const bool in_row = x < p.nx;
+        const int y = row % p.ny, z = row / p.ny;
+        const int n = row * p.nx + x;
+        const uint8_t fl = in_row ? flags[n] : (uint8_t)T_SOLID;
+        const bool is_wall = (fl & F_WALL) != 0;
+        const uint32_t ballot = __ballot_sync(0xffffffffu, is_wall);
+        const int type = fl & 3;
+        if (type == T_INLET) {
+#pragma unroll
+            for (int a = 0; a < 27; ++a) st(fB + a * N + n, inlet[a]);
+#pragma unroll
+            for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
+        } else if (type != T_SOLID) {
+            uint32_t mask = 0;
+            int off = 0;
+            if (is_wall) {
+                const int lane = tid & 31;
+                const int idx = __ldg(seg_base + (n >> 5)) + __popc(ballot & ((1u << lane) - 1u));
+                mask = __ldg(wmask + idx);
+                off = __ldg(woff + idx);
+            }
+            const Nbr nb = make_nbr(x, y, z, p);
+            // the lanes at the ends of a row take the wrapped / clamped source
+            // from global memory; everyone else reads the staged row
+            const bool lfix = (x == 0), rfix = (x == p.nx - 1);
+            R fd[27];
+#pragma unroll
+            for (int a = 0; a < 27; ++a) {
+                if ((EX(a) == 1 && lfix) || (EX(a) == -1 && rfix)) fd[a] = ld<R>(fA + a * N + src_of(nb, a));
+                else fd[a] = (R)to_acc(buf[a * ROW + PAD + tid - EX(a)]);
+            }
+            if (mask) {
+#pragma unroll
+                for (int b = 0; b < 27; ++b) {
+                    const int a = OPP(b);
+                    if (!(mask & (1u << a))) continue;
+                    const float q = __ldg(lq + off + __popc(mask & ((1u << a) - 1u)));
+                    const bool thin = (mask >> b) & 1u;
+                    const R fa_b = ld<R>(fA + a * N + n);
+                    if (q <= 0.5f && !thin) {
+                        fd[b] = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];
+                    } else {
+                        const R qq = (R)fmaxf(q, 0.5f);
+                        const R fb_b = ld<R>(fA + b * N + n);
+                        fd[b] = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
+                    }
+                }
+            }
+            R ux, uy, uz;
+            collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
+            R hd[QH];
+#pragma unroll
+            for (int i = 0; i < QH; ++i) {
+                const int a = HDIR<QH>(i);
+                if ((EX(a) == 1 && lfix) || (EX(a) == -1 && rfix)) hd[i] = ld<R>(hA + i * N + src_of(nb, a));
+                else hd[i] = (R)to_acc(buf[(27 + i) * ROW + PAD + tid - EX(a)]);
+            }
+            if (mask) {
+                const R Tref = (R)p.Tref;
+#pragma unroll
+                for (int ib = 0; ib < QH; ++ib) {
+                    const int b = HDIR<QH>(ib);
+                    const int ia = HOPP<QH>(ib);
+                    const int a = HDIR<QH>(ia);
+                    if (!(mask & (1u << a))) continue;
+                    const int l = off + __popc(mask & ((1u << a) - 1u));
+                    const float q = __ldg(lq + l);
+                    const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref);
+                    const bool thin = (mask >> b) & 1u;
+                    const R ha_b = ld<R>(hA + ia * N + n);
+                    if (q <= 0.5f && !thin) {
+                        hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
+                    } else {
+                        const R qq = (R)fmaxf(q, 0.5f);
+                        const R hb_b = ld<R>(hA + ib * N + n);
+                        hd[ib] = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+                    }
+                }
+            }
+            const R Q = theta ? (R)__ldg(theta + n) : R(0);
+            collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+        }
+        __syncthreads();  // stage sidx is refilled at the next iteration
+    }
+}
+
+template <typename S, int QH>
+cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
+    using R = typename Acc<S>::R;
+    const size_t smem = (size_t)kStages * stage_bytes<S, QH>();
+    static unsigned long long configured = 0;  // per device: dynamic shared memory limit raised
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !(configured & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_staged<S, QH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured |= 1ull << dev;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<S, QH>, kTile, smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((p.nx + kTile - 1) / kTile) * p.ny * p.nz;
+    const int grid = std::max(1, std::min(tiles, num_sms * std::max(per_sm, 1)));
+    k_step_staged<S, QH><<<grid, kTile, smem, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags,
+                                                   b.theta, (const R*)b.inlet_post, b.seg_base, b.wmask, b.woff,
+                                                   b.lq, b.lwall, b.Twall, err, p);
+    return cudaGetLastError();
 }
 
 template <typename S, int QH>

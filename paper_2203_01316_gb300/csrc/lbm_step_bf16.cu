@@ -19,4 +19,6 @@ namespace lbmd {
                                                      cudaStream_t);
 LBM_INST(27)
 LBM_INST(7)
+template cudaError_t launch_step_staged<__nv_bfloat16, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
+template cudaError_t launch_step_staged<__nv_bfloat16, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 }  // namespace lbmd

@@ -19,6 +19,8 @@ namespace lbmd {
                                                      cudaStream_t);
 LBM_INST(27)
 LBM_INST(7)
+template cudaError_t launch_step_staged<float, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
+template cudaError_t launch_step_staged<float, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&, const float*, const float*, float*,
                                             AdjObjective, double*, cudaStream_t);
 template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*, float*,

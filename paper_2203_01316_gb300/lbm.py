@@ -45,7 +45,8 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lat_h", C.c_int), ("hkind", C.c_int),
                 ("storage", C.c_int), ("periodic_x", C.c_int), ("nu", C.c_double), ("k", C.c_double),
                 ("Pr", C.c_double), ("omega_bulk", C.c_double), ("rho0", C.c_double), ("T_ref", C.c_double),
-                ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int), ("step_kernel", C.c_int)]
+STEP_KERNEL = {"auto": 0, "classic": 1, "staged": 2}
 
 
 _lib = None
@@ -130,10 +131,11 @@ class Solver:
     'f32' | 'f64' | 'f16' | 'bf16'; periodic_x: True, or False for an
     inlet/outlet channel; stream: a torch.cuda.Stream or raw handle, or None
     for a library-owned stream; round_nearest: 16-bit storage rounds to
-    nearest instead of stochastically."""
+    nearest instead of stochastically; step_kernel: 'auto' | 'classic' |
+    'staged' (implementation of the step, same results)."""
 
     def __init__(self, nx, ny, nz, nu, k=0.0, Pr=0.0, lat_h=27, hkind="trt", storage="f32", periodic_x=True,
-                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False):
+                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False, step_kernel="auto"):
         self.L = lib()
         p = Params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -147,6 +149,7 @@ class Solver:
             stream = stream.cuda_stream
         p.cuda_stream = stream
         p.round_nearest = 1 if round_nearest else 0
+        p.step_kernel = STEP_KERNEL[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
         self.params = p
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.N = p.nx * p.ny * p.nz
