@@ -23,7 +23,8 @@
  *     truncated to degree <= 2 per axis (closed on the 27 indices, so exact);
  *   - the f collision is Eq. (hydro_cu_collision), the h collision
  *     Eq. (H_cm_collision) with the CM-SRT / CM-1st / CM-TRT rate sets of
- *     Sec. 2.1.1, the source term per Appendix D;
+ *     Sec. 2.1.1, or Eq. (H_cu_collision) with the Cumulants-1st rates, the
+ *     source term per Appendix D;
  *   - streaming is the push form of the evolution equation of Sec. 2.1,
  *     followed by Eq. (IBB) and Eq. (IABB) on every wall link.
  *
@@ -51,6 +52,9 @@
  *      D3Q27 list), moments {000,100,010,001,200,020,002}, cs^2 = 1/3.
  *   R8 surface heat flux of one wall: sum over its IABB links of
  *      h_abar(x_b, t+1) - h*_a(x_b, t).
+ *   R15 first-order walls (Sec. 3): BB = Eq. IBB at q = 1/2, ABB = Eq. IABB
+ *      at q = 1/2, EQ: the population arriving from the wall is the wall
+ *      equilibrium w_i T_w.
  *
  * Parity unpinned: none of the functions below lacks a pin; the cumulant
  * relaxation beyond second order is pinned only through R1's default rates.
@@ -313,9 +317,10 @@ typedef struct {
     double omega_bulk, omega3, omega4, omega5, omega6;
     double F[3];
     double u_in[3], T_in;
+    int wall_bc;     /* 0 Eq. IBB + Eq. IABB; 1 BB + EQ (first order); 2 BB + ABB */
 } orc_params;
 
-enum { KIND_TRT = 0, KIND_SRT = 1, KIND_1ST = 2 };
+enum { KIND_TRT = 0, KIND_SRT = 1, KIND_1ST = 2, KIND_CUM1 = 3 };
 
 /* Eq. (hydro_cu_collision) with reading R1 (rates) and R2 (force).  Writes
  * the post-collision populations and the velocity u that shifts h. */
@@ -359,9 +364,53 @@ static double rate_h(int kind, int order, double sH) {
     }
 }
 
+/* Eq. (H_cu_collision) with Appendix D's source, Cumulants-1st rates
+ * (Sec. 2.1.1): first-order cumulants relax with s^H toward u, every higher
+ * order is set to its equilibrium (c_s^2 on the diagonal of the second order,
+ * zero otherwise), C^Q = [Q, 0, ...].  The cumulants are those of the stored
+ * (shifted) h, normalised by its zeroth moment, which must be positive. */
+static void collide_h_cumulant(const orc_params* p, const double* h, const double u[3], double Q, double* hs) {
+    const double sH = 1.0 / (p->k / CS2 + 0.5);
+    if (p->qh == 27) {
+        const lattice_t* L = lattice(27);
+        double C[27], Cs[27];
+        cumulants(h, C);
+        const double H = C[0] + 0.5 * Q;
+        for (int r = 0; r < 27; ++r) {
+            const int* m = L->mom[r];
+            const int order = m[0] + m[1] + m[2];
+            double eq, s;
+            if (order == 0) { eq = H; s = 1.0; }
+            else if (order == 1) { eq = u[m[1] ? 1 : (m[2] ? 2 : 0)]; s = sH; }
+            else { eq = (order == 2 && (m[0] == 2 || m[1] == 2 || m[2] == 2)) ? CS2 : 0.0; s = 1.0; }
+            Cs[r] = C[r] + s * (eq - C[r]) + ((r == 0) ? (1.0 - 0.5 * s) * Q : 0.0);
+        }
+        cumulants_inverse(Cs, hs);
+        return;
+    }
+    /* D3Q7 (reading R7): the seven moments carry the mean and the per-axis
+     * variance; the post-collision distribution has mean v and variance cs^2 */
+    const lattice_t* L = lattice(7);
+    double Ht = 0.0, mean[3] = {0, 0, 0};
+    for (int a = 0; a < 7; ++a) {
+        Ht += h[a];
+        for (int d = 0; d < 3; ++d) mean[d] += L->e[a][d] * h[a];
+    }
+    double v[3];
+    for (int d = 0; d < 3; ++d) {
+        mean[d] /= Ht;
+        v[d] = mean[d] + sH * (u[d] - mean[d]);
+    }
+    equilibrium(L, Ht + Q, v, hs);
+}
+
 /* Eq. (H_cm_collision) with the Appendix D source (reading R3).  h holds the
  * shifted variable h - q/2; Q is the source (zeroth moment) of this node. */
 static void collide_h(const orc_params* p, const double* h, const double u[3], double Q, double* hs) {
+    if (p->hkind == KIND_CUM1) {
+        collide_h_cumulant(p, h, u, Q, hs);
+        return;
+    }
     const lattice_t* L = lattice(p->qh);
     const int n = L->Q;
     const double sH = 1.0 / (p->k / CS2 + 0.5);
@@ -591,6 +640,11 @@ void orc_get_post(const orc_sim* s, double* fs, double* hs) {
     memcpy(hs, s->hs, (size_t)s->p.qh * s->N * sizeof(double));
 }
 
+/* q used by the wall formulas: the first-order variants ignore the wall
+ * position and bounce back half-way (BB = Eq. IBB at q = 1/2, ABB = Eq. IABB
+ * at q = 1/2; Sec. 3) */
+static double q_eff(const orc_sim* s, float q) { return s->p.wall_bc ? 0.5 : (double)q; }
+
 /* Eq. (IBB) for one link: the population arriving at x_b in direction abar.
  * fa_b = f*_a(x_b), fab_b = f*_abar(x_b), fa_f = f*_a(x_f), thin = x_f not
  * usable (reading R5). */
@@ -641,15 +695,17 @@ int orc_stream(orc_sim* s) {
             int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
             double fa_f = thin ? 0.0 : s->fs[(size_t)a * N + xf];
             s->fn[(size_t)ab * N + n] =
-                ibb(q, s->fs[(size_t)a * N + n], s->fs[(size_t)ab * N + n], fa_f, thin);
+                ibb(q_eff(s, q), s->fs[(size_t)a * N + n], s->fs[(size_t)ab * N + n], fa_f, thin);
             /* the same link for h, when the direction belongs to h's lattice */
             for (int i = 0; i < qh; ++i) {
                 if (Lh->dir27[i] != a) continue;
                 int ib = Lh->opp[i];
                 double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
                 double heq = Lh->w[i] * s->Twall[s->wtab[(size_t)n * 27 + a]];
-                s->hn[(size_t)ib * N + n] = iabb(q, s->hs[(size_t)i * N + n],
-                                                 s->hs[(size_t)ib * N + n], ha_f, thin, heq);
+                s->hn[(size_t)ib * N + n] =
+                    (s->p.wall_bc == 1) ? heq /* EQ: the wall equilibrium itself */
+                                        : iabb(q_eff(s, q), s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n],
+                                               ha_f, thin, heq);
             }
         }
     }
@@ -768,7 +824,9 @@ double orc_surface_flux(orc_sim* s, int wall) {
             int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
             double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
             double heq = Lh->w[i] * s->Twall[wall];
-            double hin = iabb(q, s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n], ha_f, thin, heq);
+            double hin = (s->p.wall_bc == 1)
+                             ? heq
+                             : iabb(q_eff(s, q), s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n], ha_f, thin, heq);
             flux += hin - s->hs[(size_t)i * N + n];
         }
     }
@@ -816,8 +874,15 @@ int orc_num_threads(void) {
  * dJ/dtheta += e(u^k)^T lambda^k, dJ/dT_w += (dg^{k+1}/dT_w)^T mu^{k+1}.
  * The state s^0 is the given initial condition. */
 
-/* partial derivatives of one Eq. IABB arrival with respect to its inputs */
-static void iabb_partials(double q, int thin, double* d_ab, double* d_abb, double* d_af, double* d_T) {
+/* partial derivatives of one Eq. IABB arrival with respect to its inputs
+ * (EQ, wall_bc 1: the arrival is w_i T_w, only d_T = 1) */
+static void iabb_partials(const orc_sim* s, float qf, int thin, double* d_ab, double* d_abb, double* d_af,
+                          double* d_T) {
+    if (s->p.wall_bc == 1) {
+        *d_ab = 0.0; *d_abb = 0.0; *d_af = 0.0; *d_T = 1.0;
+        return;
+    }
+    const double q = q_eff(s, qf);
     if (q <= 0.5 && !thin) {
         *d_ab = -2.0 * q; *d_af = -(1.0 - 2.0 * q); *d_abb = 0.0; *d_T = 2.0;
     } else {
@@ -851,7 +916,7 @@ static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, 
             int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
             int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
             double d_ab, d_abb, d_af, d_T;
-            iabb_partials(q, thin, &d_ab, &d_abb, &d_af, &d_T);
+            iabb_partials(s, q, thin, &d_ab, &d_abb, &d_af, &d_T);
             double m = mu[(size_t)ib * N + n];
             lam[(size_t)i * N + n] += d_ab * m;
             lam[(size_t)ib * N + n] += d_abb * m;
@@ -895,7 +960,7 @@ static void objective_gradient(const orc_sim* s, int kind, int wall, int plane, 
             int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
             int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
             double d_ab, d_abb, d_af, d_T;
-            iabb_partials(q, thin, &d_ab, &d_abb, &d_af, &d_T);
+            iabb_partials(s, q, thin, &d_ab, &d_abb, &d_af, &d_T);
             lam[(size_t)i * N + n] += weight * (d_ab - 1.0);
             lam[(size_t)ib * N + n] += weight * d_abb;
             if (!thin) lam[(size_t)i * N + xf] += weight * d_af;
@@ -928,8 +993,9 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
             int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
             int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
             double ha_f = thin ? 0.0 : s->hs[(size_t)i * N + xf];
-            double hin = iabb(q, s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n], ha_f, thin,
-                              Lh->w[i] * s->Twall[wall]);
+            double hin = (s->p.wall_bc == 1) ? Lh->w[i] * s->Twall[wall]
+                                             : iabb(q_eff(s, q), s->hs[(size_t)i * N + n], s->hs[(size_t)ib * N + n],
+                                                    ha_f, thin, Lh->w[i] * s->Twall[wall]);
             F += hin - s->hs[(size_t)i * N + n];
         }
     }
@@ -939,11 +1005,13 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
 /* Forward run from the post-collision state (f_post, h_post) = s^0 over
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
- * dJ/dT_w[nwalls] to them.  Returns 0, or -1 on a streaming error. */
+ * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, -2 for the
+ * cumulant kind (its h step is not affine, so this sweep does not apply). */
 int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
                 int wall, int plane, double weight, double* J, double* dtheta, double* dTw) {
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
+    if (dtheta && s->p.hkind == KIND_CUM1) return -2; /* not affine in h: no linear adjoint here */
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
     orc_set_post(s, f_post, h_post);
     double Jv = 0.0;

@@ -21,7 +21,7 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lib = None
 
-KINDS = {"trt": 0, "srt": 1, "1st": 2}
+KINDS = {"trt": 0, "srt": 1, "1st": 2, "cum1st": 3}
 
 
 def build(force: bool = False) -> str:
@@ -44,12 +44,14 @@ class Params(C.Structure):
                 ("nu", C.c_double), ("k", C.c_double),
                 ("omega_bulk", C.c_double), ("omega3", C.c_double), ("omega4", C.c_double),
                 ("omega5", C.c_double), ("omega6", C.c_double),
-                ("F", C.c_double * 3), ("u_in", C.c_double * 3), ("T_in", C.c_double)]
+                ("F", C.c_double * 3), ("u_in", C.c_double * 3), ("T_in", C.c_double), ("wall_bc", C.c_int)]
+
+WALL_BC = {"iabb": 0, "eq": 1, "abb": 2}
 
 
 def make_params(nx=1, ny=1, nz=1, qh=27, hkind="trt", periodic_x=True, nu=0.02, k=2e-4,
                 omega_bulk=1.0, omega3=1.0, omega4=1.0, omega5=1.0, omega6=1.0,
-                F=(0.0, 0.0, 0.0), u_in=(0.0, 0.0, 0.0), T_in=0.0) -> Params:
+                F=(0.0, 0.0, 0.0), u_in=(0.0, 0.0, 0.0), T_in=0.0, wall_bc="iabb") -> Params:
     p = Params()
     p.nx, p.ny, p.nz, p.qh = nx, ny, nz, qh
     p.hkind = KINDS[hkind] if isinstance(hkind, str) else int(hkind)
@@ -60,6 +62,7 @@ def make_params(nx=1, ny=1, nz=1, qh=27, hkind="trt", periodic_x=True, nu=0.02, 
         p.F[d] = F[d]
         p.u_in[d] = u_in[d]
     p.T_in = T_in
+    p.wall_bc = WALL_BC[wall_bc] if isinstance(wall_bc, str) else int(wall_bc)
     return p
 
 
@@ -286,5 +289,6 @@ class Oracle:
                                int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
                                dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
         if rc != 0:
-            raise OracleError("orc_adjoint: streaming error")
+            raise OracleError("orc_adjoint: " + ("the cumulant kind has no linear adjoint" if rc == -2
+                                                 else "streaming error"))
         return J.value, dth, dTw

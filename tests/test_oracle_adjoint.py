@@ -12,12 +12,12 @@ from oracle import oracle as O
 from paper_2203_01316_gb300 import inputs as I
 
 
-def _plate_case(qh=27, kind="trt", qb=0.3, qt=0.7, seed=5):
+def _plate_case(qh=27, kind="trt", qb=0.3, qt=0.7, seed=5, wall_bc="iabb"):
     w = I.plate_channel(nx=6, ny=9, nz=4, q_bottom=qb, q_top=qt, theta_max=1e-3, seed=seed)
     N = len(w["rho"])
     w["u"] = I.uniform(seed + 1, 3 * N, -0.03, 0.03).reshape(3, N)
     w["T"] = I.uniform(seed + 2, N, 0.2, 1.0)
-    p = O.make_params(nx=6, ny=9, nz=4, qh=qh, hkind=kind, nu=0.05, k=0.01, F=(2e-4, 0.0, 1e-4))
+    p = O.make_params(nx=6, ny=9, nz=4, qh=qh, hkind=kind, nu=0.05, k=0.01, F=(2e-4, 0.0, 1e-4), wall_bc=wall_bc)
     return w, p
 
 
@@ -52,10 +52,11 @@ def _J(w, p, Tw, theta, fpost, hpost, nsteps, window, obj):
     return J
 
 
-@pytest.mark.parametrize("qh,kind", [(27, "trt"), (27, "srt"), (27, "1st"), (7, "trt")])
+@pytest.mark.parametrize("qh,kind,wall_bc", [(27, "trt", "iabb"), (27, "srt", "iabb"), (27, "1st", "iabb"),
+                                             (7, "trt", "iabb"), (27, "trt", "eq"), (27, "trt", "abb")])
 @pytest.mark.parametrize("obj", [("surface", 1, 0.7), ("section", 3, 1.3)])
-def test_plate_adjoint_matches_finite_differences(qh, kind, obj):
-    w, p = _plate_case(qh, kind)
+def test_plate_adjoint_matches_finite_differences(qh, kind, wall_bc, obj):
+    w, p = _plate_case(qh, kind, wall_bc=wall_bc)
     Tw = [1.0, 0.1]
     o, fpost, hpost = _setup(w, p, Tw)
     nsteps, window = 10, (4, 10)
@@ -99,6 +100,15 @@ def test_channel_adjoint_directional_derivative(qh):
               _J(w, p, Tw, theta - eps * v, fpost, hpost, nsteps, window, obj)) / (2 * eps)
         assert abs(dth @ v - fd) <= 1e-8 * max(abs(fd), 1e-6)
         assert np.all(dth[w["flags"] == I.INLET] == 0.0)
+
+
+def test_cumulant_kind_has_no_linear_adjoint():
+    w, p = _plate_case()
+    p.hkind = O.KINDS["cum1st"]
+    w["T"][:] = 0.6
+    o, fpost, hpost = _setup(w, p, [1.0, 0.1])
+    with pytest.raises(O.OracleError):
+        o.adjoint(fpost, hpost, 3, (0, 3), ("surface", 0, 1.0), nwalls=2)
 
 
 def test_objective_value_matches_surface_flux():

@@ -138,3 +138,41 @@ def test_f_second_order_cumulant_relaxation():
     wn = {3: 0.5, 4: 0.25, 5: 0.0, 6: 0.9}
     for r in range(10, 27):
         assert abs(Cs2[r] - (1 - wn[order[r]]) * C[r]) < 1e-14
+
+
+# ---- Cumulants-1st (Eq. H_cu_collision) ------------------------------------
+def _w1(c, u):
+    return 1.0 - u * u - CS2 if c == 0 else 0.5 * (u * u + c * u + CS2)
+
+
+@pytest.mark.parametrize("Q", [0.0, 2e-3])
+def test_cumulant_h_collision_is_maxwellian_at_relaxed_mean(Q):
+    # with every order >= 2 at equilibrium the post-collision cumulants are
+    # (H + Q/2, v, cs^2 I, 0, ...), v = (1 - s) mean + s u: the product-form
+    # discrete Maxwellian at velocity v (closed form)
+    rng = np.random.default_rng(30)
+    e = O.lattice(27)[0]
+    k = 2e-3
+    s = 1.0 / (3 * k + 0.5)
+    p = O.make_params(hkind="cum1st", k=k)
+    for _ in range(3):
+        u = rng.uniform(-0.1, 0.1, 3)
+        h = _perturbed(27, 1.3, rng.uniform(-0.1, 0.1, 3), rng, scale=0.3)
+        mean = (e.T @ h) / h.sum()
+        v = (1 - s) * mean + s * u
+        Hs = h.sum() + Q
+        closed = np.array([Hs * _w1(a, v[0]) * _w1(b, v[1]) * _w1(c, v[2]) for a, b, c in e])
+        assert np.allclose(O.collide_h(p, h, u, Q=Q), closed, atol=1e-14)
+
+
+def test_cumulant_h_collision_d3q7_and_equilibrium_fixed_point():
+    rng = np.random.default_rng(31)
+    p = O.make_params(qh=7, hkind="cum1st", k=1e-3)
+    u = rng.uniform(-0.1, 0.1, 3)
+    heq = O.equilibrium(0.8, u, Q=7)
+    assert np.allclose(O.collide_h(p, heq, u), heq, atol=1e-15)
+    h = _perturbed(7, 0.8, u, rng)
+    hs = O.collide_h(p, h, u, Q=1e-3)
+    assert abs(hs.sum() - (h.sum() + 1e-3)) < 1e-14
+    heq27 = O.equilibrium(0.8, u)
+    assert np.allclose(O.collide_h(O.make_params(hkind="cum1st", k=1e-3), heq27, u), heq27, atol=1e-15)

@@ -146,7 +146,7 @@ def test_shear_wave_decay_rate():
     assert abs(rate / (nu * kx * kx) - 1.0) < 0.01
 
 
-@pytest.mark.parametrize("kind", ["trt", "srt"])
+@pytest.mark.parametrize("kind", ["trt", "srt", "cum1st"])
 def test_temperature_mode_advection_diffusion(kind):
     # T = 1 + a sin(k (x - U t)) exp(-kappa k^2 t) for uniform u = (U, 0, 0)
     L, a, U, kappa = 32, 0.01, 0.05, 0.02
@@ -254,3 +254,76 @@ def test_geometry_validation():
     with pytest.raises(O.OracleError):
         o.set_geometry(flags, links, nwalls=1)  # wall id 1 out of range
     o.set_geometry(flags, links, nwalls=2)
+
+
+# ---- first-order wall variants (Sec. 3): BB + EQ, BB + ABB ---------------
+@pytest.mark.parametrize("mode", ["eq", "abb"])
+def test_first_order_wall_formulas(mode):
+    ny = 6
+    flags, links = _plate(ny, 0.3, 0.8)
+    o = _sim(1, ny, 1, flags, links, nwalls=2, wall_bc=mode)
+    Tw = (0.9, 0.2)
+    for w in (0, 1):
+        o.set_wall_temperature(w, Tw[w])
+    rng = np.random.default_rng(40)
+    fs = rng.uniform(0.1, 1.0, (27, ny))
+    hs = rng.uniform(0.1, 1.0, (27, ny))
+    o.set_post(fs, hs)
+    assert o.stream() == 0
+    f, h = o.state()
+    e, w, opp, _ = O.lattice(27)
+    for n, a, wall in zip(links["node"], links["dir"], links["wall"]):
+        ab = opp[a]
+        assert f[ab, n] == fs[a, n]                                      # BB
+        if mode == "eq":
+            assert abs(h[ab, n] - w[a] * Tw[wall]) < 1e-16                # EQ: wall equilibrium
+        else:
+            assert abs(h[ab, n] - (-hs[a, n] + 2 * w[a] * Tw[wall])) < 1e-15  # ABB
+
+
+@pytest.mark.parametrize("mode", ["eq", "abb"])
+def test_first_order_walls_keep_uniform_state(mode):
+    ny = 7
+    flags, links = _plate(ny, 0.3, 0.8, nx=2, nz=2)
+    o = _sim(2, ny, 2, flags, links, nwalls=2, k=1e-3, wall_bc=mode)
+    for w in (0, 1):
+        o.set_wall_temperature(w, 0.7)
+    N = 4 * ny
+    o.init_fields(np.ones(N), np.zeros((3, N)), np.full(N, 0.7))
+    f0, h0 = o.state()
+    o.step(20)
+    f1, h1 = o.state()
+    fl = flags != I.SOLID
+    assert np.allclose(f1[:, fl], f0[:, fl], atol=1e-15) and np.allclose(h1[:, fl], h0[:, fl], atol=1e-15)
+
+
+def test_abb_slab_puts_the_walls_half_way():
+    # ABB ignores q: the steady conduction profile is linear between the
+    # half-way points y = 0.5 and y = ny - 1.5 whatever q says (first order)
+    ny, kappa = 12, 0.1
+    flags, links = _plate(ny, 0.3, 0.8)
+    o = _sim(1, ny, 1, flags, links, nwalls=2, k=kappa, wall_bc="abb")
+    o.set_wall_temperature(0, 1.0)
+    o.set_wall_temperature(1, 0.0)
+    o.init_fields(np.ones(ny), np.zeros((3, ny)), np.full(ny, 0.5))
+    o.step(4000)
+    _, _, T = o.macros()
+    y = np.arange(ny, dtype=float)
+    Texp = 1.0 - (y - 0.5) / (ny - 2)
+    fl = flags == I.FLUID
+    assert np.abs(T[fl] - Texp[fl]).max() < 1e-6
+    assert abs(o.surface_flux(0) * (ny - 2) / kappa - 1.0) < 1e-5
+
+
+def test_eq_slab_is_linear_and_conserves_the_flux():
+    ny, kappa = 12, 0.1
+    flags, links = _plate(ny, 0.3, 0.8)
+    o = _sim(1, ny, 1, flags, links, nwalls=2, k=kappa, wall_bc="eq")
+    o.set_wall_temperature(0, 1.0)
+    o.set_wall_temperature(1, 0.0)
+    o.init_fields(np.ones(ny), np.zeros((3, ny)), np.full(ny, 0.5))
+    o.step(6000)
+    _, _, T = o.macros()
+    Ti = T[2:ny - 2]
+    assert np.abs(np.diff(Ti, 2)).max() < 1e-9
+    assert abs(o.surface_flux(0) + o.surface_flux(1)) < 1e-9
