@@ -49,10 +49,13 @@ typedef enum {
 
 typedef enum { LBM_D3Q27 = 27, LBM_D3Q7 = 7 } lbm_lattice;
 
-/* Sec. 2.1.1: rates of the h central moments (s^H = 1/(3k + 1/2)).
- * TRT: odd orders s^H, even orders 1.  SRT: all s^H.  1ST: order 1 s^H,
- * higher orders 1. */
-typedef enum { LBM_H_CM_TRT = 0, LBM_H_CM_SRT = 1, LBM_H_CM_1ST = 2 } lbm_hkind;
+/* Sec. 2.1.1: rates of the h collision (s^H = 1/(3k + 1/2)).  Central-moment
+ * kinds (Eq. H_cm_collision): TRT: odd orders s^H, even orders 1.  SRT: all
+ * s^H.  1ST: order 1 s^H, higher orders 1.  CUM_1ST (Eq. H_cu_collision,
+ * "Cumulants-1st"): first-order cumulants s^H, higher orders set to their
+ * equilibrium; needs a positive zeroth moment sum(h) everywhere, and has no
+ * adjoint here (its step is not affine in h). */
+typedef enum { LBM_H_CM_TRT = 0, LBM_H_CM_SRT = 1, LBM_H_CM_1ST = 2, LBM_H_CUM_1ST = 3 } lbm_hkind;
 
 /* Storage of populations in HBM.  Every type stores the shifted values
  * f - w*rho0 and h - w*T_ref; arithmetic is FP32 (FP64 for LBM_F64).  The
@@ -77,7 +80,15 @@ typedef struct {
                             random bits hashed from node, population and time level),
                             1 = round to nearest even */
     int step_kernel;     /* lbm_step_kernel: implementation of lbm_step (same results) */
+    int wall_bc;         /* lbm_wall_bc: wall rules */
 } lbm_params;
+
+/* Wall rules (Sec. 3).  IBB_IABB: Eq. IBB for f, Eq. IABB for h, with each
+ * link's q (second order).  BB_EQ: bounce-back for f (Eq. IBB at q = 1/2) and
+ * EQ for h: the population arriving from the wall is the wall equilibrium
+ * w_i T_w (first order).  BB_ABB: bounce-back and anti-bounce-back (Eq. IABB
+ * at q = 1/2). */
+typedef enum { LBM_WALL_IBB_IABB = 0, LBM_WALL_BB_EQ = 1, LBM_WALL_BB_ABB = 2 } lbm_wall_bc;
 
 /* LBM_STEP_AUTO and LBM_STEP_CLASSIC run the classic kernel, which loads
  * each population directly (the faster one on GB300: the step is close to

@@ -227,9 +227,10 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (N * 27 >= (int64_t(1) << 31)) return fail(nullptr, LBM_ERR_INVALID, "nx*ny*nz*27 must stay below 2^31");
     if (!p.periodic_x && p.nx < 4) return fail(nullptr, LBM_ERR_INVALID, "an inlet/outlet channel needs nx >= 4");
     if (p.lat_h != 27 && p.lat_h != 7) return fail(nullptr, LBM_ERR_INVALID, "lat_h must be 27 or 7");
-    if (p.hkind < 0 || p.hkind > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown hkind");
+    if (p.hkind < 0 || p.hkind > 3) return fail(nullptr, LBM_ERR_INVALID, "unknown hkind");
     if (p.storage < 0 || p.storage > 3) return fail(nullptr, LBM_ERR_INVALID, "unknown storage");
     if (p.step_kernel < 0 || p.step_kernel > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown step_kernel");
+    if (p.wall_bc < 0 || p.wall_bc > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown wall_bc");
     if (!(p.nu > 0.0) || !std::isfinite(p.nu)) return fail(nullptr, LBM_ERR_INVALID, "nu must be > 0");
     double k = p.k, Pr = p.Pr;
     if (k > 0.0 && Pr > 0.0) {
@@ -308,13 +309,15 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     for (int o = 0; o <= 6; ++o) {
         double s = 1.0;
         if (p.hkind == LBM_H_CM_SRT) s = sH;
-        else if (p.hkind == LBM_H_CM_1ST) s = (o == 1) ? sH : 1.0;
+        else if (p.hkind == LBM_H_CM_1ST || p.hkind == LBM_H_CUM_1ST) s = (o == 1) ? sH : 1.0;
         else s = (o % 2 == 1) ? sH : 1.0;
         d.sh[o] = s;
     }
     d.rho0 = p.rho0;
     d.Tref = p.T_ref;
     d.stochastic = p.round_nearest ? 0 : 1;
+    d.hkind = p.hkind;
+    d.wall_bc = p.wall_bc;
     d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;
@@ -460,9 +463,12 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
     }
     // adjoint reverse table: node y = x - e_a of each link (x, a) with
     // q <= 1/2 whose y is fluid or outlet (Eq. IABB reads h*_a(y) there)
+    // the first-order variants bounce back half-way: q = 1/2 on the device
+    std::vector<float> qdev(sq);
+    if (c->p.wall_bc != 0) std::fill(qdev.begin(), qdev.end(), 0.5f);
     std::vector<std::pair<int64_t, int32_t>> rev;  // (y*32 + a, link index)
     for (int64_t i = 0; i < n_links; ++i) {
-        if (!(sq[i] <= 0.5f)) continue;
+        if (!(qdev[i] < 0.5f)) continue;  // coefficient 1 - 2q vanishes at q = 1/2
         const int a = sd[i];
         const int yv = nbr(sn[i], -lbmd::EX(a), -lbmd::EY(a), -lbmd::EZ(a));
         if (yv < 0 || fl[yv] == lbmd::T_SOLID || fl[yv] == lbmd::T_INLET) continue;
@@ -519,7 +525,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         CK(cudaMemcpyAsync(c->d_segbase, segbase.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
         CK(cudaMemcpyAsync(c->d_wmask, wmask.data(), c->nw * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
         CK(cudaMemcpyAsync(c->d_woff, woff.data(), c->nw * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "wall upload");
-        CK(cudaMemcpyAsync(c->d_lq, sq.data(), n_links * sizeof(float), cudaMemcpyHostToDevice, c->stream), "link upload");
+        CK(cudaMemcpyAsync(c->d_lq, qdev.data(), n_links * sizeof(float), cudaMemcpyHostToDevice, c->stream), "link upload");
         CK(cudaMemcpyAsync(c->d_lwall, sw.data(), n_links * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "link upload");
         if (cudaMalloc(&c->d_dlink, n_links * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&c->d_rsegbase, nseg * sizeof(int32_t)) != cudaSuccess) {
@@ -972,6 +978,8 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next
                             const lbm_objective* obj, double* dJ_dtheta) {
     if (!c || !mu_next || !out) return LBM_ERR_INVALID;
     if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    if (c->p.hkind == LBM_H_CUM_1ST)
+        return fail(c, LBM_ERR_INVALID, "the adjoint covers the central-moment kinds (affine h step) only");
     lbm_status st = check_objective(c, obj);
     if (st != LBM_OK) return st;
     DeviceGuard g(c->device);

@@ -211,6 +211,8 @@ template <typename R> __device__ __forceinline__ void inverse_cube(R* c, R vx, R
 struct DevParams {
     int nx, ny, nz, N, periodic_x;
     int stochastic;      // 16-bit storage: 1 stochastic rounding, 0 round to nearest
+    int hkind;           // 0..2 central-moment kinds, 3 Cumulants-1st
+    int wall_bc;         // 0 Eq. IBB + Eq. IABB, 1 BB + EQ, 2 BB + ABB (BB/ABB: q = 1/2 on the device)
     uint32_t step;       // time level being written (random stream of st_sr)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6
@@ -378,9 +380,46 @@ __device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const D
 }
 
 template <typename R, int QH>
+__device__ __forceinline__ void heq_dev(R* hd, R psi, R ux, R uy, R uz, const DevParams& p);
+
+// ---- h: Cumulants-1st (Eq. H_cu_collision + App. D source) -----------------
+// With every cumulant of order >= 2 set to its equilibrium (c_s^2 on the
+// diagonal of the second order, zero elsewhere), the post-collision cumulants
+// (H + Q/2, v, c_s^2 I, 0, ...) are those of the discrete Maxwellian at the
+// relaxed mean velocity v = (1 - s) m + s u, m = sum(e h)/sum(h): the result
+// is that equilibrium.  The zeroth moment sum(h) must be positive.
+template <typename R, int QH>
+__device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+    R dH = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < QH; ++i) {
+        const int a = HDIR<QH>(i);
+        const R v = hd[i];
+        dH += v;
+        if (EX(a) != 0) jx += EX(a) * v;
+        if (EY(a) != 0) jy += EY(a) * v;
+        if (EZ(a) != 0) jz += EZ(a) * v;
+    }
+    const R Ht = (R)p.Tref + dH;  // zeroth moment of the stored (App. D shifted) h
+    const R iH = R(1) / Ht;
+    const R s = (R)p.sh[1];
+    const R vx = jx * iH + s * (ux - jx * iH);
+    const R vy = jy * iH + s * (uy - jy * iH);
+    const R vz = jz * iH + s * (uz - jz * iH);
+    heq_dev<R, QH>(hd, Ht + Q, vx, vy, vz, p);
+}
+
+// CUM: the Cumulants-1st kind (compile time, so the central-moment kinds
+// keep their register allocation)
+template <typename R, int QH, bool CUM = false>
 __device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
-    if constexpr (QH == 27) collide_h27<R>(hd, ux, uy, uz, Q, p);
-    else collide_h7<R>(hd, ux, uy, uz, Q, p);
+    if constexpr (CUM) {
+        collide_h_cum<R, QH>(hd, ux, uy, uz, Q, p);
+    } else if constexpr (QH == 27) {
+        collide_h27<R>(hd, ux, uy, uz, Q, p);
+    } else {
+        collide_h7<R>(hd, ux, uy, uz, Q, p);
+    }
 }
 
 // ---- equilibria in deviation form ------------------------------------------

@@ -149,13 +149,13 @@ __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __res
     }
 }
 
-template <typename S, int QH>
+template <typename S, int QH, bool CUM = false>
 __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __restrict__ hB, int n,
                                                 const DevParams& p, typename Acc<S>::R ux,
                                                 typename Acc<S>::R uy, typename Acc<S>::R uz,
                                                 typename Acc<S>::R Q) {
     using R = typename Acc<S>::R;
-    collide_h<R, QH>(hd, ux, uy, uz, Q, p);
+    collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
     if (sizeof(S) == 2 && p.stochastic) {
 #pragma unroll
         for (int i = 0; i < QH; ++i)
@@ -181,7 +181,9 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
 // FP64 arithmetic needs twice the registers: 2 blocks per SM
 template <typename S> constexpr int step_min_blocks() { return sizeof(typename Acc<S>::R) == 8 ? 2 : LBM_STEP_MIN_BLOCKS; }
 
-template <typename S, int QH, bool DO_H, bool REC>
+// EQ: the BB + EQ wall rule (compile time, so the default rules keep their
+// register allocation); CUM: the Cumulants-1st h kind
+template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* __restrict__ fA, S* __restrict__ fB,
                                                   const S* __restrict__ hA, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags,
@@ -273,6 +275,10 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
             const float q = __ldg(lq + l);
             const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref);
             const bool thin = (mask >> b) & 1u;
+            if constexpr (EQ) {  // EQ: the wall equilibrium w T_w itself
+                hd[ib] = R(0.5) * heq2;
+                continue;
+            }
             const R ha_b = ld<R>(hA + ia * N + n);
             if (q <= 0.5f && !thin) {
                 hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S>()) k_step(const S* 
         }
     }
     const R Q = theta ? (R)__ldg(theta + n) : R(0);
-    collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+    collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
     }
 }
 
@@ -345,7 +351,7 @@ __device__ __forceinline__ void stage_issue(const S* __restrict__ fA, const S* _
     }
 }
 
-template <typename S, int QH>
+template <typename S, int QH, bool CUM = false>
 __global__ void __launch_bounds__(kTile) k_step_staged(const S* __restrict__ fA, S* __restrict__ fB,
                                                         const S* __restrict__ hA, S* __restrict__ hB,
                                                         const uint8_t* __restrict__ flags,
@@ -476,6 +482,10 @@ __global__ void __launch_bounds__(kTile) k_step_staged(const S* __restrict__ fA,
                     const float q = __ldg(lq + l);
                     const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref);
                     const bool thin = (mask >> b) & 1u;
+                    if (p.wall_bc == 1) {  // EQ
+                        hd[ib] = R(0.5) * heq2;
+                        continue;
+                    }
                     const R ha_b = ld<R>(hA + ia * N + n);
                     if (q <= 0.5f && !thin) {
                         hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
@@ -487,34 +497,41 @@ __global__ void __launch_bounds__(kTile) k_step_staged(const S* __restrict__ fA,
                 }
             }
             const R Q = theta ? (R)__ldg(theta + n) : R(0);
-            collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+            collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
         }
         __syncthreads();  // stage sidx is refilled at the next iteration
     }
 }
 
-template <typename S, int QH>
-cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
+template <typename S, int QH, bool CUM>
+cudaError_t launch_step_staged_kind(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
     using R = typename Acc<S>::R;
     const size_t smem = (size_t)kStages * stage_bytes<S, QH>();
     static unsigned long long configured = 0;  // per device: dynamic shared memory limit raised
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !(configured & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_staged<S, QH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_step_staged<S, QH, CUM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<S, QH>, kTile, smem);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<S, QH, CUM>, kTile, smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((p.nx + kTile - 1) / kTile) * p.ny * p.nz;
     const int grid = std::max(1, std::min(tiles, num_sms * std::max(per_sm, 1)));
-    k_step_staged<S, QH><<<grid, kTile, smem, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags,
-                                                   b.theta, (const R*)b.inlet_post, b.seg_base, b.wmask, b.woff,
-                                                   b.lq, b.lwall, b.Twall, err, p);
+    k_step_staged<S, QH, CUM><<<grid, kTile, smem, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB,
+                                                        b.flags, b.theta, (const R*)b.inlet_post, b.seg_base,
+                                                        b.wmask, b.woff, b.lq, b.lwall, b.Twall, err, p);
     return cudaGetLastError();
+}
+
+template <typename S, int QH>
+cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
+    return p.hkind == 3 ? launch_step_staged_kind<S, QH, true>(b, p, err, num_sms, s)
+                        : launch_step_staged_kind<S, QH, false>(b, p, err, num_sms, s);
 }
 
 template <typename S, int QH>
@@ -525,8 +542,20 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
 #define LBM_STEP_ARGS                                                                                            \
     (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, b.seg_base, \
         b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, p
-    if (advance_h && !urec) k_step<S, QH, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
-    else if (advance_h) k_step<S, QH, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+    const bool cum = p.hkind == 3, eq = p.wall_bc == 1;
+    if (advance_h) {
+        const int v = (urec ? 4 : 0) | (cum ? 2 : 0) | (eq ? 1 : 0);
+        switch (v) {
+            case 0: k_step<S, QH, true, false, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 1: k_step<S, QH, true, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 2: k_step<S, QH, true, false, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 3: k_step<S, QH, true, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 4: k_step<S, QH, true, true, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 5: k_step<S, QH, true, true, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 6: k_step<S, QH, true, true, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            default: k_step<S, QH, true, true, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+        }
+    }
     else if (urec) k_step<S, QH, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
     else k_step<S, QH, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
 #undef LBM_STEP_ARGS
@@ -534,7 +563,7 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
 }
 
 // ---- initialisation: equilibria, App. D shift, one collision -------------
-template <typename S, int QH>
+template <typename S, int QH, bool CUM = false>
 __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags, const float* __restrict__ theta,
                                                   const typename Acc<S>::R* __restrict__ inlet,
@@ -568,7 +597,7 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restri
     heq_dev<R, QH>(hd, r * (R)T[n] - R(0.5) * Q, vx, vy, vz, p);
     R ux, uy, uz;
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
-    collide_store_h<S, QH>(hd, hB, n, p, ux, uy, uz, Q);
+    collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
 }
 
 template <typename S, int QH>
@@ -576,7 +605,12 @@ cudaError_t launch_init(const Buffers& b, const DevParams& p, const double* rho,
                         cudaStream_t s) {
     using R = typename Acc<S>::R;
     const int grid = (p.N + kBlock - 1) / kBlock;
-    k_init<S, QH><<<grid, kBlock, 0, s>>>((S*)b.fB, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, rho, u, T, p);
+    if (p.hkind == 3)
+        k_init<S, QH, true><<<grid, kBlock, 0, s>>>((S*)b.fB, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, rho,
+                                                    u, T, p);
+    else
+        k_init<S, QH><<<grid, kBlock, 0, s>>>((S*)b.fB, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, rho, u, T,
+                                              p);
     return cudaGetLastError();
 }
 
@@ -771,7 +805,9 @@ __global__ void __launch_bounds__(kRedThreads) k_surface_flux(const S* __restric
             const bool thin = (mask >> b) & 1u;
             const R ha_b = ld<R>(hA + ia * N + n);
             R hin;
-            if (q <= 0.5f && !thin) {
+            if (p.wall_bc == 1) {
+                hin = R(0.5) * heq2;
+            } else if (q <= 0.5f && !thin) {
                 const R ha_f = ld<R>(hA + ia * N + src_of(nb, a));
                 hin = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * ha_f) + heq2;
             } else {
@@ -827,8 +863,10 @@ template <typename R> __device__ __forceinline__ void inv3T(R& a, R& b, R& c, R 
 // partial derivatives of one Eq. IABB arrival with respect to h*_a(x_b),
 // h*_abar(x_b) and T_w (the latter per unit weight w_a)
 template <typename R>
-__device__ __forceinline__ void iabb_partials(float q, bool thin, R& d_ab, R& d_abb, R& d_T) {
-    if (q <= 0.5f && !thin) {
+__device__ __forceinline__ void iabb_partials(float q, bool thin, int wall_bc, R& d_ab, R& d_abb, R& d_T) {
+    if (wall_bc == 1) {  // EQ: the arrival is w T_w
+        d_ab = R(0); d_abb = R(0); d_T = R(1);
+    } else if (q <= 0.5f && !thin) {
         d_ab = -R(2) * (R)q; d_abb = R(0); d_T = R(2);
     } else {
         const R qq = (R)fmaxf(q, 0.5f);
@@ -929,7 +967,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
             const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
             const bool thin = (mask >> HDIR<QH>(ib)) & 1u;
             R d_ab, d_abb, d_T;
-            iabb_partials<R>(q, thin, d_ab, d_abb, d_T);
+            iabb_partials<R>(q, thin, p.wall_bc, d_ab, d_abb, d_T);
             const R m = mu_next[ib * N + n] + cw;
             lam[i] += d_ab * m - cw;
             lam[ib] += d_abb * m;

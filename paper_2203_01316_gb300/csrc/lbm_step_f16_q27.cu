@@ -1,0 +1,18 @@
+// Kernel instantiations for FP16 (shifted) storage, D3Q27 h.
+#define LBM_KERNEL_TU
+#include "lbm_kernels.cuh"
+
+namespace lbmd {
+template cudaError_t launch_step<__half, 27>(const Buffers&, const DevParams&, cudaStream_t, bool);
+template cudaError_t launch_objective<__half, 27>(const Buffers&, const DevParams&, AdjObjective, double*, double*,
+                                              cudaStream_t);
+template cudaError_t launch_init<__half, 27>(const Buffers&, const DevParams&, const double*, const double*,
+                                         const double*, cudaStream_t);
+template cudaError_t launch_macros<__half, 27>(const Buffers&, const DevParams&, double*, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_populations<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_balances<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_surface_flux<__half, 27>(const Buffers&, const DevParams&, int, double*, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_step_staged<__half, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
+}  // namespace lbmd

@@ -1,0 +1,20 @@
+// Kernel instantiations for FP32 storage, D3Q7 h.
+#define LBM_KERNEL_TU
+#include "lbm_kernels.cuh"
+
+namespace lbmd {
+template cudaError_t launch_step<float, 7>(const Buffers&, const DevParams&, cudaStream_t, bool);
+template cudaError_t launch_objective<float, 7>(const Buffers&, const DevParams&, AdjObjective, double*, double*,
+                                              cudaStream_t);
+template cudaError_t launch_init<float, 7>(const Buffers&, const DevParams&, const double*, const double*,
+                                         const double*, cudaStream_t);
+template cudaError_t launch_macros<float, 7>(const Buffers&, const DevParams&, double*, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_populations<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_balances<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_surface_flux<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_step_staged<float, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
+template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*, float*,
+                                           AdjObjective, double*, cudaStream_t);
+}  // namespace lbmd

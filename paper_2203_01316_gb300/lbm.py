@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_ERR_INVALID, LBM_ERR_NOMEM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = range(6)
 STATUS = {1: "LBM_ERR_INVALID", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_STATE"}
-HKIND = {"trt": 0, "srt": 1, "1st": 2}
+HKIND = {"trt": 0, "srt": 1, "1st": 2, "cum1st": 3}
 STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
 
 # every symbol declared in include/lbm.h
@@ -45,7 +45,9 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lat_h", C.c_int), ("hkind", C.c_int),
                 ("storage", C.c_int), ("periodic_x", C.c_int), ("nu", C.c_double), ("k", C.c_double),
                 ("Pr", C.c_double), ("omega_bulk", C.c_double), ("rho0", C.c_double), ("T_ref", C.c_double),
-                ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int), ("step_kernel", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int), ("step_kernel", C.c_int),
+                ("wall_bc", C.c_int)]
+WALL_BC = {"iabb": 0, "eq": 1, "abb": 2}
 STEP_KERNEL = {"auto": 0, "classic": 1, "staged": 2}
 
 
@@ -127,15 +129,17 @@ class Solver:
     """One lattice Boltzmann context (see include/lbm.h for the semantics).
 
     nx, ny, nz: grid; nu: viscosity; k or Pr: thermal diffusivity or Prandtl
-    number; lat_h: 27 or 7; hkind: 'trt' | 'srt' | '1st'; storage:
+    number; lat_h: 27 or 7; hkind: 'trt' | 'srt' | '1st' | 'cum1st'; storage:
     'f32' | 'f64' | 'f16' | 'bf16'; periodic_x: True, or False for an
     inlet/outlet channel; stream: a torch.cuda.Stream or raw handle, or None
     for a library-owned stream; round_nearest: 16-bit storage rounds to
     nearest instead of stochastically; step_kernel: 'auto' | 'classic' |
-    'staged' (implementation of the step, same results)."""
+    'staged' (implementation of the step, same results); wall_bc: 'iabb'
+    (Eq. IBB/IABB with q) | 'eq' (BB + EQ) | 'abb' (BB + ABB)."""
 
     def __init__(self, nx, ny, nz, nu, k=0.0, Pr=0.0, lat_h=27, hkind="trt", storage="f32", periodic_x=True,
-                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False, step_kernel="auto"):
+                 omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False, step_kernel="auto",
+                 wall_bc="iabb"):
         self.L = lib()
         p = Params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -150,6 +154,7 @@ class Solver:
         p.cuda_stream = stream
         p.round_nearest = 1 if round_nearest else 0
         p.step_kernel = STEP_KERNEL[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
+        p.wall_bc = WALL_BC[wall_bc] if isinstance(wall_bc, str) else int(wall_bc)
         self.params = p
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.N = p.nx * p.ny * p.nz

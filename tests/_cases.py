@@ -7,13 +7,13 @@ from paper_2203_01316_gb300 import inputs as I
 
 
 def make_pair(w, nu, k, qh=27, hkind="trt", storage="f32", F=(0.0, 0.0, 0.0), wall_T=(1.0,),
-              rho0=1.0, T_ref=0.0, theta=None, omega_bulk=1.0, oracle=True):
+              rho0=1.0, T_ref=0.0, theta=None, omega_bulk=1.0, oracle=True, wall_bc="iabb"):
     from paper_2203_01316_gb300 import Solver
     nx, ny, nz = w["dims"]
     u_in = w.get("u_in", (0.0, 0.0, 0.0))
     T_in = w.get("T_in", 0.0)
     s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=qh, hkind=hkind, storage=storage, periodic_x=w["periodic_x"],
-               omega_bulk=omega_bulk, rho0=rho0, T_ref=T_ref)
+               omega_bulk=omega_bulk, rho0=rho0, T_ref=T_ref, wall_bc=wall_bc)
     s.set_geometry(w["flags"], w["links"], n_walls=w["nwalls"])
     for i, T in enumerate(wall_T[: w["nwalls"]]):
         s.set_bc(i, T)
@@ -26,7 +26,7 @@ def make_pair(w, nu, k, qh=27, hkind="trt", storage="f32", F=(0.0, 0.0, 0.0), wa
     o = None
     if oracle:
         p = O.make_params(nx=nx, ny=ny, nz=nz, qh=qh, hkind=hkind, periodic_x=w["periodic_x"], nu=nu, k=k,
-                          F=F, u_in=u_in, T_in=T_in, omega_bulk=omega_bulk)
+                          F=F, u_in=u_in, T_in=T_in, omega_bulk=omega_bulk, wall_bc=wall_bc)
         o = O.Oracle(p)
         o.set_geometry(w["flags"], w["links"], nwalls=w["nwalls"])
         for i, T in enumerate(wall_T[: w["nwalls"]]):

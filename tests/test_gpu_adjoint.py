@@ -25,11 +25,11 @@ def _torch():
     return torch
 
 
-def _solver(w, storage, qh, kind, nu, k, F, Tw, theta, T_ref=0.5):
+def _solver(w, storage, qh, kind, nu, k, F, Tw, theta, T_ref=0.5, wall_bc="iabb"):
     from paper_2203_01316_gb300 import Solver
     nx, ny, nz = w["dims"]
     s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=qh, hkind=kind, storage=storage, periodic_x=w["periodic_x"],
-               T_ref=T_ref)
+               T_ref=T_ref, wall_bc=wall_bc)
     s.set_geometry(w["flags"], w["links"], n_walls=w["nwalls"])
     for i, T in enumerate(Tw):
         s.set_bc(i, T)
@@ -69,26 +69,28 @@ def _channel():
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-@pytest.mark.parametrize("case,qh,kind,obj", [
-    ("plate", 27, "trt", ("surface", 1, 0.9)),
-    ("plate", 27, "srt", ("section", 4, 1.0)),
-    ("plate", 27, "1st", ("surface", 0, 1.0)),
-    ("plate", 7, "trt", ("surface", 1, 1.0)),
-    ("channel", 27, "trt", ("surface", 0, 1.0)),
-    ("channel", 7, "srt", ("section", 17, 1.0)),
+@pytest.mark.parametrize("case,qh,kind,obj,wall_bc", [
+    ("plate", 27, "trt", ("surface", 1, 0.9), "iabb"),
+    ("plate", 27, "srt", ("section", 4, 1.0), "iabb"),
+    ("plate", 27, "1st", ("surface", 0, 1.0), "iabb"),
+    ("plate", 7, "trt", ("surface", 1, 1.0), "iabb"),
+    ("plate", 27, "trt", ("surface", 1, 1.0), "eq"),
+    ("plate", 27, "trt", ("surface", 0, 1.0), "abb"),
+    ("channel", 27, "trt", ("surface", 0, 1.0), "iabb"),
+    ("channel", 7, "srt", ("section", 17, 1.0), "iabb"),
 ])
-def test_adjoint_matches_oracle(storage, case, qh, kind, obj):
+def test_adjoint_matches_oracle(storage, case, qh, kind, obj, wall_bc):
     w = _plate() if case == "plate" else _channel()
     Tw = [1.0, 0.1][: w["nwalls"]]
     nu, k, F = 0.05, 0.01, ((2e-4, 0.0, 1e-4) if case == "plate" else (0.0, 0.0, 0.0))
     theta = w["theta"].astype(np.float32).astype(np.float64)
-    s = _solver(w, storage, qh, kind, nu, k, F, Tw, theta)
+    s = _solver(w, storage, qh, kind, nu, k, F, Tw, theta, wall_bc=wall_bc)
     f0, h0 = s.populations()
     nsteps, window, every = 11, (4, 11), 4
     Jg, dth_g, dTw_g, _ = _gpu_gradients(s, theta, Tw, nsteps, window, obj, every)
     nx, ny, nz = w["dims"]
     p = O.make_params(nx=nx, ny=ny, nz=nz, qh=qh, hkind=kind, periodic_x=w["periodic_x"], nu=nu, k=k, F=F,
-                      u_in=w.get("u_in", (0, 0, 0)), T_in=w.get("T_in", 0.0))
+                      u_in=w.get("u_in", (0, 0, 0)), T_in=w.get("T_in", 0.0), wall_bc=wall_bc)
     o = O.Oracle(p)
     o.set_geometry(w["flags"], w["links"], nwalls=w["nwalls"])
     for i, T in enumerate(Tw):

@@ -90,6 +90,27 @@ def test_one_step_small_channel(storage, qh, kind):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("qh", [27, 7])
+def test_one_step_cumulant_h_kind(storage, qh):
+    # Cumulants-1st needs a positive zeroth moment of h: inlet T 0.5, wall 1.0
+    w = small_channel(u_in=0.03, T_in=0.5)
+    w["T"][:] = 0.5
+    s, o = make_pair(w, nu=0.03, k=2e-3, qh=qh, hkind="cum1st", storage=storage, wall_T=(1.0,), T_ref=0.5)
+    s.step(7)
+    _one_step_parity(s, o, TOL1[storage], qh)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("wall_bc", ["eq", "abb"])
+def test_one_step_first_order_walls(storage, wall_bc):
+    w = small_channel()
+    s, o = make_pair(w, nu=0.03, k=2e-3, storage=storage, wall_T=(0.8,), T_ref=0.1, wall_bc=wall_bc)
+    s.step(5)
+    _one_step_parity(s, o, TOL1[storage], 27)
+    assert abs(s.surface_flux(0) - o.surface_flux(0)) <= 1e-5 * max(1.0, abs(o.surface_flux(0)))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
 def test_one_step_plate_with_force_and_source(storage):
     w = I.plate_channel(nx=33, ny=13, nz=9, q_bottom=0.3, q_top=0.7, theta_max=1e-3, seed=3)
     s, o = make_pair(w, nu=0.05, k=5e-3, storage=storage, F=(2e-4, -1e-4, 5e-5), wall_T=(1.0, 0.0),
