@@ -92,6 +92,7 @@ __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfl
 // the FP32 bit pattern and truncating (FP32 -> FP16 drops 13 mantissa bits,
 // -> BF16 drops 16).  FP16 subnormals, overflow and non-finite values use
 // round-to-nearest.
+// r: 32 random bits; the top bits supply the random fraction
 __device__ __forceinline__ void st_sr(float* p, float v, uint32_t) { *p = v; }
 __device__ __forceinline__ void st_sr(double* p, double v, uint32_t) { *p = v; }
 __device__ __forceinline__ void st_sr(__half* p, float v, uint32_t r) {
@@ -100,18 +101,30 @@ __device__ __forceinline__ void st_sr(__half* p, float v, uint32_t r) {
         *p = __float2half_rn(v);
         return;
     }
-    *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+    *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
 }
 __device__ __forceinline__ void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
     if (!isfinite(v)) {
         *p = __float2bfloat16_rn(v);
         return;
     }
-    *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xFFFFu)));
+    *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r >> 16)));
 }
 
+// Random bits of the stores of one node: a strong hash of (node, array,
+// time level) seeds a linear congruential sequence (Numerical Recipes
+// constants) that advances once per store; st_sr uses only its top bits,
+// which are well distributed.  Reproducible, and one multiply-add per store.
+struct SrStream {
+    uint32_t s;
+    __device__ __forceinline__ uint32_t next() {
+        s = s * 1664525u + 1013904223u;
+        return s;
+    }
+};
+
 // counter-based 32-bit hash (the "lowbias32" integer mixer of C. Wellons) of
-// (node, population slot, step): reproducible random bits for st_sr
+// (node and array, time level): the seed of a node's SrStream
 __device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t step) {
     uint32_t x = key ^ (step * 0x9E3779B9u);
     x ^= x >> 16;
