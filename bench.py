@@ -447,6 +447,114 @@ def porous_study(args):
     print(json.dumps(out), flush=True)
 
 
+def validation_cylinders(args):
+    """Sec. 4.3: steady conduction between concentric cylinders (inner
+    diameter D/2 at T = 1, outer D at T = 0, k = 0.1, CM-TRT, no flow) on the
+    GPU path (FP64 storage), against T(r) = 1 - ln(r/r_in)/ln(r_out/r_in),
+    for Eq. IABB, ABB and EQ walls over D = 16 ... 128: normalised L2 error
+    and observed order between successive grids."""
+    import torch  # noqa: F401
+    from paper_2203_01316_gb300 import Solver, build, inputs as I
+    build.build()
+    Ds = [int(d) for d in args.sizes.split(",")] if args.sizes else [16, 32, 64, 128]
+    k = 0.1
+    out = {}
+    for bc in ("iabb", "abb", "eq"):
+        errs = []
+        for D in Ds:
+            w = I.concentric_cylinders(D)
+            n = w["dims"][0]
+            s = Solver(n, n, 1, nu=1.0 / 6.0, k=k, lat_h=27, hkind="trt", storage="f64", periodic_x=True,
+                       T_ref=0.5, wall_bc=bc)
+            s.set_geometry(w["flags"], w["links"], n_walls=2)
+            s.set_bc(0, 1.0)
+            s.set_bc(1, 0.0)
+            s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+            steps = int(12 * (D / 4.0) ** 2 / k) + 200  # about twelve diffusion times across the gap
+            s.step(steps)
+            _, _, T = s.macros()
+            s.close()
+            fl = np.asarray(w["flags"]) == 0
+            r = w["r"][fl]
+            Ta = 1.0 - np.log(r / w["R_inner"]) / np.log(w["R_outer"] / w["R_inner"])
+            errs.append(float(np.sqrt(np.sum((Ta - T[fl]) ** 2) / np.sum(Ta ** 2))))
+        orders = [math.log(errs[i] / errs[i + 1]) / math.log(Ds[i + 1] / Ds[i]) for i in range(len(Ds) - 1)]
+        out[bc] = {"D": Ds, "L2": errs, "observed_order": orders}
+    line = {"validation": "concentric cylinders (Sec. 4.3), CM-TRT, k = 0.1, FP64 storage", "results": out}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def lattice_convolution(T0, n, u=(0.0, 0.0)):
+    """n steps of T(x) <- sum_a h^eq_a(T(x - e_a), u) on a periodic L x L
+    plane: the D3Q27 h step at s^H = 1 (every kind collapses to its
+    equilibrium), applied as a product of 1-D transfer functions (Sec. 2.1,
+    product-form discrete equilibrium with c_s^2 = 1/3) by FFT in FP64."""
+    Ly, Lx = T0.shape
+    def sym(L, v):
+        th = np.fft.fftfreq(L) * 2.0 * np.pi
+        a = 1.0 / 3.0 + v * v
+        return (1.0 - a) + 0.5 * (a + v) * np.exp(-1j * th) + 0.5 * (a - v) * np.exp(1j * th)
+    G = np.outer(sym(Ly, u[1]), sym(Lx, u[0]))
+    return np.real(np.fft.ifft2(np.fft.fft2(T0) * G ** n))
+
+
+def hill_closed_form(L, s0, k, n, ux):
+    """Sec. 4.1 closed form in 2-D (N = 2), centre advected by u_x n and
+    wrapped into the periodic box, with the nearest periodic images."""
+    yy, xx = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    s2 = s0 + 2.0 * k * n
+    cx = (L / 2.0 + ux * n) % L
+    C = np.zeros((L, L))
+    for ix in (-1, 0, 1):
+        for iy in (-1, 0, 1):
+            C += (s0 / s2) * np.exp(-((xx - cx + ix * L) ** 2 + (yy - L / 2.0 + iy * L) ** 2) / (2.0 * s2))
+    return C
+
+
+def validation_hill(args):
+    """Sec. 4.1: advection-diffusion of a Gaussian hill on a periodic
+    256 x 256 x 1 box (sigma0^2 = 100, t_SI = 100, k_SI = 4, so n = 400/k
+    steps), at rest and at u_x = 0.1 (lattice units), for every h kind and
+    k from 1/6 down; normalised L2 error of the hill C = T - 1 against the
+    closed form (FP32 storage).  At k = 1/6 the result is also compared with
+    the exact lattice convolution the step reduces to there."""
+    import torch  # noqa: F401
+    from paper_2203_01316_gb300 import Solver, build, inputs as I
+    build.build()
+    L, s0 = 256, 100.0
+    ks = [float(v) for v in args.sizes.split(",")] if args.sizes else [1.0 / 6.0, 1e-2, 1e-3, 1e-4]
+    out, lat = {}, {}
+    for kind in ("trt", "srt", "1st", "cum1st"):
+        for ux in (0.0, 0.1):
+            key = f"{kind}, u_x = {ux:g}"
+            out[key] = {}
+            for k in ks:
+                n = int(round(400.0 / k))
+                w = I.gaussian_hill(L, s0)
+                w["u"][0] = ux
+                s = Solver(L, L, 1, nu=1.0 / 6.0, k=k, lat_h=27, hkind=kind, storage="f32", periodic_x=True,
+                           T_ref=1.0)
+                s.set_geometry(w["flags"], None)
+                s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+                t0 = time.perf_counter()
+                s.step(n)
+                _, _, T = s.macros()
+                dt = time.perf_counter() - t0
+                s.close()
+                Cn = T.reshape(L, L) - 1.0
+                Ca = hill_closed_form(L, s0, k, n, ux)
+                out[key][f"{k:.4g}"] = float(np.sqrt(np.sum((Ca - Cn) ** 2) / np.sum(Ca ** 2)))
+                if k == 1.0 / 6.0:
+                    Cl = lattice_convolution(w["T"].reshape(L, L) - 1.0, n, (ux, 0.0))
+                    lat[key] = float(np.abs(Cl - Cn).max())
+                print(f"# {key} k={k:.4g} n={n} {dt:.1f}s L2={out[key][f'{k:.4g}']:.3e}", file=sys.stderr, flush=True)
+    line = {"validation": "Gaussian hill (Sec. 4.1), 256x256x1, sigma0^2 = 100, n = 400/k steps, FP32",
+            "L2": out, "k=1/6: max |C - lattice convolution|": lat}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -553,6 +661,9 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--validation", choices=["cylinders", "hill"],
+                    help="run one of the paper's validation workloads on the GPU path")
+    ap.add_argument("--sizes", default="", help="validation: comma-separated D (cylinders) or k (hill)")
     ap.add_argument("--workload", choices=["sphere", "porous"], default="sphere",
                     help="porous: the 512x256x256 porous bed (see porous_study)")
     ap.add_argument("--spin", type=int, default=2000, help="porous: forward steps before the adjoint")
@@ -565,7 +676,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.precision:
+    if args.validation == "cylinders":
+        validation_cylinders(args)
+    elif args.validation == "hill":
+        validation_hill(args)
+    elif args.precision:
         precision_study(args)
     elif args.workload == "porous":
         porous_study(args)

@@ -246,3 +246,62 @@ def porous_bed(nx=512, ny=256, nz=256, n_spheres=200, dmin=12.0, dmax=24.0, gap=
             "rho": np.ones(N), "u": u, "T": np.full(N, T_in), "periodic_x": False,
             "nwalls": 1, "centres": np.array(centres), "radii": np.array(radii),
             "u_in": (u_in, 0.0, 0.0), "T_in": T_in}
+
+
+def concentric_cylinders(D, seed=1234, margin=2):
+    """Two coaxial cylinders along z (2-D: nz = 1): the inner one of
+    diameter D/2 (wall 0) and the outer one of diameter D (wall 1), centre
+    offset by a seeded sub-lattice shift; fluid between them.  Solid is
+    r <= D/4 or r >= D/2 (distance in the x-y plane); q is the fraction of
+    each link at which its projection crosses the circle."""
+    n = int(math.ceil(D)) + 2 * margin
+    off = uniform(seed, 2)
+    c = np.array([n / 2.0 + off[0] - 0.5, n / 2.0 + off[1] - 0.5])
+    R1, R2 = D / 4.0, D / 2.0
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2
+    flags = np.where((r2 <= R1 * R1) | (r2 >= R2 * R2), SOLID, FLUID).astype(np.uint8)
+    nodes, dirs, qs, walls = [], [], [], []
+    fl = flags == FLUID
+    Xb, Yb = x[fl], y[fl]
+    for a in range(1, 27):
+        ex, ey, _ = E27[a]
+        if ex == 0 and ey == 0:
+            continue
+        Xt, Yt = (Xb + ex) % n, (Yb + ey) % n
+        tgt_solid = flags[Yt, Xt] == SOLID
+        if not tgt_solid.any():
+            continue
+        dx, dy = Xb[tgt_solid] - c[0], Yb[tgt_solid] - c[1]
+        tr2 = (Xb[tgt_solid] + ex - c[0]) ** 2 + (Yb[tgt_solid] + ey - c[1]) ** 2
+        inner = tr2 <= R1 * R1
+        ee = float(ex * ex + ey * ey)
+        de = dx * ex + dy * ey
+        dd = dx * dx + dy * dy
+        R = np.where(inner, R1, R2)
+        disc = np.maximum(de * de - ee * (dd - R * R), 0.0)
+        # entering the inner circle: the smaller root; leaving the outer one: the larger
+        t = np.where(inner, (-de - np.sqrt(disc)) / ee, (-de + np.sqrt(disc)) / ee)
+        t = np.clip(t, np.nextafter(0.0, 1.0), 1.0)
+        nodes.append(node_index(Xb[tgt_solid], Yb[tgt_solid], 0, n, n))
+        dirs.append(np.full(int(tgt_solid.sum()), a))
+        qs.append(t.astype(np.float32))
+        walls.append(np.where(inner, 0, 1))
+    links = _sort_links(np.concatenate(nodes), np.concatenate(dirs), np.concatenate(qs), np.concatenate(walls))
+    N = n * n
+    return {"dims": (n, n, 1), "flags": flags.reshape(-1), "links": links, "rho": np.ones(N),
+            "u": np.zeros((3, N)), "T": np.full(N, 0.5), "periodic_x": True, "nwalls": 2,
+            "centre": c, "R_inner": R1, "R_outer": R2,
+            "r": np.sqrt(r2).reshape(-1)}
+
+
+def gaussian_hill(L=256, sigma0_sq=100.0, C0=1.0, T0=1.0):
+    """Periodic L x L x 1 box with T = T0 + C0 exp(-|x - x0|^2 / (2 sigma0^2))
+    at rest (Sec. 4.1 initial condition; T0 keeps the zeroth moment of h
+    positive for every collision kind)."""
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    x0 = L / 2.0
+    C = C0 * np.exp(-((x - x0) ** 2 + (y - x0) ** 2) / (2.0 * sigma0_sq))
+    N = L * L
+    return {"dims": (L, L, 1), "flags": np.zeros(N, np.uint8), "links": _empty_links(), "rho": np.ones(N),
+            "u": np.zeros((3, N)), "T": (T0 + C).reshape(-1), "periodic_x": True, "nwalls": 1}
