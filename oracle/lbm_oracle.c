@@ -891,6 +891,48 @@ static void iabb_partials(const orc_sim* s, float qf, int thin, double* d_ab, do
     }
 }
 
+/* Jacobian of the Cumulants-1st collision (Eq. H_cu_collision with the App. D
+ * source) at the pre-collision h of one node.  With every cumulant of order
+ * >= 2 at its equilibrium the result is h* = (H + Q) M(v): M(v) is the
+ * lattice equilibrium of unit zeroth moment at v = (1 - s) m + s u, with
+ * H = sum h and m = sum e h / H (the first cumulants).  Hence
+ *     dh*_a/dh_b = M_a(v) + (H + Q) sum_d dM_a/dv_d (1 - s) (e_bd - m_d) / H,
+ *     dh*_a/dQ   = M_a(v).
+ * M is a polynomial of degree two in each v_d, so a central difference of the
+ * equilibrium in v_d is its derivative up to rounding.  Jm[a * Q_h + b]. */
+static void cum_jacobian(const orc_params* p, const double* h, const double u[3], double Q, double* Jm,
+                         double* dQ) {
+    const lattice_t* L = lattice(p->qh);
+    const int n = L->Q;
+    const double s = 1.0 / (p->k / CS2 + 0.5);
+    double H = 0.0, m[3] = {0.0, 0.0, 0.0}, v[3];
+    for (int a = 0; a < n; ++a) {
+        H += h[a];
+        for (int d = 0; d < 3; ++d) m[d] += L->e[a][d] * h[a];
+    }
+    for (int d = 0; d < 3; ++d) {
+        m[d] /= H;
+        v[d] = m[d] + s * (u[d] - m[d]);
+    }
+    equilibrium(L, 1.0, v, dQ);
+    double dM[3][27];
+    const double eps = 1e-3;
+    for (int d = 0; d < 3; ++d) {
+        double vp[3] = {v[0], v[1], v[2]}, vm[3] = {v[0], v[1], v[2]}, Mp[27], Mm[27];
+        vp[d] += eps;
+        vm[d] -= eps;
+        equilibrium(L, 1.0, vp, Mp);
+        equilibrium(L, 1.0, vm, Mm);
+        for (int a = 0; a < n; ++a) dM[d][a] = (Mp[a] - Mm[a]) / (2.0 * eps);
+    }
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double acc = 0.0;
+            for (int d = 0; d < 3; ++d) acc += dM[d][a] * (1.0 - s) * (L->e[b][d] - m[d]);
+            Jm[a * n + b] = dQ[a] + (H + Q) * acc / H;
+        }
+}
+
 /* lam += P^T mu (transpose of the h part of orc_stream), dTw += (db/dT_w)^T mu.
  * mu is zero at solid and inlet nodes. */
 static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, double* dTw) {
@@ -1005,20 +1047,25 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
 /* Forward run from the post-collision state (f_post, h_post) = s^0 over
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
- * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, -2 for the
- * cumulant kind (its h step is not affine, so this sweep does not apply). */
+ * dJ/dT_w[nwalls] to them.  Returns 0, or -1 on a streaming error.
+ * The Cumulants-1st collision is not affine in h: for that kind the forward
+ * keeps the pre-collision h of every level and the reverse sweep applies the
+ * transpose of the collision's Jacobian there (cum_jacobian); streaming and
+ * the walls stay affine. */
 int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
                 int wall, int plane, double weight, double* J, double* dtheta, double* dTw) {
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
-    if (dtheta && s->p.hkind == KIND_CUM1) return -2; /* not affine in h: no linear adjoint here */
+    const int cum = s->p.hkind == KIND_CUM1;
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
+    double* hrec = (dtheta && cum) ? (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double)) : NULL;
     orc_set_post(s, f_post, h_post);
     double Jv = 0.0;
     for (int k = 0; k <= nsteps; ++k) {
         if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane);
         if (k == nsteps) break;
-        if (orc_stream(s) != 0) { free(urec); return -1; }
+        if (orc_stream(s) != 0) { free(urec); free(hrec); return -1; }
+        if (hrec) memcpy(hrec + (size_t)(k + 1) * HN, s->h, HN * sizeof(double));
         g_record_u = urec ? urec + (size_t)(k + 1) * 3 * N : NULL;
         orc_collide(s);
         g_record_u = NULL;
@@ -1038,13 +1085,19 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
             if (s->flags[n] == FL_SOLID || s->flags[n] == FL_INLET) continue;
             double u[3], Lm[27 * 27], col[27], unit[27], e[27], zero[27];
             for (int d = 0; d < 3; ++d) u[d] = urec[(size_t)k * 3 * N + (size_t)d * N + n];
-            for (int j = 0; j < qh; ++j) {
-                for (int i = 0; i < qh; ++i) unit[i] = (i == j) ? 1.0 : 0.0;
-                collide_h(&s->p, unit, u, 0.0, col);
-                for (int i = 0; i < qh; ++i) Lm[i * qh + j] = col[i];
+            if (cum) {
+                double g[27];
+                for (int i = 0; i < qh; ++i) g[i] = hrec[(size_t)k * HN + (size_t)i * N + n];
+                cum_jacobian(&s->p, g, u, theta_at(s, n), Lm, e);
+            } else {
+                for (int j = 0; j < qh; ++j) {
+                    for (int i = 0; i < qh; ++i) unit[i] = (i == j) ? 1.0 : 0.0;
+                    collide_h(&s->p, unit, u, 0.0, col);
+                    for (int i = 0; i < qh; ++i) Lm[i * qh + j] = col[i];
+                }
+                for (int i = 0; i < qh; ++i) zero[i] = 0.0;
+                collide_h(&s->p, zero, u, 1.0, e);
             }
-            for (int i = 0; i < qh; ++i) zero[i] = 0.0;
-            collide_h(&s->p, zero, u, 1.0, e);
             double dth = 0.0;
             for (int i = 0; i < qh; ++i) dth += e[i] * lam[(size_t)i * N + n];
             dtheta[n] += dth;
@@ -1058,5 +1111,6 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     free(mu);
     free(lam);
     free(urec);
+    free(hrec);
     return 0;
 }

@@ -102,13 +102,59 @@ def test_channel_adjoint_directional_derivative(qh):
         assert np.all(dth[w["flags"] == I.INLET] == 0.0)
 
 
-def test_cumulant_kind_has_no_linear_adjoint():
-    w, p = _plate_case()
-    p.hkind = O.KINDS["cum1st"]
-    w["T"][:] = 0.6
-    o, fpost, hpost = _setup(w, p, [1.0, 0.1])
-    with pytest.raises(O.OracleError):
-        o.adjoint(fpost, hpost, 3, (0, 3), ("surface", 0, 1.0), nwalls=2)
+def _richardson(Jof, x0, eps):
+    """Central difference with one Richardson step: the O(eps^2) truncation
+    of the nonlinear J cancels, leaving O(eps^4)."""
+    d1 = (Jof(x0 + eps) - Jof(x0 - eps)) / (2 * eps)
+    d2 = (Jof(x0 + eps / 2) - Jof(x0 - eps / 2)) / eps
+    return (4 * d2 - d1) / 3
+
+
+@pytest.mark.parametrize("qh", [27, 7])
+@pytest.mark.parametrize("obj", [("surface", 1, 0.7), ("section", 3, 1.3)])
+def test_cumulant_adjoint_matches_finite_differences(qh, obj):
+    # Cumulants-1st (Eq. H_cu_collision): h* = (H + Q) M(v) with v depending on
+    # h / H, so J is not affine; the reverse sweep uses the collision's
+    # Jacobian at the recorded pre-collision states
+    w, p = _plate_case(qh, "cum1st")
+    Tw = [1.0, 0.1]
+    o, fpost, hpost = _setup(w, p, Tw)
+    nsteps, window = 10, (4, 10)
+    J, dth, dTw = o.adjoint(fpost, hpost, nsteps, window, obj, nwalls=2)
+    theta = w["theta"].copy()
+    fluid = np.nonzero(w["flags"] == I.FLUID)[0]
+    for n in np.random.default_rng(8).choice(fluid, 5, replace=False):
+        def Jt(x, n=n):
+            t = theta.copy()
+            t[n] = x
+            return _J(w, p, Tw, t, fpost, hpost, nsteps, window, obj)
+        fd = _richardson(Jt, theta[n], 1e-3)
+        assert abs(dth[n] - fd) <= 1e-8 * max(abs(fd), 1e-3), (n, dth[n], fd)
+    for wall in range(2):
+        def JT(x, wall=wall):
+            T = list(Tw)
+            T[wall] = x
+            return _J(w, p, T, theta, fpost, hpost, nsteps, window, obj)
+        fd = _richardson(JT, Tw[wall], 1e-3)
+        assert abs(dTw[wall] - fd) <= 1e-8 * max(abs(fd), 1e-3), (wall, dTw[wall], fd)
+    assert np.all(dth[w["flags"] == I.SOLID] == 0.0)
+
+
+def test_cumulant_adjoint_at_unit_rate_equals_cm_kinds():
+    # at s^H = 1 (k = 1/6) the mean is fully relaxed to u: every kind
+    # collapses to h* = (H + Q) M(u), the same affine map, so the
+    # Cumulants-1st gradient equals the CM-TRT one
+    w, p = _plate_case(27, "cum1st")
+    p.k = 1.0 / 6.0
+    Tw = [1.0, 0.1]
+    o, fpost, hpost = _setup(w, p, Tw)
+    Jc, dc, dTc = o.adjoint(fpost, hpost, 6, (2, 6), ("surface", 0, 1.0), nwalls=2)
+    p.hkind = O.KINDS["trt"]
+    o2, _, _ = _setup(w, p, Tw)
+    Jt, dt, dTt = o2.adjoint(fpost, hpost, 6, (2, 6), ("surface", 0, 1.0), nwalls=2)
+    assert abs(Jc - Jt) < 1e-13 * abs(Jt)
+    assert np.abs(dc - dt).max() < 1e-12 * np.abs(dt).max()
+    assert np.abs(dTc - dTt).max() < 1e-12 * np.abs(dTt).max()
 
 
 def test_objective_value_matches_surface_flux():
