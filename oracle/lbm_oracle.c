@@ -429,8 +429,15 @@ static void collide_h(const orc_params* p, const double* h, const double u[3], d
     solve(n, T, Ys, hs);
 }
 
+/* index of the velocity of lattice L with the y component reversed */
+static int flip_y(const lattice_t* L, int a) {
+    for (int b = 0; b < L->Q; ++b)
+        if (L->e[b][0] == L->e[a][0] && L->e[b][1] == -L->e[a][1] && L->e[b][2] == L->e[a][2]) return b;
+    return a;
+}
+
 /* ---- simulation state ---- */
-enum { FL_FLUID = 0, FL_SOLID = 1, FL_INLET = 2, FL_OUTLET = 3 };
+enum { FL_FLUID = 0, FL_SOLID = 1, FL_INLET = 2, FL_OUTLET = 3, FL_MIRROR = 4 };
 
 typedef struct {
     orc_params p;
@@ -441,7 +448,9 @@ typedef struct {
     double* hs;
     double* fn;     /* streaming target */
     double* hn;
-    uint8_t* flags;
+    uint8_t* flags;   /* mirror nodes are kept as FL_SOLID here, see mirror */
+    int* mirror;      /* per node: the node it mirrors (symmetry row), or -1 */
+    int has_mirror;
     float* qtab;    /* [N*27], -1 where no wall link */
     int* wtab;      /* [N*27], wall id of the link */
     double* Twall;  /* per wall id */
@@ -477,6 +486,8 @@ orc_sim* orc_create(const orc_params* p) {
     s->hs = (double*)calloc((size_t)p->qh * N, sizeof(double));
     s->hn = (double*)calloc((size_t)p->qh * N, sizeof(double));
     s->flags = (uint8_t*)calloc(N, 1);
+    s->mirror = (int*)malloc(N * sizeof(int));
+    for (size_t i = 0; i < N; ++i) s->mirror[i] = -1;
     s->qtab = (float*)malloc(27 * N * sizeof(float));
     s->wtab = (int*)calloc(27 * N, sizeof(int));
     for (size_t i = 0; i < 27 * N; ++i) s->qtab[i] = -1.0f;
@@ -488,23 +499,39 @@ orc_sim* orc_create(const orc_params* p) {
 void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->f); free(s->fs); free(s->fn); free(s->h); free(s->hs); free(s->hn);
-    free(s->flags); free(s->qtab); free(s->wtab); free(s->Twall); free(s->theta);
+    free(s->flags); free(s->mirror); free(s->qtab); free(s->wtab); free(s->Twall); free(s->theta);
     free(s);
 }
 
-/* Geometry: flags (0 fluid, 1 solid, 2 inlet, 3 outlet) and the wall links
- * (node x_b, direction a with x_b + e_a solid, q in (0,1], wall id).
+/* Geometry: flags (0 fluid, 1 solid, 2 inlet, 3 outlet, 4 symmetry row) and
+ * the wall links (node x_b, direction a with x_b + e_a solid, q in (0,1],
+ * wall id).  Symmetry rows (the symmetry planes of Sec. 4.4, reading R15)
+ * are the whole rows y = 0 and / or y = ny - 1; each of their nodes mirrors
+ * the node next to it in y (y = 1 or y = ny - 2), which must not be solid.
  * Returns 0, or a negative code naming the first rule broken:
  *  -1 flag out of range, -2 inlet/outlet planes wrong, -3 link node not
  *  fluid, -4 link target not solid, -5 q outside (0,1], -6 duplicate link,
  *  -7 fluid->solid link missing, -8 solid adjacent to the outlet plane,
- *  -9 wall id out of range. */
+ *  -9 wall id out of range, -10 symmetry rows wrong (or a wall link from a
+ *  node next to one). */
 int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* lnode,
                      const int* ldir, const float* lq, const int* lwall, int nwalls) {
-    const int N = s->N, nx = s->p.nx;
+    const int N = s->N, nx = s->p.nx, ny = s->p.ny;
     for (int n = 0; n < N; ++n) {
-        if (flags[n] > 3) return -1;
-        int x = n % nx;
+        if (flags[n] > 4) return -1;
+        int x = n % nx, y = (n / nx) % ny;
+        if (flags[n] == FL_MIRROR) {
+            if (ny < 3 || (y != 0 && y != ny - 1)) return -10;
+            int src = n + (y == 0 ? nx : -nx);
+            if (flags[src] == FL_SOLID || flags[src] == FL_MIRROR) return -10;
+            continue;
+        }
+        if ((y == 0 || y == ny - 1) && ny >= 3) {
+            /* a symmetry row is whole */
+            int other = n - x;
+            for (int xx = 0; xx < nx; ++xx)
+                if (flags[other + xx] == FL_MIRROR) return -10;
+        }
         if (s->p.periodic_x) {
             if (flags[n] == FL_INLET || flags[n] == FL_OUTLET) return -2;
         } else {
@@ -513,13 +540,28 @@ int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* ln
             if (x == nx - 2 && flags[n] == FL_SOLID) return -8;
         }
     }
+    s->has_mirror = 0;
+    for (int n = 0; n < N; ++n) {
+        int y = (n / nx) % ny;
+        s->mirror[n] = -1;
+        if (flags[n] == FL_MIRROR) {
+            s->mirror[n] = n + (y == 0 ? nx : -nx);
+            s->has_mirror = 1;
+        }
+    }
     memcpy(s->flags, flags, (size_t)N);
+    for (int n = 0; n < N; ++n)
+        if (s->flags[n] == FL_MIRROR) s->flags[n] = FL_SOLID;
     for (size_t i = 0; i < 27 * (size_t)N; ++i) { s->qtab[i] = -1.0f; s->wtab[i] = 0; }
     const lattice_t* L = lattice(27);
     for (int l = 0; l < nlinks; ++l) {
         int n = lnode[l], a = ldir[l];
         if (n < 0 || n >= N || a < 0 || a >= 27) return -3;
         if (flags[n] != FL_FLUID) return -3;
+        if (s->has_mirror) { /* solid bodies keep off the symmetry rows' neighbours */
+            int y = (n / nx) % ny;
+            if ((y == 1 && s->mirror[n - nx] >= 0) || (y == ny - 2 && s->mirror[n + nx] >= 0)) return -10;
+        }
         int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
         if (t < 0 || flags[t] != FL_SOLID) return -4;
         if (!(lq[l] > 0.0f && lq[l] <= 1.0f)) return -5;
@@ -529,7 +571,7 @@ int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* ln
         s->wtab[(size_t)n * 27 + a] = lwall[l];
     }
     for (int n = 0; n < N; ++n) {
-        if (flags[n] == FL_SOLID) continue;
+        if (flags[n] == FL_SOLID || flags[n] == FL_MIRROR) continue;
         for (int a = 1; a < 27; ++a) {
             int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
             if (t >= 0 && flags[t] == FL_SOLID) {
@@ -671,8 +713,22 @@ int orc_stream(orc_sim* s) {
     const lattice_t* Lh = lattice(qh);
     for (size_t i = 0; i < 27 * (size_t)N; ++i) s->fn[i] = NAN;
     for (size_t i = 0; i < (size_t)qh * N; ++i) s->hn[i] = NAN;
+    /* symmetry rows (reading R15): specular reflection at the plane halfway
+     * between a symmetry row and its neighbour row.  Each symmetry node takes
+     * the post-collision populations of the node it mirrors with e_y
+     * reversed and pushes them like any node; what arrives there is unused. */
+    if (s->has_mirror) {
+        for (int n = 0; n < N; ++n) {
+            int m = s->mirror[n];
+            if (m < 0) continue;
+            for (int a = 0; a < 27; ++a)
+                s->fs[(size_t)a * N + n] = s->fs[(size_t)flip_y(L, a) * N + m];
+            for (int a = 0; a < qh; ++a)
+                s->hs[(size_t)a * N + n] = s->hs[(size_t)flip_y(Lh, a) * N + m];
+        }
+    }
     for (int n = 0; n < N; ++n) {
-        if (s->flags[n] == FL_SOLID) continue;
+        if (s->flags[n] == FL_SOLID && s->mirror[n] < 0) continue;
         for (int a = 0; a < 27; ++a) {
             int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
             if (t < 0 || s->flags[t] == FL_SOLID) continue;
@@ -738,6 +794,10 @@ int orc_stream(orc_sim* s) {
         if (s->flags[n] == FL_SOLID) {
             for (int a = 0; a < 27; ++a) s->fn[(size_t)a * N + n] = 0.0;
             for (int a = 0; a < qh; ++a) s->hn[(size_t)a * N + n] = 0.0;
+            if (s->mirror[n] >= 0) { /* a symmetry node holds no state of its own */
+                for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = 0.0;
+                for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = 0.0;
+            }
             continue;
         }
         for (int a = 0; a < 27; ++a) missing += isnan(s->fn[(size_t)a * N + n]) ? 1 : 0;
@@ -1047,7 +1107,8 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
 /* Forward run from the post-collision state (f_post, h_post) = s^0 over
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
- * dJ/dT_w[nwalls] to them.  Returns 0, or -1 on a streaming error.
+ * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, or -3 for a
+ * geometry with symmetry rows (their transpose is not built).
  * The Cumulants-1st collision is not affine in h: for that kind the forward
  * keeps the pre-collision h of every level and the reverse sweep applies the
  * transpose of the collision's Jacobian there (cum_jacobian); streaming and
@@ -1057,6 +1118,7 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
     const int cum = s->p.hkind == KIND_CUM1;
+    if (dtheta && s->has_mirror) return -3; /* the transpose of the symmetry rows is not built */
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
     double* hrec = (dtheta && cum) ? (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double)) : NULL;
     orc_set_post(s, f_post, h_post);

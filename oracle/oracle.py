@@ -289,5 +289,5 @@ class Oracle:
                                int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
                                dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
         if rc != 0:
-            raise OracleError("orc_adjoint: streaming error")
+            raise OracleError("orc_adjoint: " + ("no adjoint with symmetry rows" if rc == -3 else "streaming error"))
         return J.value, dth, dTw

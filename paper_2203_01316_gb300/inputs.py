@@ -28,7 +28,7 @@ E27 = np.array([
     [0, 0, 0, 1, 0, 1, 1, 0, 0, -1, 0, -1, 0, 1, -1, 1, 1, 0, -1, -1, 1, 1, -1, -1, -1, 1, -1],
 ], dtype=np.int64).T
 
-FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+FLUID, SOLID, INLET, OUTLET, MIRROR = 0, 1, 2, 3, 4
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -305,3 +305,62 @@ def gaussian_hill(L=256, sigma0_sq=100.0, C0=1.0, T0=1.0):
     N = L * L
     return {"dims": (L, L, 1), "flags": np.zeros(N, np.uint8), "links": _empty_links(), "rho": np.ones(N),
             "u": np.zeros((3, N)), "T": (T0 + C).reshape(-1), "periodic_x": True, "nwalls": 1}
+
+
+def confined_cylinder(S=1, xc=None, seed=None, U=None, T_in=10.0, T_cyl=11.0):
+    """Sec. 4.4 confined cylinder: a channel of L = 1000 S by H = 150 S nodes
+    between two symmetry planes (rows y = 0 and y = ny - 1 are symmetry rows,
+    so ny = H + 2 and the planes lie H apart), nz = 1; cylinder of diameter
+    D = 30 S centred on the channel axis at x = xc (default L/5, a reading);
+    inlet plane x = 0 at u = (U, 0, 0) with U = 0.01/S and T_in = 10, outlet
+    x = L - 1; cylinder wall 0 at T_cyl = 11.  q from the exact crossing of
+    the circle (2-D); a seeded sub-node offset of the centre when seed is
+    given."""
+    L, H, D = int(round(1000 * S)), int(round(150 * S)), 30.0 * S
+    nx, ny = L, H + 2
+    if xc is None:
+        xc = L / 5.0
+    c = np.array([float(xc), (ny - 1) / 2.0])
+    if seed is not None:
+        c += uniform(seed, 2, -0.5, 0.5)
+    R = D / 2.0
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2
+    flags = np.where(r2 <= R * R, SOLID, FLUID).astype(np.uint8)
+    flags[:, 0] = INLET
+    flags[:, nx - 1] = OUTLET
+    flags[0, :] = MIRROR
+    flags[ny - 1, :] = MIRROR
+    fl = flags == FLUID
+    Xb, Yb = x[fl], y[fl]
+    nodes, dirs, qs = [], [], []
+    for a in range(1, 27):
+        ex, ey, _ = E27[a]
+        if ex == 0 and ey == 0:
+            continue
+        Xt, Yt = Xb + ex, Yb + ey
+        ok = (Xt >= 0) & (Xt < nx) & (Yt >= 0) & (Yt < ny)
+        hit = np.zeros(len(Xb), bool)
+        hit[ok] = flags[Yt[ok], Xt[ok]] == SOLID
+        if not hit.any():
+            continue
+        dx, dy = Xb[hit] - c[0], Yb[hit] - c[1]
+        ee = float(ex * ex + ey * ey)
+        de = dx * ex + dy * ey
+        dd = dx * dx + dy * dy
+        disc = np.maximum(de * de - ee * (dd - R * R), 0.0)
+        t = np.clip((-de - np.sqrt(disc)) / ee, np.nextafter(0.0, 1.0), 1.0)
+        nodes.append(node_index(Xb[hit], Yb[hit], 0, nx, ny))
+        dirs.append(np.full(int(hit.sum()), a))
+        qs.append(t.astype(np.float32))
+    links = _sort_links(np.concatenate(nodes), np.concatenate(dirs), np.concatenate(qs),
+                        np.zeros(sum(len(v) for v in nodes), np.int64))
+    N = nx * ny
+    if U is None:
+        U = 0.01 / S
+    u = np.zeros((3, N))
+    u[0] = np.where(flags.reshape(-1) == SOLID, 0.0, U)
+    return {"dims": (nx, ny, 1), "flags": flags.reshape(-1), "links": links, "rho": np.ones(N), "u": u,
+            "T": np.full(N, T_in), "periodic_x": False, "nwalls": 1, "u_in": (U, 0.0, 0.0), "T_in": T_in,
+            "T_cyl": T_cyl, "D": D, "H": H, "centre": c, "S": S,
+            "sections": (int(round(50 * S)), nx - 1 - int(round(100 * S)))}
