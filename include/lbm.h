@@ -191,14 +191,17 @@ lbm_status lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes, int is_device)
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes, int is_device);
 
 /* ---- adjoint of the h evolution -------------------------------------------
- * One-way coupling (Sec. 2: h does not act on f) makes the h step affine in
+ * One-way coupling (Sec. 2: h does not act on f) fixes the velocity field of
+ * the h evolution.  For the central-moment kinds the h step is then affine in
  * the h state, the per-node source Q (App. D) and the wall temperatures
- * (Eq. IABB), with the velocity field fixed:
+ * (Eq. IABB):
  *     g^{k+1} = P s^k + b(T_w),   s^{k+1} = L(u^{k+1}) g^{k+1} + e(u^{k+1}) Q
  * (s^k: post-collision h of level k, g: arrivals after streaming and walls,
- * L, e from Eq. H_cm_collision).  An objective is a linear flux F of s^k
- * summed with a weight over a window of levels; the adjoint runs the
- * transposed steps backwards.  Velocity records, adjoint arrays: element type
+ * L, e from Eq. H_cm_collision).  The Cumulants-1st collision is nonlinear in
+ * g; its adjoint uses the Jacobian at recorded states (lbm_step_record_h,
+ * lbm_adjoint_step_h).  An objective is a linear flux F of s^k summed with a
+ * weight over a window of levels; the adjoint runs the transposed steps
+ * backwards.  Velocity records, adjoint arrays: element type
  * float, or double for LBM_F64 contexts; SoA [3][N] and [Q_h][N]. */
 typedef enum { LBM_OBJ_SURFACE_FLUX = 0, LBM_OBJ_SECTION_FLUX = 1 } lbm_objective_kind;
 typedef struct {
@@ -217,6 +220,13 @@ lbm_status lbm_objective_accumulate(lbm_ctx* ctx, const lbm_objective* obj, doub
  * recomputation of the adjoint needs no h). */
 lbm_status lbm_step_record(lbm_ctx* ctx, int n, void* u_rec, int advance_h);
 
+/* lbm_step_record with advance_h = 1 that also copies, for each step
+ * k = 1..n, the post-collision h of every node as deviations h* - w T_ref to
+ * h_rec + (k-1)*Q_h*N (device, SoA [Q_h][N], element type as for u_rec).
+ * The Cumulants-1st collision (Eq. H_cu_collision) is not linear in h, so its
+ * adjoint needs these records (lbm_adjoint_step_h); solid nodes hold zeros. */
+lbm_status lbm_step_record_h(lbm_ctx* ctx, int n, void* u_rec, void* h_rec);
+
 /* One level of the adjoint sweep.  mu_next: adjoint of the arrivals of level
  * k+1 (zeros at the last level).  Computes lambda^k = P^T mu_next + dJ/ds^k
  * (obj: the objective term of level k, NULL when level k is outside the
@@ -230,6 +240,17 @@ lbm_status lbm_step_record(lbm_ctx* ctx, int n, void* u_rec, int advance_h);
  * Asynchronous. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_next, void* out,
                             const lbm_objective* obj, double* dJ_dtheta);
+
+/* lbm_adjoint_step for every h kind, given also h_level, the level's
+ * post-collision h record from lbm_step_record_h (ignored by the
+ * central-moment kinds, may be NULL there and at the initial level).  For
+ * Cumulants-1st the level's collision is h* = (H + Q) M(v), M the unit
+ * equilibrium at v = (1 - s^H) m + s^H u, m = sum e h / H (Eq. H_cu_collision
+ * with every cumulant of order >= 2 at equilibrium, App. D source), and the
+ * call applies the transpose of its Jacobian at the recorded state.
+ * lbm_adjoint_step itself returns LBM_ERR_INVALID for that kind. */
+lbm_status lbm_adjoint_step_h(lbm_ctx* ctx, const void* u_level, const void* h_level, const void* mu_next, void* out,
+                              const lbm_objective* obj, double* dJ_dtheta);
 
 /* dJ/dT_w accumulated by lbm_adjoint_step since the last reset, per wall
  * (host double[n_walls]); reset = 1 clears the accumulators.  Synchronises. */

@@ -9,9 +9,11 @@ steps from a saved state s^0.
 
 Forward: runs the steps, keeping a device checkpoint of the state every
 `every` steps.  Backward: for each segment, last first, restores its
-checkpoint, recomputes the velocity of every level of the segment (f only;
-h is affine and its adjoint needs only u), then runs the adjoint kernel
-level by level.  All arithmetic runs in the CUDA library; this module only
+checkpoint, recomputes the velocity of every level of the segment, then runs
+the adjoint kernel level by level.  For the central-moment kinds the h step
+is affine and its adjoint needs only u, so the recomputation advances f only;
+the Cumulants-1st collision is nonlinear in h, so there the recomputation
+advances h as well and keeps each level's post-collision h for the adjoint.  All arithmetic runs in the CUDA library; this module only
 orders the calls and owns the device buffers (torch tensors).
 """
 from __future__ import annotations
@@ -69,11 +71,14 @@ class ThermalObjective(torch.autograd.Function):
             L = seg_end - seg_start
             s.load_state(ctx.ckpts[seg_start])
             urec = torch.empty(L * 3 * N, dtype=rdt, device=dev)
-            s.step_record(L, urec, advance_h=False)
+            hrec = torch.empty(L * qh * N, dtype=rdt, device=dev) if s.cumulant_h else None
+            s.step_record(L, urec, advance_h=False, h_rec=hrec)
             for k in range(seg_end, seg_start, -1):
                 obj = ctx.objective if lo <= k <= hi else None
-                u_k = urec[(k - seg_start - 1) * 3 * N:(k - seg_start) * 3 * N]
-                s.adjoint_step(u_k, mu_next, mu_out, obj, dtheta)
+                j = k - seg_start - 1
+                u_k = urec[j * 3 * N:(j + 1) * 3 * N]
+                h_k = hrec[j * qh * N:(j + 1) * qh * N] if hrec is not None else None
+                s.adjoint_step(u_k, mu_next, mu_out, obj, dtheta, h_level=h_k)
                 mu_next, mu_out = mu_out, mu_next
         # level 0: the initial state is given; only its objective and wall terms remain
         obj0 = ctx.objective if lo <= 0 <= hi else None

@@ -974,12 +974,35 @@ lbm_status lbm_step_record(lbm_ctx* c, int n, void* u_rec, int advance_h) {
     return LBM_OK;
 }
 
-lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next, void* out,
-                            const lbm_objective* obj, double* dJ_dtheta) {
+lbm_status lbm_step_record_h(lbm_ctx* c, int n, void* u_rec, void* h_rec) {
+    if (!c) return LBM_ERR_INVALID;
+    if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
+    if (n > 0 && (!u_rec || !h_rec)) return fail(c, LBM_ERR_INVALID, "null velocity or h record");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    DeviceGuard g(c->device);
+    const size_t rsize = c->p.storage == LBM_F64 ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < n; ++i) {
+        lbm_status st = lbm_step_record(c, 1, (char*)u_rec + (size_t)i * 3 * c->N * rsize, 1);
+        if (st != LBM_OK) return st;
+        const Buffers b = buffers(c);
+        const DevParams p = c->dp;
+        void* rec = (char*)h_rec + (size_t)i * c->qh * c->N * rsize;
+        cudaError_t e = dispatch(c, [&](auto tag) {
+            using Tg = decltype(tag);
+            return lbmd::launch_record_h<typename Tg::S, Tg::Q>(b, p, rec, c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "h record launch");
+    }
+    return LBM_OK;
+}
+
+static lbm_status adjoint_step_impl(lbm_ctx* c, const void* u_level, const void* h_level, const void* mu_next,
+                                    void* out, const lbm_objective* obj, double* dJ_dtheta) {
     if (!c || !mu_next || !out) return LBM_ERR_INVALID;
     if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
-    if (c->p.hkind == LBM_H_CUM_1ST)
-        return fail(c, LBM_ERR_INVALID, "the adjoint covers the central-moment kinds (affine h step) only");
+    if (c->p.hkind == LBM_H_CUM_1ST && u_level && !h_level)
+        return fail(c, LBM_ERR_INVALID,
+                    "the Cumulants-1st adjoint needs the level's h record (lbm_step_record_h, lbm_adjoint_step_h)");
     lbm_status st = check_objective(c, obj);
     if (st != LBM_OK) return st;
     DeviceGuard g(c->device);
@@ -988,18 +1011,30 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next
     const lbmd::AdjObjective a = to_adj(obj);
     cudaError_t e;
     if (c->p.storage == LBM_F64) {
-        e = c->qh == 27 ? lbmd::launch_adjoint<double, 27>(b, p, (const double*)u_level, (const double*)mu_next,
-                                                          (double*)out, a, dJ_dtheta, c->stream)
-                        : lbmd::launch_adjoint<double, 7>(b, p, (const double*)u_level, (const double*)mu_next,
-                                                         (double*)out, a, dJ_dtheta, c->stream);
+        using R = double;
+        e = c->qh == 27 ? lbmd::launch_adjoint<R, 27>(b, p, (const R*)u_level, (const R*)h_level, (const R*)mu_next,
+                                                     (R*)out, a, dJ_dtheta, c->stream)
+                        : lbmd::launch_adjoint<R, 7>(b, p, (const R*)u_level, (const R*)h_level, (const R*)mu_next,
+                                                    (R*)out, a, dJ_dtheta, c->stream);
     } else {
-        e = c->qh == 27 ? lbmd::launch_adjoint<float, 27>(b, p, (const float*)u_level, (const float*)mu_next,
-                                                         (float*)out, a, dJ_dtheta, c->stream)
-                        : lbmd::launch_adjoint<float, 7>(b, p, (const float*)u_level, (const float*)mu_next,
-                                                        (float*)out, a, dJ_dtheta, c->stream);
+        using R = float;
+        e = c->qh == 27 ? lbmd::launch_adjoint<R, 27>(b, p, (const R*)u_level, (const R*)h_level, (const R*)mu_next,
+                                                     (R*)out, a, dJ_dtheta, c->stream)
+                        : lbmd::launch_adjoint<R, 7>(b, p, (const R*)u_level, (const R*)h_level, (const R*)mu_next,
+                                                    (R*)out, a, dJ_dtheta, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
     return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next, void* out,
+                            const lbm_objective* obj, double* dJ_dtheta) {
+    return adjoint_step_impl(c, u_level, nullptr, mu_next, out, obj, dJ_dtheta);
+}
+
+lbm_status lbm_adjoint_step_h(lbm_ctx* c, const void* u_level, const void* h_level, const void* mu_next, void* out,
+                              const lbm_objective* obj, double* dJ_dtheta) {
+    return adjoint_step_impl(c, u_level, h_level, mu_next, out, obj, dJ_dtheta);
 }
 
 lbm_status lbm_adjoint_wall_gradient(lbm_ctx* c, double* dJ_dTwall, int reset) {

@@ -393,7 +393,7 @@ __device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const D
 }
 
 template <typename R, int QH>
-__device__ __forceinline__ void heq_dev(R* hd, R psi, R ux, R uy, R uz, const DevParams& p);
+__device__ __forceinline__ void heq_dev(R* hd, R dpsi, R ux, R uy, R uz, const DevParams& p);
 
 // ---- h: Cumulants-1st (Eq. H_cu_collision + App. D source) -----------------
 // With every cumulant of order >= 2 set to its equilibrium (c_s^2 on the
@@ -416,10 +416,11 @@ __device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, cons
     const R Ht = (R)p.Tref + dH;  // zeroth moment of the stored (App. D shifted) h
     const R iH = R(1) / Ht;
     const R s = (R)p.sh[1];
-    const R vx = jx * iH + s * (ux - jx * iH);
-    const R vy = jy * iH + s * (uy - jy * iH);
-    const R vz = jz * iH + s * (uz - jz * iH);
-    heq_dev<R, QH>(hd, Ht + Q, vx, vy, vz, p);
+    // v = u + (1 - s)(m - u): exactly u at s = 1
+    const R vx = ux + (R(1) - s) * (jx * iH - ux);
+    const R vy = uy + (R(1) - s) * (jy * iH - uy);
+    const R vz = uz + (R(1) - s) * (jz * iH - uz);
+    heq_dev<R, QH>(hd, dH + Q, vx, vy, vz, p);
 }
 
 // CUM: the Cumulants-1st kind (compile time, so the central-moment kinds
@@ -436,11 +437,11 @@ __device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const De
 }
 
 // ---- equilibria in deviation form ------------------------------------------
-// f^eq(rho, u) - w rho0: central moments about u are (rho - rho0) E + rho0 D(u)
+// f^eq(rho0 + drho, u) - w rho0: central moments about u are drho E + rho0 D(u)
+// (the density enters as its deviation, like heq_dev's zeroth moment)
 template <typename R>
-__device__ __forceinline__ void feq_dev(R* fd, R rho, R ux, R uy, R uz, const DevParams& p) {
+__device__ __forceinline__ void feq_dev(R* fd, R drho, R ux, R uy, R uz, const DevParams& p) {
     const R rho0 = (R)p.rho0;
-    const R drho = rho - rho0;
     const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
     R cb[27];
 #pragma unroll
@@ -455,11 +456,11 @@ __device__ __forceinline__ void feq_dev(R* fd, R rho, R ux, R uy, R uz, const De
     for (int a = 0; a < 27; ++a) fd[a] = cb[CUBE(a)];
 }
 
-// h^eq(psi, u) - w Tref on the h lattice
+// h^eq(Tref + dpsi, u) - w Tref on the h lattice; the zeroth moment enters as
+// its deviation dpsi, so no Tref is added and subtracted again in FP32
 template <typename R, int QH>
-__device__ __forceinline__ void heq_dev(R* hd, R psi, R ux, R uy, R uz, const DevParams& p) {
+__device__ __forceinline__ void heq_dev(R* hd, R dpsi, R ux, R uy, R uz, const DevParams& p) {
     const R Tref = (R)p.Tref;
-    const R dpsi = psi - Tref;
     if constexpr (QH == 27) {
         const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
         R cb[27];

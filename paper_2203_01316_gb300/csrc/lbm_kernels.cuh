@@ -67,10 +67,14 @@ template <typename S, int QH> bool staged_eligible(const DevParams& p) {
 // b.urec non-null records the velocity u used by each node's collision
 template <typename S, int QH>
 cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h = true);
-// adjoint of one level of the h evolution (R = float, or double for FP64 storage)
+// adjoint of one level of the h evolution (R = float, or double for FP64
+// storage); h_level: the level's post-collision h record (Cumulants-1st only)
 template <typename R, int QH>
-cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* mu_next, R* mu_out,
-                           AdjObjective obj, double* dtheta, cudaStream_t s);
+cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* h_level,
+                           const R* mu_next, R* mu_out, AdjObjective obj, double* dtheta, cudaStream_t s);
+// rec[i * N + n] = post-collision h deviation of population i at node n (type R)
+template <typename S, int QH>
+cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s);
 // *acc += weight * F(current level) (F: surface flux of a wall or section flux of a plane)
 template <typename S, int QH>
 cudaError_t launch_objective(const Buffers& b, const DevParams& p, AdjObjective obj, double* scratch, double* acc,
@@ -156,7 +160,22 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
                                                 typename Acc<S>::R uy, typename Acc<S>::R uz,
                                                 typename Acc<S>::R Q) {
     using R = typename Acc<S>::R;
-    collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
+    if constexpr (sizeof(R) == 4) {
+        // FP32 arithmetic: the transforms' roundings bias the zeroth moment of
+        // the result (a steady energy drift over long runs at small k), so
+        // the rest population takes exactly what the others leave of the
+        // pre-collision zeroth moment plus the source
+        R pre = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) pre += hd[i];
+        collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
+        R others = R(0);
+#pragma unroll
+        for (int i = 1; i < QH; ++i) others += hd[i];
+        hd[0] = (pre + Q) - others;
+    } else {
+        collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
+    }
     if (sizeof(S) == 2 && p.stochastic) {
         SrStream rs{sr_bits(((uint32_t)n << 1) | 1u, p.step)};
 #pragma unroll
@@ -601,14 +620,13 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restri
         for (int i = 0; i < QH; ++i) st(hB + (size_t)i * p.N + n, inlet[27 + i]);
         return;
     }
-    const R r = (R)rho[n];
     const R vx = (R)u[n], vy = (R)u[(size_t)p.N + n], vz = (R)u[2 * (size_t)p.N + n];
     const R Q = theta ? (R)theta[n] : R(0);
     R fd[27];
-    feq_dev<R>(fd, r, vx, vy, vz, p);
+    feq_dev<R>(fd, (R)(rho[n] - p.rho0), vx, vy, vz, p);
     // h = h^eq(rho T, u) - q/2 with q = h^eq(Q, u): one equilibrium at rho T - Q/2
     R hd[QH];
-    heq_dev<R, QH>(hd, r * (R)T[n] - R(0.5) * Q, vx, vy, vz, p);
+    heq_dev<R, QH>(hd, (R)(rho[n] * T[n] - p.Tref) - R(0.5) * Q, vx, vy, vz, p);
     R ux, uy, uz;
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
     collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
@@ -888,9 +906,10 @@ __device__ __forceinline__ void iabb_partials(float q, bool thin, int wall_bc, R
     }
 }
 
-template <typename R, int QH>
+template <typename R, int QH, bool CUM = false>
 __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_next, R* __restrict__ out,
-                                                     const R* __restrict__ uk, double* __restrict__ dtheta,
+                                                     const R* __restrict__ uk, const R* __restrict__ hk,
+                                                     const float* __restrict__ theta, double* __restrict__ dtheta,
                                                      const uint8_t* __restrict__ flags,
                                                      const int32_t* __restrict__ seg_base,
                                                      const uint32_t* __restrict__ wmask,
@@ -999,7 +1018,77 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     }
     const R ux = uk[n], uy = uk[N + n], uz = uk[2 * N + n];
     double dth = 0.0;
-    if constexpr (QH == 27) {
+    if constexpr (CUM) {
+        // Cumulants-1st (Eq. H_cu_collision): s^k = (H + Q) M(v), M the unit
+        // equilibrium at v = (1 - s) m + s u, m = sum e g / H, H = sum g of the
+        // arrivals g.  From the recorded s^k: A = H + Q = sum s^k and
+        // v = sum e s^k / A, and (1 - s) m = v - s u.  The transposed Jacobian
+        //   mu_b = L0 + A/H sum_d ((1 - s) e_bd - (v_d - s u_d)) G_d,
+        //   L0 = sum_a lambda_a M_a(v),  G_d = sum_a lambda_a dM_a/dv_d,
+        // and dJ/dQ += L0.
+        R A = (R)p.Tref, jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            const R g = hk[i * N + n];
+            A += g;
+            if (EX(a) != 0) jx += EX(a) * g;
+            if (EY(a) != 0) jy += EY(a) * g;
+            if (EZ(a) != 0) jz += EZ(a) * g;
+        }
+        const R Q = theta ? (R)__ldg(theta + n) : R(0);
+        const R iA = R(1) / A;
+        const R v[3] = {jx * iA, jy * iA, jz * iA};
+        const R u[3] = {ux, uy, uz};
+        const R c = cs2<R>();
+        // per axis: unit-equilibrium factors and their v-derivatives at c = -1, 0, +1
+        R W[3][3], D[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R a2 = c + v[d] * v[d];
+            W[d][0] = R(0.5) * (a2 - v[d]);
+            W[d][1] = R(1) - a2;
+            W[d][2] = R(0.5) * (a2 + v[d]);
+            D[d][0] = v[d] - R(0.5);
+            D[d][1] = R(-2) * v[d];
+            D[d][2] = v[d] + R(0.5);
+        }
+        R L0 = R(0), G[3] = {R(0), R(0), R(0)};
+        if constexpr (QH == 27) {
+#pragma unroll
+            for (int a = 0; a < 27; ++a) {
+                const int cx = EX(a) + 1, cy = EY(a) + 1, cz = EZ(a) + 1;
+                const R l = lam[a];
+                L0 += l * W[0][cx] * W[1][cy] * W[2][cz];
+                G[0] += l * D[0][cx] * W[1][cy] * W[2][cz];
+                G[1] += l * W[0][cx] * D[1][cy] * W[2][cz];
+                G[2] += l * W[0][cx] * W[1][cy] * D[2][cz];
+            }
+        } else {
+            // D3Q7 unit equilibrium: rest 1 - sum_d a2_d, arms (a2_d +- v_d) / 2
+            R rest = R(1);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) rest -= c + v[d] * v[d];
+            L0 = lam[0] * rest;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                L0 += lam[1 + d] * W[d][2] + lam[4 + d] * W[d][0];
+                G[d] = lam[0] * D[d][1] + lam[1 + d] * D[d][2] + lam[4 + d] * D[d][0];
+            }
+        }
+        const R s = (R)p.sh[1];
+        const R kap = A / (A - Q);
+        R base = L0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) base -= kap * (v[d] - s * u[d]) * G[d];
+        const R c1 = kap * (R(1) - s);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            out[i * N + n] = base + c1 * (EX(a) * G[0] + EY(a) * G[1] + EZ(a) * G[2]);
+        }
+        dth = (double)L0;
+    } else if constexpr (QH == 27) {
         R cb[27];
 #pragma unroll
         for (int a = 0; a < 27; ++a) cb[CUBE(a)] = lam[a];
@@ -1079,11 +1168,32 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
 }
 
 template <typename R, int QH>
-cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* mu_next, R* mu_out,
-                           AdjObjective obj, double* dtheta, cudaStream_t s) {
+cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* h_level,
+                           const R* mu_next, R* mu_out, AdjObjective obj, double* dtheta, cudaStream_t s) {
     const int grid = (p.N + kBlock - 1) / kBlock;
-    k_adjoint<R, QH><<<grid, kBlock, 0, s>>>(mu_next, mu_out, u_level, dtheta, b.flags, b.seg_base, b.wmask, b.woff,
-                                             b.lq, b.lwall, b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p);
+#define LBM_ADJ_ARGS                                                                                             \
+    mu_next, mu_out, u_level, h_level, b.theta, dtheta, b.flags, b.seg_base, b.wmask, b.woff, b.lq, b.lwall,    \
+        b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p
+    if (p.hkind == 3) k_adjoint<R, QH, true><<<grid, kBlock, 0, s>>>(LBM_ADJ_ARGS);
+    else k_adjoint<R, QH, false><<<grid, kBlock, 0, s>>>(LBM_ADJ_ARGS);
+#undef LBM_ADJ_ARGS
+    return cudaGetLastError();
+}
+
+// copy of the post-collision h deviations (storage S) into an adjoint record
+template <typename S, int QH>
+__global__ void k_record_h(const S* __restrict__ hA, typename Acc<S>::R* __restrict__ rec, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)QH * p.N) return;
+    rec[i] = ld<R>(hA + i);
+}
+
+template <typename S, int QH>
+cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s) {
+    const size_t total = (size_t)QH * p.N;
+    const unsigned grid = (unsigned)((total + kBlock - 1) / kBlock);
+    k_record_h<S, QH><<<grid, kBlock, 0, s>>>((const S*)b.hA, (typename Acc<S>::R*)rec, p);
     return cudaGetLastError();
 }
 

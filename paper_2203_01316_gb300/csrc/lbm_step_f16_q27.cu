@@ -11,6 +11,7 @@ template cudaError_t launch_init<__half, 27>(const Buffers&, const DevParams&, c
 template cudaError_t launch_macros<__half, 27>(const Buffers&, const DevParams&, double*, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_populations<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_record_h<__half, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
 template cudaError_t launch_balances<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<__half, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

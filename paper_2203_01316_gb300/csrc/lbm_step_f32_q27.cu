@@ -11,12 +11,13 @@ template cudaError_t launch_init<float, 27>(const Buffers&, const DevParams&, co
 template cudaError_t launch_macros<float, 27>(const Buffers&, const DevParams&, double*, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_populations<float, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_record_h<float, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
 template cudaError_t launch_balances<float, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<float, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
 template cudaError_t launch_step_staged<float, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
-template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&, const float*, const float*, float*,
-                                           AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&, const float*, const float*,
+                                           const float*, float*, AdjObjective, double*, cudaStream_t);
 
 // streaming map of the step kernels (storage independent)
 __global__ void k_stream_map(const uint8_t* __restrict__ flags, const int32_t* __restrict__ wnode,

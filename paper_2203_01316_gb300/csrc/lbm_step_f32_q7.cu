@@ -11,10 +11,11 @@ template cudaError_t launch_init<float, 7>(const Buffers&, const DevParams&, con
 template cudaError_t launch_macros<float, 7>(const Buffers&, const DevParams&, double*, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_populations<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_record_h<float, 7>(const Buffers&, const DevParams&, void*, cudaStream_t);
 template cudaError_t launch_balances<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
 template cudaError_t launch_step_staged<float, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
-template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*, float*,
-                                           AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*,
+                                           const float*, float*, AdjObjective, double*, cudaStream_t);
 }  // namespace lbmd

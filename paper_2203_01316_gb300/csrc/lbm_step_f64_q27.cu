@@ -11,9 +11,10 @@ template cudaError_t launch_init<double, 27>(const Buffers&, const DevParams&, c
 template cudaError_t launch_macros<double, 27>(const Buffers&, const DevParams&, double*, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_populations<double, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_record_h<double, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
 template cudaError_t launch_balances<double, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<double, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
-template cudaError_t launch_adjoint<double, 27>(const Buffers&, const DevParams&, const double*, const double*, double*,
-                                           AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<double, 27>(const Buffers&, const DevParams&, const double*, const double*,
+                                           const double*, double*, AdjObjective, double*, cudaStream_t);
 }  // namespace lbmd

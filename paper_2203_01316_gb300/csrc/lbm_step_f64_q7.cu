@@ -11,9 +11,10 @@ template cudaError_t launch_init<double, 7>(const Buffers&, const DevParams&, co
 template cudaError_t launch_macros<double, 7>(const Buffers&, const DevParams&, double*, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_populations<double, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
+template cudaError_t launch_record_h<double, 7>(const Buffers&, const DevParams&, void*, cudaStream_t);
 template cudaError_t launch_balances<double, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<double, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
-template cudaError_t launch_adjoint<double, 7>(const Buffers&, const DevParams&, const double*, const double*, double*,
-                                           AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint<double, 7>(const Buffers&, const DevParams&, const double*, const double*,
+                                           const double*, double*, AdjObjective, double*, cudaStream_t);
 }  // namespace lbmd

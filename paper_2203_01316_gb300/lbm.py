@@ -25,7 +25,7 @@ SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_s
            "lbm_surface_flux", "lbm_nusselt", "lbm_state_size", "lbm_save_state", "lbm_load_state",
            "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
            "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
-           "lbm_adjoint_wall_gradient"]
+           "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h"]
 OBJ_SURFACE, OBJ_SECTION = 0, 1
 
 
@@ -89,6 +89,8 @@ def lib():
         "lbm_objective_accumulate": [vp, C.POINTER(Objective), vp],
         "lbm_step_record": [vp, i32, vp, i32],
         "lbm_adjoint_step": [vp, vp, vp, vp, C.POINTER(Objective), vp],
+        "lbm_step_record_h": [vp, i32, vp, vp],
+        "lbm_adjoint_step_h": [vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_adjoint_wall_gradient": [vp, C.POINTER(dbl), i32],
         "lbm_stream_map": [vp, vp, i32],
         "lbm_get_links": [vp, C.POINTER(i64), vp, vp, vp, vp],
@@ -159,6 +161,7 @@ class Solver:
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.N = p.nx * p.ny * p.nz
         self.qh = p.lat_h
+        self.cumulant_h = p.hkind == HKIND["cum1st"]
         h = C.c_void_p()
         st = self.L.lbm_create(C.byref(p), C.byref(h))
         if st != LBM_OK:
@@ -297,15 +300,27 @@ class Solver:
     def objective_accumulate(self, obj, J_device):
         self._check(self.L.lbm_objective_accumulate(self._h, C.byref(obj), J_device.data_ptr()))
 
-    def step_record(self, n, u_rec, advance_h=True):
+    def step_record(self, n, u_rec, advance_h=True, h_rec=None):
+        """n steps recording u per step into u_rec ([n, 3, N] device tensor);
+        with h_rec ([n, Q_h, N]) also the post-collision h deviations, which
+        the Cumulants-1st adjoint needs (advances h)."""
+        if h_rec is not None:
+            self._check(self.L.lbm_step_record_h(self._h, int(n), u_rec.data_ptr() if n > 0 else None,
+                                                 h_rec.data_ptr() if n > 0 else None))
+            return
         self._check(self.L.lbm_step_record(self._h, int(n), u_rec.data_ptr() if n > 0 else None,
                                            1 if advance_h else 0))
 
-    def adjoint_step(self, u_level, mu_next, out, obj=None, dtheta=None):
-        self._check(self.L.lbm_adjoint_step(self._h, u_level.data_ptr() if u_level is not None else None,
-                                            mu_next.data_ptr(), out.data_ptr(),
-                                            C.byref(obj) if obj is not None else None,
-                                            dtheta.data_ptr() if dtheta is not None else None))
+    def adjoint_step(self, u_level, mu_next, out, obj=None, dtheta=None, h_level=None):
+        """One reverse level; h_level (the level's h record) is required for
+        the Cumulants-1st kind and ignored by the central-moment kinds."""
+        args = (u_level.data_ptr() if u_level is not None else None, mu_next.data_ptr(), out.data_ptr(),
+                C.byref(obj) if obj is not None else None, dtheta.data_ptr() if dtheta is not None else None)
+        if h_level is not None or self.cumulant_h:
+            self._check(self.L.lbm_adjoint_step_h(self._h, args[0],
+                                                  h_level.data_ptr() if h_level is not None else None, *args[1:]))
+        else:
+            self._check(self.L.lbm_adjoint_step(self._h, *args))
 
     def adjoint_wall_gradient(self, n_walls, reset=True):
         g = (C.c_double * n_walls)()

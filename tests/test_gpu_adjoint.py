@@ -78,6 +78,10 @@ def _channel():
     ("plate", 27, "trt", ("surface", 0, 1.0), "abb"),
     ("channel", 27, "trt", ("surface", 0, 1.0), "iabb"),
     ("channel", 7, "srt", ("section", 17, 1.0), "iabb"),
+    ("plate", 27, "cum1st", ("surface", 1, 0.9), "iabb"),
+    ("plate", 7, "cum1st", ("section", 4, 1.0), "iabb"),
+    ("channel", 27, "cum1st", ("surface", 0, 1.0), "iabb"),
+    ("plate", 27, "cum1st", ("surface", 0, 1.0), "abb"),
 ])
 def test_adjoint_matches_oracle(storage, case, qh, kind, obj, wall_bc):
     w = _plate() if case == "plate" else _channel()
@@ -102,6 +106,34 @@ def test_adjoint_matches_oracle(storage, case, qh, kind, obj, wall_bc):
     assert abs(Jg - Jo) <= (1e-10 if storage == "f64" else 1e-6) * max(abs(Jo), 1e-3)
     assert np.abs(dth_g - dth_o).max() <= tol * scale
     assert np.abs(dTw_g - dTw_o).max() <= tol * max(np.abs(dTw_o).max(), 1e-12)
+
+
+def test_cumulant_adjoint_needs_h_records():
+    # the Cumulants-1st collision is not linear in h: the record-free entry
+    # point refuses it, the one with the level's h record accepts it
+    torch = _torch()
+    from paper_2203_01316_gb300 import LBMError
+    w = _plate()
+    theta = w["theta"].astype(np.float32).astype(np.float64)
+    s = _solver(w, "f32", 27, "cum1st", 0.05, 0.01, (0.0, 0.0, 0.0), [1.0, 0.1], theta)
+    N = s.N
+    u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+    h = torch.empty(27 * N, dtype=torch.float32, device="cuda")
+    s.step_record(1, u, h_rec=h)
+    mu = torch.zeros(27 * N, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(mu)
+    st = s.L.lbm_adjoint_step(s._h, u.data_ptr(), mu.data_ptr(), out.data_ptr(), None, None)
+    assert st == 1  # LBM_ERR_INVALID
+    with pytest.raises(LBMError):
+        s._check(s.L.lbm_adjoint_step_h(s._h, u.data_ptr(), None, mu.data_ptr(), out.data_ptr(), None, None))
+    s.adjoint_step(u, mu, out, h_level=h)
+    s.sync()
+    assert torch.count_nonzero(out).item() == 0
+    # the h record holds the post-collision deviations of the state reached
+    _, hp = s.populations()
+    rec = h.view(27, N).cpu().numpy().astype(np.float64) + 0.5 * O.lattice(27)[1][:, None]
+    fl = w["flags"] != I.SOLID
+    assert np.abs(rec[:, fl] - hp[:, fl]).max() < 1e-6
 
 
 def _config4():

@@ -2,8 +2,9 @@
 asynchronous bulk copies) against the classic kernel (direct loads): both
 run the same arithmetic on the same values, so every stored population must
 agree to rounding level after two steps, relative to the largest stored
-magnitude: 1e-6 for FP32, 4 units in the last place for FP16/BF16 (ptxas
-may contract multiply-adds differently in the two kernels),
+magnitude: 1e-6 for FP32 (26e-6 for the rest population of h, which closes
+the zeroth moment from the others), 4 units in the last place for FP16/BF16
+(ptxas may contract multiply-adds differently in the two kernels),
 for every storage type the staged kernel serves and both h lattices; a wrong
 source row shows up as a gross difference.  The staged kernel must also pass
 the oracle's one-step check itself."""
@@ -53,10 +54,21 @@ def test_staged_equals_classic_bitwise(case, storage, qh):
     a, b = out
     # rounding-level differences only: FP32 1e-6 of the largest stored
     # magnitude (wall links and collisions carry contraction differences),
-    # 16-bit 4 units in the last place of it; a wrong source row is ~1e-2
+    # 16-bit 4 units in the last place of it; a wrong source row is ~1e-2.
+    # In FP32 the rest population of h closes the zeroth moment from the
+    # other Q_h - 1 outputs, so it carries the sum of their differences:
+    # (Q_h - 1) times the bound.
+    N = nx * ny * nz
+    assert a.size == (27 + qh) * N
     scale = np.abs(a).max()
-    tol = 1e-6 * scale if storage == "f32" else 4.0 * _ulp(np.array([scale]), storage)[0]
-    assert np.abs(a - b).max() <= tol
+    if storage == "f32":
+        d = np.abs(a - b)
+        rest = slice(27 * N, 28 * N)
+        assert d[rest].max() <= (qh - 1) * 1e-6 * scale
+        d[rest] = 0.0
+        assert d.max() <= 1e-6 * scale
+    else:
+        assert np.abs(a - b).max() <= 4.0 * _ulp(np.array([scale]), storage)[0]
 
 
 def _stored(blob, storage):
