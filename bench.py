@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import math
 import os
@@ -517,40 +518,114 @@ def validation_hill(args):
     256 x 256 x 1 box (sigma0^2 = 100, t_SI = 100, k_SI = 4, so n = 400/k
     steps), at rest and at u_x = 0.1 (lattice units), for every h kind and
     k from 1/6 down; normalised L2 error of the hill C = T - 1 against the
-    closed form (FP32 storage).  At k = 1/6 the result is also compared with
-    the exact lattice convolution the step reduces to there."""
+    closed form, in FP64 (k >= 1e-3: the scheme's own error) and in FP32
+    (every k).  At k = 1/6 the FP32 result is also compared with the exact
+    lattice convolution the step reduces to there."""
     import torch  # noqa: F401
     from paper_2203_01316_gb300 import Solver, build, inputs as I
     build.build()
     L, s0 = 256, 100.0
     ks = [float(v) for v in args.sizes.split(",")] if args.sizes else [1.0 / 6.0, 1e-2, 1e-3, 1e-4]
     out, lat = {}, {}
-    for kind in ("trt", "srt", "1st", "cum1st"):
-        for ux in (0.0, 0.1):
-            key = f"{kind}, u_x = {ux:g}"
-            out[key] = {}
-            for k in ks:
-                n = int(round(400.0 / k))
-                w = I.gaussian_hill(L, s0)
-                w["u"][0] = ux
-                s = Solver(L, L, 1, nu=1.0 / 6.0, k=k, lat_h=27, hkind=kind, storage="f32", periodic_x=True,
-                           T_ref=1.0)
-                s.set_geometry(w["flags"], None)
-                s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
-                t0 = time.perf_counter()
-                s.step(n)
-                _, _, T = s.macros()
-                dt = time.perf_counter() - t0
-                s.close()
-                Cn = T.reshape(L, L) - 1.0
-                Ca = hill_closed_form(L, s0, k, n, ux)
-                out[key][f"{k:.4g}"] = float(np.sqrt(np.sum((Ca - Cn) ** 2) / np.sum(Ca ** 2)))
-                if k == 1.0 / 6.0:
-                    Cl = lattice_convolution(w["T"].reshape(L, L) - 1.0, n, (ux, 0.0))
-                    lat[key] = float(np.abs(Cl - Cn).max())
-                print(f"# {key} k={k:.4g} n={n} {dt:.1f}s L2={out[key][f'{k:.4g}']:.3e}", file=sys.stderr, flush=True)
-    line = {"validation": "Gaussian hill (Sec. 4.1), 256x256x1, sigma0^2 = 100, n = 400/k steps, FP32",
+    for storage, kind, ux in itertools.product(("f64", "f32"), ("trt", "srt", "1st", "cum1st"), (0.0, 0.1)):
+        key = f"{storage}, {kind}, u_x = {ux:g}"
+        out[key] = {}
+        for k in ks:
+            if storage == "f64" and k < 1e-3:
+                continue  # 4e6 FP64 steps: about 15 minutes per run on GB300
+            n = int(round(400.0 / k))
+            w = I.gaussian_hill(L, s0)
+            w["u"][0] = ux
+            s = Solver(L, L, 1, nu=1.0 / 6.0, k=k, lat_h=27, hkind=kind, storage=storage, periodic_x=True,
+                       T_ref=1.0)
+            s.set_geometry(w["flags"], None)
+            s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+            t0 = time.perf_counter()
+            s.step(n)
+            _, _, T = s.macros()
+            dt = time.perf_counter() - t0
+            s.close()
+            Cn = T.reshape(L, L) - 1.0
+            Ca = hill_closed_form(L, s0, k, n, ux)
+            out[key][f"{k:.4g}"] = float(np.sqrt(np.sum((Ca - Cn) ** 2) / np.sum(Ca ** 2)))
+            if k == 1.0 / 6.0 and storage == "f32":
+                Cl = lattice_convolution(w["T"].reshape(L, L) - 1.0, n, (ux, 0.0))
+                lat[key] = float(np.abs(Cl - Cn).max())
+            print(f"# {key} k={k:.4g} n={n} {dt:.1f}s L2={out[key][f'{k:.4g}']:.3e}", file=sys.stderr, flush=True)
+    line = {"validation": "Gaussian hill (Sec. 4.1), 256x256x1, sigma0^2 = 100, n = 400/k steps",
             "L2": out, "k=1/6: max |C - lattice convolution|": lat}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def confined_nu(S, kind, wall_bc, Pr, storage="f32", max_flow_throughs=4.0, tol=2e-3, xc=None, inlet_bc="zou_he"):
+    """Sec. 4.4 confined cylinder on the GPU path: steps until the heat flux
+    through the cylinder surface (q_s, Eq. heat_flux_thorough_heater) and the
+    heat carried through the outlet section minus the inlet section (q_x,
+    Eq. heat_flux_section, sections 50 S and 100 S from the planes) agree to
+    tol and the Nusselt number has stopped changing, or until
+    max_flow_throughs times L/U steps.  Nu = q D / (k A dT) with A = pi D
+    (per unit depth), q the mean of q_s and q_x."""
+    from paper_2203_01316_gb300 import Solver, inputs as I
+    w = I.confined_cylinder(S, xc=xc)
+    nx, ny, nz = w["dims"]
+    nu = 0.03
+    k = nu / Pr
+    s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind=kind, storage=storage, periodic_x=False,
+               T_ref=w["T_in"], wall_bc=wall_bc, inlet_bc=inlet_bc)
+    s.set_geometry(w["flags"], w["links"], n_walls=1)
+    s.set_bc(0, w["T_cyl"])
+    s.set_inlet(w["u_in"], w["T_in"])
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    U = w["u_in"][0]
+    through = int(nx / U)
+    chunk = max(1000, through // 40)
+    xin, xout = w["sections"]
+    dT = w["T_cyl"] - w["T_in"]
+    steps, nu_prev = 0, None
+    t0 = time.perf_counter()
+    while True:
+        s.step(chunk)
+        steps += chunk
+        qs = s.surface_flux(0)
+        qx = s.section_flux(xout) - s.section_flux(xin)
+        q = 0.5 * (qs + qx)
+        Nu = q / (k * math.pi * dT)
+        mism = abs(qs - qx) / max(abs(qs), 1e-30)
+        done = (mism < tol and nu_prev is not None and abs(Nu - nu_prev) < 1e-4 * abs(Nu)
+                and steps >= through)
+        if done or steps >= max_flow_throughs * through or not math.isfinite(Nu):
+            break
+        nu_prev = Nu
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"Nu": Nu, "q_surface": qs, "q_x": qx, "mismatch": mism, "steps": steps, "converged": bool(done),
+            "seconds": round(dt, 1), "MLUPS": round(nx * ny * nz * steps / dt / 1e6)}
+
+
+def validation_confined(args):
+    """Sec. 4.4 Nusselt-number table: four h kernels x first-order (BB + EQ)
+    and second-order (Eq. IBB + Eq. IABB) walls x Pr in {10, 100, 1000} on the
+    meshes S given by --sizes (default 1: 1000 x 150, D = 30, U = 0.01,
+    nu = 0.03, Re = 10), FP32 storage with T_ref = T_in."""
+    import torch  # noqa: F401
+    from paper_2203_01316_gb300 import build
+    build.build()
+    Ss = [float(v) if "." in v else int(v) for v in args.sizes.split(",")] if args.sizes else [1]
+    kinds = args.kinds.split(",") if args.kinds else ["1st", "srt", "trt", "cum1st"]
+    prs = [float(v) for v in args.prs.split(",")] if args.prs else [10.0, 100.0, 1000.0]
+    out = []
+    for S in Ss:
+        for Pr in prs:
+            for kind in kinds:
+                for order, bc in (("1st", "eq"), ("2nd", "iabb")):
+                    if args.orders and order not in args.orders.split(","):
+                        continue
+                    r = confined_nu(S, kind, bc, Pr, inlet_bc=args.inlet)
+                    r.update({"S": S, "Pr": Pr, "kernel": kind, "bc_order": order})
+                    out.append(r)
+                    print("# " + json.dumps(r), file=sys.stderr, flush=True)
+    line = {"validation": f"confined cylinder Nu (Sec. 4.4), Re = 10, FP32, {args.inlet} inlet", "results": out}
     print(json.dumps(line), flush=True)
     return line
 
@@ -661,7 +736,12 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
-    ap.add_argument("--validation", choices=["cylinders", "hill"],
+    ap.add_argument("--kinds", default="", help="validation confined: comma-separated h kinds")
+    ap.add_argument("--prs", default="", help="validation confined: comma-separated Prandtl numbers")
+    ap.add_argument("--orders", default="", help="validation confined: wall-rule orders, '1st', '2nd' or both")
+    ap.add_argument("--inlet", default="zou_he", choices=["zou_he", "equilibrium"],
+                    help="validation confined: inlet plane rule")
+    ap.add_argument("--validation", choices=["cylinders", "hill", "confined"],
                     help="run one of the paper's validation workloads on the GPU path")
     ap.add_argument("--sizes", default="", help="validation: comma-separated D (cylinders) or k (hill)")
     ap.add_argument("--workload", choices=["sphere", "porous"], default="sphere",
@@ -680,6 +760,8 @@ def main():
         validation_cylinders(args)
     elif args.validation == "hill":
         validation_hill(args)
+    elif args.validation == "confined":
+        validation_confined(args)
     elif args.precision:
         precision_study(args)
     elif args.workload == "porous":

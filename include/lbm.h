@@ -81,7 +81,18 @@ typedef struct {
                             1 = round to nearest even */
     int step_kernel;     /* lbm_step_kernel: implementation of lbm_step (same results) */
     int wall_bc;         /* lbm_wall_bc: wall rules */
+    int inlet_bc;        /* lbm_inlet_bc: inlet plane rule (periodic_x = 0) */
 } lbm_params;
+
+/* Inlet plane rules (Sec. 4.4).  EQUILIBRIUM: the inlet nodes hold the
+ * equilibria at (rho = 1, u_in) and (T_in, u_in) as their post-collision
+ * state.  ZOU_HE: the inlet nodes stream and collide like fluid nodes; the
+ * populations entering from outside (e_x = +1) are set by non-equilibrium
+ * bounce-back at u_in for f (density from mass and x-momentum, transverse
+ * momentum corrected to rho u_in exactly) and, for h, take the equilibrium
+ * shape at u_in with the amplitude that makes the zeroth moment rho T_in.
+ * With ZOU_HE the plane x = 1 holds no solid node. */
+typedef enum { LBM_INLET_EQUILIBRIUM = 0, LBM_INLET_ZOU_HE = 1 } lbm_inlet_bc;
 
 /* Wall rules (Sec. 3).  IBB_IABB: Eq. IBB for f, Eq. IABB for h, with each
  * link's q (second order).  BB_EQ: bounce-back for f (Eq. IBB at q = 1/2) and
@@ -106,16 +117,25 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out);
 /* Free every resource of the context (synchronises its stream). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 
-/* Geometry (Sec. 3).  flags: uint8[N], 0 fluid, 1 solid, 2 inlet, 3 outlet.
+/* Geometry (Sec. 3).  flags: uint8[N], 0 fluid, 1 solid, 2 inlet, 3 outlet,
+ * 4 symmetry row.
  * Wall links: n_links entries (link_node[l], link_dir[l]) meaning node
  * link_node is fluid and link_node + e_{link_dir} is solid; link_q in (0,1]
  * is the fraction of the link at which the wall lies (Eq. IBB's q);
  * link_wall in [0, n_walls) names the wall, whose temperature lbm_set_bc
- * sets.  Rules checked (LBM_ERR_INVALID otherwise): with periodic_x = 0 the
- * x = 0 plane is all inlet, x = nx-1 all outlet, and x = nx-2 holds no solid;
- * inlet/outlet flags appear nowhere else; every fluid->solid link is listed
- * exactly once.  Links may come in any order.  Replaces any earlier geometry;
- * the populations must be (re)initialised afterwards. */
+ * sets.  Symmetry rows model the symmetry planes of Sec. 4.4: the whole row
+ * y = 0 and / or y = ny-1 (every x and z) may be flagged 4; the plane lies
+ * halfway between that row and its neighbour row, where populations reflect
+ * specularly (e_y reversed).  Symmetry nodes hold no state of their own
+ * (macros, balances and fluxes skip them, and populations read zero there).
+ * Rules checked (LBM_ERR_INVALID otherwise): with periodic_x = 0 the
+ * x = 0 plane is all inlet, x = nx-1 all outlet (symmetry rows excepted),
+ * and x = nx-2 holds no solid; inlet/outlet flags appear nowhere else; every
+ * fluid->solid link is listed exactly once; symmetry rows are whole, their
+ * neighbour rows hold no solid node and no wall link.  Links may come in any
+ * order.  Replaces any earlier geometry; the populations must be
+ * (re)initialised afterwards.  The adjoint entry points refuse geometries
+ * with symmetry rows and contexts with the Zou-He inlet. */
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, int64_t n_links,
                             const int32_t* link_node, const int32_t* link_dir,
                             const float* link_q, const int32_t* link_wall, int n_walls,

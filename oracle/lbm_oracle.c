@@ -318,6 +318,7 @@ typedef struct {
     double F[3];
     double u_in[3], T_in;
     int wall_bc;     /* 0 Eq. IBB + Eq. IABB; 1 BB + EQ (first order); 2 BB + ABB */
+    int inlet_bc;    /* 0 equilibrium inlet plane (reading R6); 1 Zou-He (reading R20) */
 } orc_params;
 
 enum { KIND_TRT = 0, KIND_SRT = 1, KIND_1ST = 2, KIND_CUM1 = 3 };
@@ -511,7 +512,8 @@ void orc_destroy(orc_sim* s) {
  * Returns 0, or a negative code naming the first rule broken:
  *  -1 flag out of range, -2 inlet/outlet planes wrong, -3 link node not
  *  fluid, -4 link target not solid, -5 q outside (0,1], -6 duplicate link,
- *  -7 fluid->solid link missing, -8 solid adjacent to the outlet plane,
+ *  -7 fluid->solid link missing, -8 solid adjacent to the outlet plane (or,
+ *  with the Zou-He inlet, to the inlet plane),
  *  -9 wall id out of range, -10 symmetry rows wrong (or a wall link from a
  *  node next to one). */
 int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* lnode,
@@ -538,6 +540,7 @@ int orc_set_geometry(orc_sim* s, const uint8_t* flags, int nlinks, const int* ln
             if ((x == 0) != (flags[n] == FL_INLET)) return -2;
             if ((x == nx - 1) != (flags[n] == FL_OUTLET)) return -2;
             if (x == nx - 2 && flags[n] == FL_SOLID) return -8;
+            if (s->p.inlet_bc && x == 1 && flags[n] == FL_SOLID) return -8; /* Zou-He reads x = 1 */
         }
     }
     s->has_mirror = 0;
@@ -656,7 +659,7 @@ void orc_collide(orc_sim* s) {
             for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = 0.0;
             continue;
         }
-        if (fl == FL_INLET) { /* reading R6 */
+        if (fl == FL_INLET && !s->p.inlet_bc) { /* reading R6 */
             for (int a = 0; a < 27; ++a) s->fs[(size_t)a * N + n] = feq_in[a];
             for (int a = 0; a < qh; ++a) s->hs[(size_t)a * N + n] = heq_in[a];
             continue;
@@ -701,6 +704,52 @@ static double iabb(double q, double ha_b, double hab_b, double ha_f, int thin, d
     if (q <= 0.5 && !thin) return -(2.0 * q * ha_b + (1.0 - 2.0 * q) * ha_f) + 2.0 * heq_w;
     if (q <= 0.5) q = 0.5;
     return (-ha_b + (2.0 * q - 1.0) * hab_b + 2.0 * heq_w) / (2.0 * q);
+}
+
+/* Zou-He inlet (Sec. 4.4; reading R20) at inlet node n after the pushes: the
+ * populations with e_x = +1 (arriving from outside) are unknown.
+ * f: non-equilibrium bounce-back at the prescribed velocity u_in,
+ *     f_a = f_abar + f^eq_a(rho, u_in) - f^eq_abar(rho, u_in) - e_ya N_y - e_za N_z,
+ * with rho from mass and x-momentum, rho (1 - u_x) = sum_{e_x=0} f + 2 sum_{e_x=-1} f,
+ * and N_d = sum_{e_x=0} e_d (f - f^eq) / 6 so that the transverse momentum is
+ * rho u_d exactly (the six unknowns with e_d != 0 share the correction).
+ * h: the unknowns take the shape of the equilibrium at u_in with the amplitude
+ * that makes the zeroth moment rho T_in. */
+static void zou_he_inlet(orc_sim* s, int n) {
+    const int N = s->N, qh = s->p.qh;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    const double* u = s->p.u_in;
+    double known0 = 0.0, known_out = 0.0;
+    for (int a = 0; a < 27; ++a) {
+        double v = s->fn[(size_t)a * N + n];
+        if (L->e[a][0] == 0) known0 += v;
+        else if (L->e[a][0] < 0) known_out += v;
+    }
+    const double rho = (known0 + 2.0 * known_out) / (1.0 - u[0]);
+    double feq[27];
+    equilibrium(L, rho, u, feq);
+    double Nt[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 27; ++a) {
+        if (L->e[a][0] != 0) continue;
+        for (int d = 1; d < 3; ++d) Nt[d] += L->e[a][d] * (s->fn[(size_t)a * N + n] - feq[a]);
+    }
+    for (int d = 1; d < 3; ++d) Nt[d] /= 6.0;
+    for (int a = 0; a < 27; ++a) {
+        if (L->e[a][0] != 1) continue;
+        int ab = L->opp[a];
+        s->fn[(size_t)a * N + n] = s->fn[(size_t)ab * N + n] + feq[a] - feq[ab] - L->e[a][1] * Nt[1] -
+                                   L->e[a][2] * Nt[2];
+    }
+    double M[27], known_h = 0.0, unknown_w = 0.0;
+    equilibrium(Lh, 1.0, u, M);
+    for (int a = 0; a < qh; ++a) {
+        if (Lh->e[a][0] == 1) unknown_w += M[a];
+        else known_h += s->hn[(size_t)a * N + n];
+    }
+    const double amp = (rho * s->p.T_in - known_h) / unknown_w;
+    for (int a = 0; a < qh; ++a)
+        if (Lh->e[a][0] == 1) s->hn[(size_t)a * N + n] = amp * M[a];
 }
 
 /* Streaming of fs, hs (push, Sec. 2.1 evolution equation) with Eq. (IBB),
@@ -765,14 +814,16 @@ int orc_stream(orc_sim* s) {
             }
         }
     }
-    /* planes (reading R6) */
+    /* planes (reading R6; Zou-He inlet, reading R20) */
     if (!s->p.periodic_x) {
         double feq_in[27], heq_in[27];
         equilibrium(L, 1.0, s->p.u_in, feq_in);
         equilibrium(Lh, s->p.T_in, s->p.u_in, heq_in);
         for (int n = 0; n < N; ++n) {
             int x = n % nx;
-            if (s->flags[n] == FL_INLET) {
+            if (s->flags[n] == FL_INLET && s->p.inlet_bc) {
+                zou_he_inlet(s, n);
+            } else if (s->flags[n] == FL_INLET) {
                 for (int a = 0; a < 27; ++a) s->fn[(size_t)a * N + n] = feq_in[a];
                 for (int a = 0; a < qh; ++a) s->hn[(size_t)a * N + n] = heq_in[a];
             } else if (s->flags[n] == FL_OUTLET && x == nx - 1) {
@@ -1108,7 +1159,8 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
  * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, or -3 for a
- * geometry with symmetry rows (their transpose is not built).
+ * geometry with symmetry rows or a Zou-He inlet (their transposes are not
+ * built).
  * The Cumulants-1st collision is not affine in h: for that kind the forward
  * keeps the pre-collision h of every level and the reverse sweep applies the
  * transpose of the collision's Jacobian there (cum_jacobian); streaming and
@@ -1118,7 +1170,8 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
     const int cum = s->p.hkind == KIND_CUM1;
-    if (dtheta && s->has_mirror) return -3; /* the transpose of the symmetry rows is not built */
+    /* the transposes of the symmetry rows and of the Zou-He inlet are not built */
+    if (dtheta && (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x))) return -3;
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
     double* hrec = (dtheta && cum) ? (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double)) : NULL;
     orc_set_post(s, f_post, h_post);

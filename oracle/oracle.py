@@ -44,14 +44,16 @@ class Params(C.Structure):
                 ("nu", C.c_double), ("k", C.c_double),
                 ("omega_bulk", C.c_double), ("omega3", C.c_double), ("omega4", C.c_double),
                 ("omega5", C.c_double), ("omega6", C.c_double),
-                ("F", C.c_double * 3), ("u_in", C.c_double * 3), ("T_in", C.c_double), ("wall_bc", C.c_int)]
+                ("F", C.c_double * 3), ("u_in", C.c_double * 3), ("T_in", C.c_double), ("wall_bc", C.c_int),
+                ("inlet_bc", C.c_int)]
 
 WALL_BC = {"iabb": 0, "eq": 1, "abb": 2}
+INLET_BC = {"equilibrium": 0, "zou_he": 1}
 
 
 def make_params(nx=1, ny=1, nz=1, qh=27, hkind="trt", periodic_x=True, nu=0.02, k=2e-4,
                 omega_bulk=1.0, omega3=1.0, omega4=1.0, omega5=1.0, omega6=1.0,
-                F=(0.0, 0.0, 0.0), u_in=(0.0, 0.0, 0.0), T_in=0.0, wall_bc="iabb") -> Params:
+                F=(0.0, 0.0, 0.0), u_in=(0.0, 0.0, 0.0), T_in=0.0, wall_bc="iabb", inlet_bc="equilibrium") -> Params:
     p = Params()
     p.nx, p.ny, p.nz, p.qh = nx, ny, nz, qh
     p.hkind = KINDS[hkind] if isinstance(hkind, str) else int(hkind)
@@ -63,6 +65,7 @@ def make_params(nx=1, ny=1, nz=1, qh=27, hkind="trt", periodic_x=True, nu=0.02, 
         p.u_in[d] = u_in[d]
     p.T_in = T_in
     p.wall_bc = WALL_BC[wall_bc] if isinstance(wall_bc, str) else int(wall_bc)
+    p.inlet_bc = INLET_BC[inlet_bc] if isinstance(inlet_bc, str) else int(inlet_bc)
     return p
 
 
@@ -289,5 +292,6 @@ class Oracle:
                                int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
                                dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
         if rc != 0:
-            raise OracleError("orc_adjoint: " + ("no adjoint with symmetry rows" if rc == -3 else "streaming error"))
+            raise OracleError("orc_adjoint: " + ("no adjoint with symmetry rows or a Zou-He inlet" if rc == -3
+                                                 else "streaming error"))
         return J.value, dth, dTw

@@ -61,6 +61,9 @@ struct lbm_ctx {
 
 static std::string g_create_err;
 
+// user flag of a symmetry-row node (stored as solid on the device)
+static constexpr uint8_t kMirror = 4;
+
 // message slot of calls made without a context (read with lbm_last_error(NULL))
 void lbm_internal_set_global_error(const std::string& msg) { g_create_err = msg; }
 
@@ -231,6 +234,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (p.storage < 0 || p.storage > 3) return fail(nullptr, LBM_ERR_INVALID, "unknown storage");
     if (p.step_kernel < 0 || p.step_kernel > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown step_kernel");
     if (p.wall_bc < 0 || p.wall_bc > 2) return fail(nullptr, LBM_ERR_INVALID, "unknown wall_bc");
+    if (p.inlet_bc < 0 || p.inlet_bc > 1) return fail(nullptr, LBM_ERR_INVALID, "unknown inlet_bc");
     if (!(p.nu > 0.0) || !std::isfinite(p.nu)) return fail(nullptr, LBM_ERR_INVALID, "nu must be > 0");
     double k = p.k, Pr = p.Pr;
     if (k > 0.0 && Pr > 0.0) {
@@ -318,6 +322,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     d.stochastic = p.round_nearest ? 0 : 1;
     d.hkind = p.hkind;
     d.wall_bc = p.wall_bc;
+    d.zou_he = (p.inlet_bc == LBM_INLET_ZOU_HE && !p.periodic_x) ? 1 : 0;
     d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;
@@ -377,10 +382,20 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         return x + nx * (y + ny * z);
     };
     int64_t nonsolid = 0;
+    bool mirror_row[2] = {false, false};  // symmetry rows y = 0, y = ny - 1
     for (int n = 0; n < N; ++n) {
         const uint8_t t = fl[n];
-        if (t > 3) return fail(c, LBM_ERR_INVALID, "flag value above 3 at node " + std::to_string(n));
-        const int x = n % nx;
+        if (t > 4) return fail(c, LBM_ERR_INVALID, "flag value above 4 at node " + std::to_string(n));
+        const int x = n % nx, y = (n / nx) % ny;
+        if (t == kMirror) {
+            if (ny < 3 || (y != 0 && y != ny - 1))
+                return fail(c, LBM_ERR_INVALID, "symmetry node outside the rows y = 0 and y = ny-1");
+            const int src = n + (y == 0 ? nx : -nx);
+            if (fl[src] == lbmd::T_SOLID || fl[src] == kMirror)
+                return fail(c, LBM_ERR_INVALID, "the node beside symmetry node " + std::to_string(n) + " is solid");
+            mirror_row[y == 0 ? 0 : 1] = true;
+            continue;
+        }
         if (c->p.periodic_x) {
             if (t == lbmd::T_INLET || t == lbmd::T_OUTLET)
                 return fail(c, LBM_ERR_INVALID, "inlet/outlet flag in a periodic-x grid");
@@ -389,8 +404,18 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
             if ((x == nx - 1) != (t == lbmd::T_OUTLET))
                 return fail(c, LBM_ERR_INVALID, "the x=nx-1 plane must be all outlet");
             if (x == nx - 2 && t == lbmd::T_SOLID) return fail(c, LBM_ERR_INVALID, "solid node next to the outlet");
+            if (c->dp.zou_he && x == 1 && t == lbmd::T_SOLID)
+                return fail(c, LBM_ERR_INVALID, "solid node next to a Zou-He inlet");
         }
         if (t != lbmd::T_SOLID) ++nonsolid;
+    }
+    for (int side = 0; side < 2; ++side) {  // a symmetry row is whole
+        if (!mirror_row[side]) continue;
+        const int y = side == 0 ? 0 : ny - 1;
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x)
+                if (fl[x + (size_t)nx * (y + (size_t)ny * z)] != kMirror)
+                    return fail(c, LBM_ERR_INVALID, "a symmetry row must cover the whole x-z row");
     }
     // links: validate, sort by (node, dir)
     std::vector<int64_t> order(n_links);
@@ -398,6 +423,11 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
         const int n = ln[l], a = ld[l];
         if (n < 0 || n >= N || a < 1 || a >= 27) return fail(c, LBM_ERR_INVALID, "link node/dir out of range");
         if (fl[n] != lbmd::T_FLUID) return fail(c, LBM_ERR_INVALID, "link from a non-fluid node " + std::to_string(n));
+        {
+            const int y = (n / nx) % ny;
+            if ((mirror_row[0] && y == 1) || (mirror_row[1] && y == ny - 2))
+                return fail(c, LBM_ERR_INVALID, "wall link from a node next to a symmetry row");
+        }
         const int t = nbr(n, lbmd::EX(a), lbmd::EY(a), lbmd::EZ(a));
         if (t < 0 || fl[t] != lbmd::T_SOLID)
             return fail(c, LBM_ERR_INVALID, "link target is not solid (node " + std::to_string(n) + ")");
@@ -429,6 +459,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
     // completeness: every fluid->solid link listed; outlet nodes see no solid.
     // Nested loops with per-row neighbour offsets (y, z periodic).
     std::vector<uint8_t> iflags(fl);
+    for (auto& v : iflags)
+        if (v == kMirror) v = lbmd::T_SOLID;  // the step never writes a symmetry node
     size_t wi = 0;
     const int64_t plane = (int64_t)nx * ny;
     for (int z = 0; z < nz; ++z) {
@@ -441,7 +473,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
             const int64_t row = (int64_t)z * plane + (int64_t)y * nx;
             for (int x = 0; x < nx; ++x) {
                 const int n = (int)(row + x);
-                if (fl[n] == lbmd::T_SOLID || fl[n] == lbmd::T_INLET) continue;
+                if (fl[n] == lbmd::T_SOLID || fl[n] == lbmd::T_INLET || fl[n] == kMirror) continue;
                 uint32_t m = 0;
                 for (int a = 1; a < 27; ++a) {
                     int xx = x + lbmd::EX(a);
@@ -567,6 +599,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
     c->h_lq = std::move(sq);
     c->h_lwall = std::move(sw);
     c->n_fluid_like = nonsolid;
+    c->dp.mirror_lo = mirror_row[0] ? 1 : 0;
+    c->dp.mirror_hi = mirror_row[1] ? 1 : 0;
     c->geometry = true;
     c->initialised = false;
     return LBM_OK;
@@ -670,6 +704,24 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const
     return LBM_OK;
 }
 
+// the Zou-He inlet plane, after each step
+static cudaError_t zou_he_inlet(lbm_ctx* c, const Buffers& b, const DevParams& p, bool advance_h) {
+    if (!p.zou_he) return cudaSuccess;
+    return dispatch(c, [&](auto tag) {
+        using Tg = decltype(tag);
+        return lbmd::launch_inlet<typename Tg::S, Tg::Q>(b, p, c->stream, advance_h);
+    });
+}
+
+// symmetry rows take their mirrored populations before each step
+static cudaError_t fill_mirror(lbm_ctx* c, const Buffers& b, const DevParams& p) {
+    if (!p.mirror_lo && !p.mirror_hi) return cudaSuccess;
+    return dispatch(c, [&](auto tag) {
+        using Tg = decltype(tag);
+        return lbmd::launch_mirror<typename Tg::S, Tg::Q>(b, p, c->stream);
+    });
+}
+
 lbm_status lbm_step(lbm_ctx* c, int n) {
     if (!c) return LBM_ERR_INVALID;
     if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
@@ -680,6 +732,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
         c->dp.step += 1;
         const DevParams p = c->dp;
         cudaError_t e;
+        if ((e = fill_mirror(c, b, p)) != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
         if (c->staged) {
             switch (c->p.storage) {
                 case LBM_F32:
@@ -702,6 +755,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
             });
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        if ((e = zou_he_inlet(c, b, p, true)) != cudaSuccess) return cuda_fail(c, e, "inlet launch");
         c->cur_f = 1 - c->cur_f;
         c->cur_h = 1 - c->cur_h;
     }
@@ -963,11 +1017,14 @@ lbm_status lbm_step_record(lbm_ctx* c, int n, void* u_rec, int advance_h) {
         c->dp.step += 1;
         const DevParams p = c->dp;
         b.urec = (char*)u_rec + (size_t)i * 3 * c->N * rsize;
-        cudaError_t e = dispatch(c, [&](auto tag) {
+        cudaError_t e = fill_mirror(c, b, p);
+        if (e != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
+        e = dispatch(c, [&](auto tag) {
             using Tg = decltype(tag);
             return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream, advance_h != 0);
         });
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        if ((e = zou_he_inlet(c, b, p, advance_h != 0)) != cudaSuccess) return cuda_fail(c, e, "inlet launch");
         c->cur_f = 1 - c->cur_f;
         if (advance_h) c->cur_h = 1 - c->cur_h;
     }
@@ -1000,6 +1057,9 @@ static lbm_status adjoint_step_impl(lbm_ctx* c, const void* u_level, const void*
                                     void* out, const lbm_objective* obj, double* dJ_dtheta) {
     if (!c || !mu_next || !out) return LBM_ERR_INVALID;
     if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    if (c->dp.mirror_lo || c->dp.mirror_hi)
+        return fail(c, LBM_ERR_INVALID, "the adjoint does not cover symmetry rows");
+    if (c->dp.zou_he) return fail(c, LBM_ERR_INVALID, "the adjoint does not cover the Zou-He inlet");
     if (c->p.hkind == LBM_H_CUM_1ST && u_level && !h_level)
         return fail(c, LBM_ERR_INVALID,
                     "the Cumulants-1st adjoint needs the level's h record (lbm_step_record_h, lbm_adjoint_step_h)");

@@ -63,6 +63,11 @@ __host__ __device__ __forceinline__ constexpr double W7(int i) { return i == 0 ?
 // h lattice helpers: velocity index in the D3Q27 list, opposite, weight
 template <int QH> __host__ __device__ __forceinline__ constexpr int HDIR(int i) { return QH == 27 ? i : D7(i); }
 template <int QH> __host__ __device__ __forceinline__ constexpr int HOPP(int i) { return QH == 27 ? OPP(i) : OPP7(i); }
+// velocity with the y component reversed (D3Q27 index; D3Q7: +y <-> -y)
+__host__ __device__ __forceinline__ constexpr int FLIPY(int a) { return DIR(EX(a), -EY(a), EZ(a)); }
+template <int QH> __host__ __device__ __forceinline__ constexpr int HFLIPY(int i) {
+    return QH == 27 ? FLIPY(i) : (i == 2 ? 5 : (i == 5 ? 2 : i));
+}
 template <int QH> __host__ __device__ __forceinline__ constexpr double HW(int i) { return QH == 27 ? W27(i) : W7(i); }
 
 // ---- storage types -------------------------------------------------------
@@ -226,6 +231,8 @@ struct DevParams {
     int stochastic;      // 16-bit storage: 1 stochastic rounding, 0 round to nearest
     int hkind;           // 0..2 central-moment kinds, 3 Cumulants-1st
     int wall_bc;         // 0 Eq. IBB + Eq. IABB, 1 BB + EQ, 2 BB + ABB (BB/ABB: q = 1/2 on the device)
+    int mirror_lo, mirror_hi;  // rows y = 0 / y = ny-1 are symmetry rows
+    int zou_he;                // inlet plane: 0 fixed equilibria, 1 Zou-He (k_inlet after the step)
     uint32_t step;       // time level being written (random stream of st_sr)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6

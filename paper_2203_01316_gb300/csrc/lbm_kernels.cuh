@@ -72,6 +72,12 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
 template <typename R, int QH>
 cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_level, const R* h_level,
                            const R* mu_next, R* mu_out, AdjObjective obj, double* dtheta, cudaStream_t s);
+// Zou-He inlet plane, after a step (advance_h = false: f only)
+template <typename S, int QH>
+cudaError_t launch_inlet(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h);
+// symmetry rows: fill them in the post-collision arrays before a step
+template <typename S, int QH>
+cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s);
 // rec[i * N + n] = post-collision h deviation of population i at node n (type R)
 template <typename S, int QH>
 cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s);
@@ -1177,6 +1183,135 @@ cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_leve
     if (p.hkind == 3) k_adjoint<R, QH, true><<<grid, kBlock, 0, s>>>(LBM_ADJ_ARGS);
     else k_adjoint<R, QH, false><<<grid, kBlock, 0, s>>>(LBM_ADJ_ARGS);
 #undef LBM_ADJ_ARGS
+    return cudaGetLastError();
+}
+
+// ---- Zou-He inlet (Sec. 4.4) ------------------------------------------------
+// Runs after the step over the inlet plane x = 0 and replaces what the step
+// stored there.  Arrivals with e_x <= 0 are pulled from the post-collision
+// state A as in the step.  The unknown f (e_x = +1) follow from
+// non-equilibrium bounce-back at u_in: f_a = f_abar + f^eq_a - f^eq_abar with
+// rho from mass and x-momentum, rho (1 - u_x) = sum_{e_x=0} f + 2 sum_{e_x=-1} f,
+// less e_ya N_y + e_za N_z, N_d = sum_{e_x=0} e_d (f - f^eq) / 6, which makes
+// the transverse momentum rho u_d exactly.  The unknown h take the shape of the
+// equilibrium at u_in with the amplitude that makes sum h = rho T_in.  The
+// node then collides and stores like a fluid node.  Everything is in deviation
+// form (f - w rho0, h - w T_ref).
+template <typename S, int QH, bool CUM, bool DO_H>
+__global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* __restrict__ fB,
+                                                   const S* __restrict__ hA, S* __restrict__ hB,
+                                                   const uint8_t* __restrict__ flags,
+                                                   const float* __restrict__ theta,
+                                                   typename Acc<S>::R* __restrict__ urec, const DevParams p) {
+    using R = typename Acc<S>::R;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.ny * p.nz) return;
+    const int y = i % p.ny, z = i / p.ny;
+    const int n = p.nx * (y + p.ny * z);  // x = 0
+    if ((flags[n] & 3) != T_INLET) return;  // symmetry rows are solid on the device
+    const int N = p.N;
+    const Nbr nb = make_nbr(0, y, z, p);
+    const R ux = (R)p.uin[0], uy = (R)p.uin[1], uz = (R)p.uin[2];
+    R fd[27], fe[27];
+    R s0 = R(0), sm = R(0);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) == 1) continue;
+        fd[a] = ld<R>(fA + a * N + src_of(nb, a));
+        if (EX(a) == 0) s0 += fd[a];
+        else sm += fd[a];
+    }
+    // the e_x = 0 and e_x = -1 weights sum to 2/3 and 1/6
+    const R drho = (s0 + R(2) * sm + (R)p.rho0 * ux) / (R(1) - ux);
+    feq_dev<R>(fe, drho, ux, uy, uz, p);
+    R Ny = R(0), Nz = R(0);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) != 0) continue;
+        if (EY(a) != 0) Ny += EY(a) * (fd[a] - fe[a]);
+        if (EZ(a) != 0) Nz += EZ(a) * (fd[a] - fe[a]);
+    }
+    Ny *= R(1) / R(6);
+    Nz *= R(1) / R(6);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) != 1) continue;
+        const int b = OPP(a);
+        fd[a] = fd[b] + fe[a] - fe[b] - EY(a) * Ny - EZ(a) * Nz;
+    }
+    R vx, vy, vz;
+    collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz);
+    if (urec) {
+        urec[n] = vx;
+        urec[N + n] = vy;
+        urec[2 * N + n] = vz;
+    }
+    if constexpr (DO_H) {
+        R hd[QH], he[QH];
+        R K = R(0);
+#pragma unroll
+        for (int k = 0; k < QH; ++k) {
+            const int a = HDIR<QH>(k);
+            if (EX(a) == 1) continue;
+            hd[k] = ld<R>(hA + k * N + src_of(nb, a));
+            K += hd[k];
+        }
+        // unknown deviations = h^eq(amp, u_in) - w T_ref; with damp = amp - T_ref:
+        // damp (c_s^2 + u_x^2 + u_x)/2 = rho T_in - T_ref - K - T_ref (u_x^2 + u_x)/2
+        const R Tref = (R)p.Tref;
+        const R mU = R(0.5) * (cs2<R>() + ux * ux + ux);
+        const R target = drho * (R)p.Tin + (R)(p.rho0 * p.Tin - p.Tref);
+        const R damp = (target - K - Tref * R(0.5) * (ux * ux + ux)) / mU;
+        heq_dev<R, QH>(he, damp, ux, uy, uz, p);
+#pragma unroll
+        for (int k = 0; k < QH; ++k)
+            if (EX(HDIR<QH>(k)) == 1) hd[k] = he[k];
+        const R Q = theta ? (R)__ldg(theta + n) : R(0);
+        collide_store_h<S, QH, CUM>(hd, hB, n, p, vx, vy, vz, Q);
+    }
+}
+
+template <typename S, int QH>
+cudaError_t launch_inlet(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h) {
+    using R = typename Acc<S>::R;
+    const int total = p.ny * p.nz;
+    const int grid = (total + kBlock - 1) / kBlock;
+#define LBM_INLET_ARGS (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (R*)b.urec, p
+    if (!advance_h) k_inlet<S, QH, false, false><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
+    else if (p.hkind == 3) k_inlet<S, QH, true, true><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
+    else k_inlet<S, QH, false, true><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
+#undef LBM_INLET_ARGS
+    return cudaGetLastError();
+}
+
+// ---- symmetry rows (top and bottom symmetry planes, Sec. 4.4) -------------
+// Specular reflection at the plane halfway between a symmetry row and its
+// neighbour row: before each step every node of the rows y = 0 / y = ny-1
+// takes the post-collision populations of the node beside it (y = 1 /
+// y = ny-2) with e_y reversed; the step pulls from it like from any node and
+// never writes it (it is flagged solid and has no wall links).
+template <typename S, int QH>
+__global__ void k_mirror(S* __restrict__ fA, S* __restrict__ hA, const DevParams p) {
+    const int per = p.nx * p.nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * per) return;
+    const int side = i / per, r = i - side * per;
+    if (side == 0 ? !p.mirror_lo : !p.mirror_hi) return;
+    const int x = r % p.nx, z = r / p.nx;
+    const int yg = side == 0 ? 0 : p.ny - 1, ys = side == 0 ? 1 : p.ny - 2;
+    const size_t N = (size_t)p.N;
+    const size_t g = x + (size_t)p.nx * (yg + (size_t)p.ny * z);
+    const size_t src = x + (size_t)p.nx * (ys + (size_t)p.ny * z);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) fA[a * N + g] = fA[FLIPY(a) * N + src];
+#pragma unroll
+    for (int k = 0; k < QH; ++k) hA[k * N + g] = hA[HFLIPY<QH>(k) * N + src];
+}
+
+template <typename S, int QH>
+cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s) {
+    const int total = 2 * p.nx * p.nz;
+    k_mirror<S, QH><<<(total + kBlock - 1) / kBlock, kBlock, 0, s>>>((S*)b.fA, (S*)b.hA, p);
     return cudaGetLastError();
 }
 

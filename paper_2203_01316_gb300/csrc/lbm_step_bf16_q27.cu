@@ -12,6 +12,8 @@ template cudaError_t launch_macros<__nv_bfloat16, 27>(const Buffers&, const DevP
                                            cudaStream_t);
 template cudaError_t launch_populations<__nv_bfloat16, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_record_h<__nv_bfloat16, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
+template cudaError_t launch_mirror<__nv_bfloat16, 27>(const Buffers&, const DevParams&, cudaStream_t);
+template cudaError_t launch_inlet<__nv_bfloat16, 27>(const Buffers&, const DevParams&, cudaStream_t, bool);
 template cudaError_t launch_balances<__nv_bfloat16, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<__nv_bfloat16, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

@@ -12,6 +12,8 @@ template cudaError_t launch_macros<__half, 27>(const Buffers&, const DevParams&,
                                            cudaStream_t);
 template cudaError_t launch_populations<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_record_h<__half, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
+template cudaError_t launch_mirror<__half, 27>(const Buffers&, const DevParams&, cudaStream_t);
+template cudaError_t launch_inlet<__half, 27>(const Buffers&, const DevParams&, cudaStream_t, bool);
 template cudaError_t launch_balances<__half, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<__half, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

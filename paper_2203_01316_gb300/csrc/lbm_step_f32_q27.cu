@@ -12,6 +12,8 @@ template cudaError_t launch_macros<float, 27>(const Buffers&, const DevParams&, 
                                            cudaStream_t);
 template cudaError_t launch_populations<float, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_record_h<float, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
+template cudaError_t launch_mirror<float, 27>(const Buffers&, const DevParams&, cudaStream_t);
+template cudaError_t launch_inlet<float, 27>(const Buffers&, const DevParams&, cudaStream_t, bool);
 template cudaError_t launch_balances<float, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<float, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

@@ -12,6 +12,8 @@ template cudaError_t launch_macros<float, 7>(const Buffers&, const DevParams&, d
                                            cudaStream_t);
 template cudaError_t launch_populations<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_record_h<float, 7>(const Buffers&, const DevParams&, void*, cudaStream_t);
+template cudaError_t launch_mirror<float, 7>(const Buffers&, const DevParams&, cudaStream_t);
+template cudaError_t launch_inlet<float, 7>(const Buffers&, const DevParams&, cudaStream_t, bool);
 template cudaError_t launch_balances<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

@@ -12,6 +12,8 @@ template cudaError_t launch_macros<double, 27>(const Buffers&, const DevParams&,
                                            cudaStream_t);
 template cudaError_t launch_populations<double, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_record_h<double, 27>(const Buffers&, const DevParams&, void*, cudaStream_t);
+template cudaError_t launch_mirror<double, 27>(const Buffers&, const DevParams&, cudaStream_t);
+template cudaError_t launch_inlet<double, 27>(const Buffers&, const DevParams&, cudaStream_t, bool);
 template cudaError_t launch_balances<double, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<double, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);

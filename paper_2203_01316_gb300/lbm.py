@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 LBM_OK, LBM_ERR_INVALID, LBM_ERR_NOMEM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = range(6)
 STATUS = {1: "LBM_ERR_INVALID", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_STATE"}
 HKIND = {"trt": 0, "srt": 1, "1st": 2, "cum1st": 3}
+INLET_BC = {"equilibrium": 0, "zou_he": 1}
 STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
 
 # every symbol declared in include/lbm.h
@@ -46,7 +47,7 @@ class Params(C.Structure):
                 ("storage", C.c_int), ("periodic_x", C.c_int), ("nu", C.c_double), ("k", C.c_double),
                 ("Pr", C.c_double), ("omega_bulk", C.c_double), ("rho0", C.c_double), ("T_ref", C.c_double),
                 ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int), ("step_kernel", C.c_int),
-                ("wall_bc", C.c_int)]
+                ("wall_bc", C.c_int), ("inlet_bc", C.c_int)]
 WALL_BC = {"iabb": 0, "eq": 1, "abb": 2}
 STEP_KERNEL = {"auto": 0, "classic": 1, "staged": 2}
 
@@ -137,11 +138,12 @@ class Solver:
     for a library-owned stream; round_nearest: 16-bit storage rounds to
     nearest instead of stochastically; step_kernel: 'auto' | 'classic' |
     'staged' (implementation of the step, same results); wall_bc: 'iabb'
-    (Eq. IBB/IABB with q) | 'eq' (BB + EQ) | 'abb' (BB + ABB)."""
+    (Eq. IBB/IABB with q) | 'eq' (BB + EQ) | 'abb' (BB + ABB); inlet_bc:
+    'equilibrium' (fixed inlet equilibria) | 'zou_he'."""
 
     def __init__(self, nx, ny, nz, nu, k=0.0, Pr=0.0, lat_h=27, hkind="trt", storage="f32", periodic_x=True,
                  omega_bulk=1.0, rho0=1.0, T_ref=0.0, stream=None, round_nearest=False, step_kernel="auto",
-                 wall_bc="iabb"):
+                 wall_bc="iabb", inlet_bc="equilibrium"):
         self.L = lib()
         p = Params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -157,6 +159,7 @@ class Solver:
         p.round_nearest = 1 if round_nearest else 0
         p.step_kernel = STEP_KERNEL[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
         p.wall_bc = WALL_BC[wall_bc] if isinstance(wall_bc, str) else int(wall_bc)
+        p.inlet_bc = INLET_BC[inlet_bc] if isinstance(inlet_bc, str) else int(inlet_bc)
         self.params = p
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.N = p.nx * p.ny * p.nz

@@ -327,3 +327,47 @@ def test_eq_slab_is_linear_and_conserves_the_flux():
     Ti = T[2:ny - 2]
     assert np.abs(np.diff(Ti, 2)).max() < 1e-9
     assert abs(o.surface_flux(0) + o.surface_flux(1)) < 1e-9
+
+
+@pytest.mark.parametrize("qh", [27, 7])
+def test_zou_he_inlet_sets_the_prescribed_moments(qh):
+    # Sec. 4.4 inlet, reading R20: after streaming, every inlet node carries
+    # the prescribed velocity (x-momentum rho u_in, no transverse momentum)
+    # and the zeroth moment of h is rho T_in, whatever the state behind it
+    nx, ny, nz = 9, 6, 5
+    flags = np.asarray(I.channel_flags(nx, ny, nz)).reshape(-1)
+    N = nx * ny * nz
+    uin, Tin = (0.05, 0.0, 0.0), 0.7
+    o = O.Oracle(O.make_params(nx=nx, ny=ny, nz=nz, qh=qh, periodic_x=False, nu=0.05, k=0.01, u_in=uin, T_in=Tin,
+                               inlet_bc="zou_he"))
+    o.set_geometry(flags, None)
+    rng = np.random.default_rng(40)
+    u = np.stack([0.05 + 0.02 * rng.uniform(-1, 1, N), 0.02 * rng.uniform(-1, 1, N), 0.02 * rng.uniform(-1, 1, N)])
+    o.init_fields(1.0 + 0.01 * rng.uniform(-1, 1, N), u.reshape(-1), 0.7 + 0.2 * rng.uniform(-1, 1, N))
+    o.step(3)
+    f, h = o.state()
+    e = O.lattice(27)[0].astype(float)
+    inlet = np.nonzero(flags == I.INLET)[0]
+    rho = f[:, inlet].sum(axis=0)
+    mom = e.T @ f[:, inlet]
+    assert np.abs(mom[0] - rho * uin[0]).max() < 1e-14
+    assert np.abs(mom[1:]).max() < 1e-14
+    assert np.abs(h[:, inlet].sum(axis=0) - rho * Tin).max() < 1e-14
+    # the rest of the state is far from the inlet state
+    assert np.abs(f[:, inlet + 1].sum(axis=0) - 1.0).max() > 1e-4
+
+
+def test_zou_he_uniform_channel_is_steady():
+    nx, ny, nz = 12, 5, 4
+    flags = np.asarray(I.channel_flags(nx, ny, nz)).reshape(-1)
+    N = nx * ny * nz
+    o = O.Oracle(O.make_params(nx=nx, ny=ny, nz=nz, periodic_x=False, nu=0.05, k=0.01, u_in=(0.04, 0.0, 0.0),
+                               T_in=0.7, inlet_bc="zou_he"))
+    o.set_geometry(flags, None)
+    u = np.zeros((3, N))
+    u[0] = 0.04
+    o.init_fields(np.ones(N), u.reshape(-1), np.full(N, 0.7))
+    o.step(30)
+    r, uu, T = o.macros()
+    assert np.abs(r - 1).max() < 1e-14 and np.abs(uu[0] - 0.04).max() < 1e-14
+    assert np.abs(uu[1:]).max() < 1e-14 and np.abs(T - 0.7).max() < 1e-14
