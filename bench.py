@@ -527,7 +527,8 @@ def validation_hill(args):
     L, s0 = 256, 100.0
     ks = [float(v) for v in args.sizes.split(",")] if args.sizes else [1.0 / 6.0, 1e-2, 1e-3, 1e-4]
     out, lat = {}, {}
-    for storage, kind, ux in itertools.product(("f64", "f32"), ("trt", "srt", "1st", "cum1st"), (0.0, 0.1)):
+    storages = args.storages.split(",") if args.storages else ["f64", "f32"]
+    for storage, kind, ux in itertools.product(storages, ("trt", "srt", "1st", "cum1st"), (0.0, 0.1)):
         key = f"{storage}, {kind}, u_x = {ux:g}"
         out[key] = {}
         for k in ks:
@@ -736,6 +737,7 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--storages", default="", help="validation hill: comma-separated storages (f64, f32)")
     ap.add_argument("--kinds", default="", help="validation confined: comma-separated h kinds")
     ap.add_argument("--prs", default="", help="validation confined: comma-separated Prandtl numbers")
     ap.add_argument("--orders", default="", help="validation confined: wall-rule orders, '1st', '2nd' or both")
