@@ -169,6 +169,24 @@ def time_steps(s, steps, warmup, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
+def replica_time(dt, device=None):
+    """Timed region of the whole job: the replicas run at the same time, so
+    the job ends with the slowest rank (max over ranks; dt itself when not
+    distributed)."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return dt
+    t = torch.tensor([dt], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, units_per_rank, steps, dt):
+    """Whole-job throughput in millions of units per second: every rank
+    processed units_per_rank * steps in the job time dt."""
+    return world * units_per_rank * steps / dt / 1e6
+
+
 def oracle_rate(budget_s, max_steps=None):
     """FP64 oracle on a scaled copy of the workload (same shape, fewer
     nodes); returns (MLUPS, cores, sample description, steps run)."""
@@ -650,12 +668,9 @@ def run_ours(args):
     s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
     with ClockSampler(local) as clk:
         dt = time_steps(s, args.steps, args.warmup, stream)
-    if ws > 1:
-        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = replica_time(dt, device="cuda")
     mass, energy = s.balances()  # also checks that nothing diverged
-    value = ws * N * args.steps / dt / 1e6
+    value = replica_value(ws, N, args.steps, dt)
     ms = dt / args.steps * 1e3
     bpv = BYTES_PER_VALUE[args.storage]
     alg_bytes = n_active * 2 * (27 + 27) * bpv
@@ -669,7 +684,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic", "config": _config(w, args.storage),
-            "fluid_mlups": ws * n_active * args.steps / dt / 1e6,
+            "fluid_mlups": replica_value(ws, n_active, args.steps, dt),
             "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
             "balances": {"mass": mass, "energy": energy}}
     if args.no_extras:
