@@ -228,3 +228,21 @@ def test_geometry_rejections_match_oracle():
         with pytest.raises(O.OracleError):
             o.set_geometry(fl, lk, nwalls=1)
     s.set_geometry(w["flags"], w["links"], n_walls=1)
+
+
+def test_non_finite_state_is_reported_as_diverged():
+    # a non-finite temperature at one node spreads through the steps; the
+    # synchronising calls report it instead of returning numbers
+    from paper_2203_01316_gb300 import LBMError
+    w = small_channel()
+    w["T"] = w["T"].copy()
+    fluid = np.nonzero(np.asarray(w["flags"]).reshape(-1) == I.FLUID)[0]
+    w["T"][fluid[len(fluid) // 2]] = np.nan
+    s, _ = make_pair(w, nu=0.03, k=2e-3, oracle=False)
+    s.step(3)
+    with pytest.raises(LBMError) as e:
+        s.balances()
+    assert e.value.status == 4  # LBM_ERR_DIVERGED
+    with pytest.raises(LBMError) as e:
+        s.macros()
+    assert e.value.status == 4

@@ -13,8 +13,10 @@ Tolerance for the hill in FP32: populations are stored as deviations from
 w T_ref with T_ref = 1 and rounded to about 1e-8 each step, the collision
 closes the zeroth moment exactly, and the temperature is read back in FP32
 (one ulp of T ~ 1 is 1.2e-7).  Over 2400 steps the largest difference
-measured on GB300 is 4.0e-7; the bound used is 1e-6 absolute, 9e-6 of the
-hill's 0.11 final height."""
+measured on GB300 is 4.0e-7 for D3Q27 and 1.4e-6 for D3Q7 (its rest weight
+is zero, so the rest population that closes the zeroth moment carries the
+others' rounding); the bound used is 3e-6 absolute, 2.7e-5 of the hill's
+0.11 final height."""
 import numpy as np
 import pytest
 
@@ -111,7 +113,7 @@ def test_hill_unit_rate_full_size_is_the_lattice_convolution(Q, kind, ux):
     n = 2400
     C0, C = _gpu_hill(1.0 / 6.0, n, ux, kind, Q)
     ref = np.real(np.fft.ifft2(np.fft.fft2(C0) * _transfer(C0.shape[0], (ux, 0.0), Q) ** n))
-    assert np.abs(C - ref).max() < 1e-6
+    assert np.abs(C - ref).max() < 3e-6
 
 
 def _hill_l2(C, L, s0, k, n, ux):
