@@ -49,7 +49,8 @@ def _params(**kw):
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(lat_h=19), dict(hkind=7), dict(storage=9), dict(nu=-1.0),
                                  dict(k=0.0, Pr=0.0), dict(k=2e-4, Pr=50.0), dict(omega_bulk=2.5),
-                                 dict(nx=2048, ny=2048, nz=32), dict(periodic_x=0, nx=3)])
+                                 dict(nx=2048, ny=2048, nz=32), dict(periodic_x=0, nx=3), dict(wall_bc=3),
+                                 dict(inlet_bc=2), dict(step_kernel=5), dict(hkind=4)])
 def test_invalid_parameters_rejected_without_gpu(L, bad):
     h = C.c_void_p()
     st = L.lbm_create(C.byref(_params(**bad)), C.byref(h))
