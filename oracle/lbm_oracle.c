@@ -1229,3 +1229,240 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     free(hrec);
     return 0;
 }
+
+/* ---- adjoint of the coupled f + h evolution --------------------------------
+ * Gradients of the same objectives with respect to parameters of the flow:
+ * the body force F (reading R2) and the inlet velocity u_in (reading R6).
+ * The h step depends on the flow through u, so the adjoint carries an f
+ * part: with the pre-collision arrivals g_f, g_h of level k,
+ *     s_f = C_f(g_f; F),  u = U(g_f; F),  s_h = C_h(g_h, u; Q)
+ * (Eq. hydro_cu_collision, Eq. H_cm_collision / H_cu_collision), and the
+ * reverse sweep applies, per node,
+ *     w   = (dC_h/du)^T lambda_h
+ *     mu_f = (dC_f/dg_f)^T lambda_f + (dU/dg_f)^T w
+ *     mu_h = (dC_h/dg_h)^T lambda_h
+ *     dJ/dF += (dC_f/dF)^T lambda_f + (dU/dF)^T w,   dJ/dQ += (dC_h/dQ)^T lambda_h,
+ * with lambda = P^T mu^{k+1} + dJ/ds^k as before (streaming, Eq. IBB for f,
+ * Eq. IABB for h, the planes).  The inlet plane holds the equilibria at u_in
+ * at every level k >= 1, so dJ/du_in += (d f^eq_in/du_in)^T lambda_f +
+ * (d h^eq_in/du_in)^T lambda_h there.  Every Jacobian is read off the
+ * forward functions themselves by 4-point central differences,
+ * D = [8 (F(x+e) - F(x-e)) - (F(x+2e) - F(x-2e))] / (12 e), whose error is
+ * O(e^4): exact for the polynomial dependence on u and F, and at the level
+ * of rounding for the rational dependence on the density. */
+static double cd4(double fp1, double fm1, double fp2, double fm2, double e) {
+    return (8.0 * (fp1 - fm1) - (fp2 - fm2)) / (12.0 * e);
+}
+
+/* lam += P_f^T mu (transpose of the f part of orc_stream). */
+static void stream_transpose_f(const orc_sim* s, const double* mu, double* lam) {
+    const int N = s->N, nx = s->p.nx;
+    const lattice_t* L = lattice(27);
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] == FL_SOLID) continue;
+        for (int a = 0; a < 27; ++a) {
+            int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
+            if (t < 0 || s->flags[t] == FL_SOLID || s->flags[t] == FL_INLET) continue;
+            lam[(size_t)a * N + n] += mu[(size_t)a * N + t];
+        }
+    }
+    for (int n = 0; n < N; ++n) { /* Eq. IBB: the arrival ab at n from the link (n, a) */
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int a = 1; a < 27; ++a) {
+            float qf = s->qtab[(size_t)n * 27 + a];
+            if (qf < 0.0f) continue;
+            int ab = L->opp[a];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            const double q = q_eff(s, qf);
+            const double m = mu[(size_t)ab * N + n];
+            if (q <= 0.5 && !thin) {
+                lam[(size_t)a * N + n] += 2.0 * q * m;
+                lam[(size_t)a * N + xf] += (1.0 - 2.0 * q) * m;
+            } else {
+                const double qq = q <= 0.5 ? 0.5 : q;
+                lam[(size_t)a * N + n] += m / (2.0 * qq);
+                lam[(size_t)ab * N + n] += (2.0 * qq - 1.0) / (2.0 * qq) * m;
+            }
+        }
+    }
+    if (!s->p.periodic_x) {
+        for (int n = 0; n < N; ++n) {
+            if (s->flags[n] != FL_OUTLET || n % nx != nx - 1) continue;
+            for (int a = 0; a < 27; ++a) {
+                if (L->e[a][0] >= 0) continue;
+                int src = neighbour(s, n, 0, -L->e[a][1], -L->e[a][2]);
+                lam[(size_t)a * N + src] += mu[(size_t)a * N + n];
+            }
+        }
+    }
+}
+
+/* Returns 0, -1 on a streaming error, -3 for a geometry with symmetry rows or
+ * a Zou-He inlet.  dF[3] and duin[3] (and dtheta[N], dTw[nwalls]) are added to. */
+int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
+                     int wall, int plane, double weight, double* J, double* dtheta, double* dTw, double* dF,
+                     double* duin) {
+    const int N = s->N, qh = s->p.qh;
+    const size_t FN = (size_t)27 * N, HN = (size_t)qh * N;
+    if (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x)) return -3;
+    double* frec = (double*)malloc((size_t)(nsteps + 1) * FN * sizeof(double));
+    double* hrec = (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double));
+    orc_set_post(s, f_post, h_post);
+    double Jv = 0.0;
+    for (int k = 0; k <= nsteps; ++k) {
+        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane);
+        if (k == nsteps) break;
+        if (orc_stream(s) != 0) { free(frec); free(hrec); return -1; }
+        memcpy(frec + (size_t)(k + 1) * FN, s->f, FN * sizeof(double));
+        memcpy(hrec + (size_t)(k + 1) * HN, s->h, HN * sizeof(double));
+        orc_collide(s);
+    }
+    *J = Jv;
+    const lattice_t* L = lattice(27);
+    const lattice_t* Lh = lattice(qh);
+    /* derivatives of the inlet equilibria with respect to u_in */
+    double dfin[3][27], dhin[3][27];
+    {
+        const double e = 1e-3;
+        for (int d = 0; d < 3; ++d) {
+            double fv[4][27], hv[4][27];
+            const double off[4] = {e, -e, 2 * e, -2 * e};
+            for (int j = 0; j < 4; ++j) {
+                double u[3] = {s->p.u_in[0], s->p.u_in[1], s->p.u_in[2]};
+                u[d] += off[j];
+                equilibrium(L, 1.0, u, fv[j]);
+                equilibrium(Lh, s->p.T_in, u, hv[j]);
+            }
+            for (int a = 0; a < 27; ++a) dfin[d][a] = cd4(fv[0][a], fv[1][a], fv[2][a], fv[3][a], e);
+            for (int a = 0; a < qh; ++a) dhin[d][a] = cd4(hv[0][a], hv[1][a], hv[2][a], hv[3][a], e);
+        }
+    }
+    double* muf = (double*)calloc(FN, sizeof(double));
+    double* muh = (double*)calloc(HN, sizeof(double));
+    double* lamf = (double*)calloc(FN, sizeof(double));
+    double* lamh = (double*)calloc(HN, sizeof(double));
+    double* gF = (double*)calloc((size_t)3 * N, sizeof(double));
+    for (int k = nsteps; k >= 0; --k) {
+        for (size_t i = 0; i < FN; ++i) lamf[i] = 0.0;
+        for (size_t i = 0; i < HN; ++i) lamh[i] = 0.0;
+        if (k < nsteps) {
+            stream_transpose_f(s, muf, lamf);
+            stream_transpose_h(s, muh, lamh, dTw);
+        }
+        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, weight, lamh, dTw);
+        for (size_t i = 0; i < FN; ++i) muf[i] = 0.0;
+        for (size_t i = 0; i < HN; ++i) muh[i] = 0.0;
+        if (k == 0) break;
+        /* inlet nodes hold the equilibria at u_in */
+        if (!s->p.periodic_x && duin) {
+            for (int n = 0; n < N; ++n) {
+                if (s->flags[n] != FL_INLET) continue;
+                for (int d = 0; d < 3; ++d) {
+                    double acc = 0.0;
+                    for (int a = 0; a < 27; ++a) acc += dfin[d][a] * lamf[(size_t)a * N + n];
+                    for (int a = 0; a < qh; ++a) acc += dhin[d][a] * lamh[(size_t)a * N + n];
+                    duin[d] += acc;
+                }
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int n = 0; n < N; ++n) {
+            if (s->flags[n] == FL_SOLID || s->flags[n] == FL_INLET) continue;
+            double g[27], gh[27], u[3], fs0[27], hs0[27];
+            for (int a = 0; a < 27; ++a) g[a] = frec[(size_t)k * FN + (size_t)a * N + n];
+            for (int a = 0; a < qh; ++a) gh[a] = hrec[(size_t)k * HN + (size_t)a * N + n];
+            const double Q = theta_at(s, n);
+            collide_f(&s->p, g, fs0, u);
+            double lf[27], lh[27];
+            for (int a = 0; a < 27; ++a) lf[a] = lamf[(size_t)a * N + n];
+            for (int a = 0; a < qh; ++a) lh[a] = lamh[(size_t)a * N + n];
+            /* w = (dC_h/du)^T lambda_h and (dC_h/dg_h)^T lambda_h, dC_h/dQ */
+            double w[3];
+            {
+                const double e = 1e-3;
+                const double off[4] = {e, -e, 2 * e, -2 * e};
+                for (int d = 0; d < 3; ++d) {
+                    double v[4];
+                    for (int j = 0; j < 4; ++j) {
+                        double uu[3] = {u[0], u[1], u[2]}, hs[27];
+                        uu[d] += off[j];
+                        collide_h(&s->p, gh, uu, Q, hs);
+                        double dot = 0.0;
+                        for (int a = 0; a < qh; ++a) dot += lh[a] * hs[a];
+                        v[j] = dot;
+                    }
+                    w[d] = cd4(v[0], v[1], v[2], v[3], e);
+                }
+                const double eh = 1e-4;
+                const double offh[4] = {eh, -eh, 2 * eh, -2 * eh};
+                for (int b = 0; b < qh; ++b) {
+                    double v[4];
+                    for (int j = 0; j < 4; ++j) {
+                        double gg[27], hs[27];
+                        for (int a = 0; a < qh; ++a) gg[a] = gh[a];
+                        gg[b] += offh[j];
+                        collide_h(&s->p, gg, u, Q, hs);
+                        double dot = 0.0;
+                        for (int a = 0; a < qh; ++a) dot += lh[a] * hs[a];
+                        v[j] = dot;
+                    }
+                    muh[(size_t)b * N + n] = cd4(v[0], v[1], v[2], v[3], eh);
+                }
+                if (dtheta) {
+                    double v[4];
+                    for (int j = 0; j < 4; ++j) {
+                        double hs[27];
+                        collide_h(&s->p, gh, u, Q + offh[j], hs);
+                        double dot = 0.0;
+                        for (int a = 0; a < qh; ++a) dot += lh[a] * hs[a];
+                        v[j] = dot;
+                    }
+                    dtheta[n] += cd4(v[0], v[1], v[2], v[3], eh);
+                }
+            }
+            /* mu_f = (dC_f/dg)^T lambda_f + (dU/dg)^T w */
+            {
+                const double e = 1e-4;
+                const double off[4] = {e, -e, 2 * e, -2 * e};
+                for (int b = 0; b < 27; ++b) {
+                    double v[4];
+                    for (int j = 0; j < 4; ++j) {
+                        double gg[27], fs[27], uu[3];
+                        for (int a = 0; a < 27; ++a) gg[a] = g[a];
+                        gg[b] += off[j];
+                        collide_f(&s->p, gg, fs, uu);
+                        double dot = 0.0;
+                        for (int a = 0; a < 27; ++a) dot += lf[a] * fs[a];
+                        for (int d = 0; d < 3; ++d) dot += w[d] * uu[d];
+                        v[j] = dot;
+                    }
+                    muf[(size_t)b * N + n] = cd4(v[0], v[1], v[2], v[3], e);
+                }
+                /* dJ/dF: F enters the collision and the velocity of h */
+                for (int d = 0; d < 3; ++d) {
+                    double v[4];
+                    for (int j = 0; j < 4; ++j) {
+                        orc_params pp = s->p;
+                        pp.F[d] += off[j];
+                        double fs[27], uu[3];
+                        collide_f(&pp, g, fs, uu);
+                        double dot = 0.0;
+                        for (int a = 0; a < 27; ++a) dot += lf[a] * fs[a];
+                        for (int dd = 0; dd < 3; ++dd) dot += w[dd] * uu[dd];
+                        v[j] = dot;
+                    }
+                    gF[(size_t)d * N + n] += cd4(v[0], v[1], v[2], v[3], e);
+                }
+            }
+        }
+    }
+    if (dF)
+        for (int d = 0; d < 3; ++d) {
+            double acc = 0.0;
+            for (int n = 0; n < N; ++n) acc += gF[(size_t)d * N + n];
+            dF[d] += acc;
+        }
+    free(muf); free(muh); free(lamf); free(lamh); free(gF); free(frec); free(hrec);
+    return 0;
+}

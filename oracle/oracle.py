@@ -111,6 +111,10 @@ def lib():
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
                                   C.c_void_p]
+        L.orc_adjoint_flow.restype = C.c_int
+        L.orc_adjoint_flow.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]
     return _lib
 
 
@@ -295,3 +299,26 @@ class Oracle:
             raise OracleError("orc_adjoint: " + ("no adjoint with symmetry rows or a Zou-He inlet" if rc == -3
                                                  else "streaming error"))
         return J.value, dth, dTw
+
+    def adjoint_flow(self, f_post, h_post, nsteps, window, objective, nwalls=1):
+        """Adjoint of the coupled f + h evolution: (J, dJ/dtheta[N],
+        dJ/dT_w[nwalls], dJ/dF[3], dJ/du_in[3]) for the objective of
+        adjoint() (F: body force; u_in: inlet velocity of the equilibrium
+        inlet plane)."""
+        kind = 0 if objective[0] == "surface" else 1
+        wall = int(objective[1]) if kind == 0 else 0
+        plane = int(objective[1]) if kind == 1 else 0
+        f_post = np.ascontiguousarray(f_post, dtype=np.float64)
+        h_post = np.ascontiguousarray(h_post, dtype=np.float64)
+        J = C.c_double()
+        dth = np.zeros(self.N)
+        dTw = np.zeros(nwalls)
+        dF = np.zeros(3)
+        duin = np.zeros(3)
+        rc = lib().orc_adjoint_flow(self._h, f_post.ctypes.data, h_post.ctypes.data, int(nsteps), int(window[0]),
+                                    int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
+                                    dth.ctypes.data, dTw.ctypes.data, dF.ctypes.data, duin.ctypes.data)
+        if rc != 0:
+            raise OracleError("orc_adjoint_flow: " + ("no adjoint with symmetry rows or a Zou-He inlet"
+                                                      if rc == -3 else "streaming error"))
+        return J.value, dth, dTw, dF, duin

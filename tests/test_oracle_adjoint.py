@@ -168,3 +168,50 @@ def test_objective_value_matches_surface_flux():
     o2.set_theta(w["theta"])
     o2.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
     assert abs(J - o2.surface_flux(0)) < 1e-14
+
+
+# ---- the coupled f + h adjoint: gradients with respect to the flow --------
+def _J_flow(w, p, Tw, fpost, hpost, nsteps, window, obj, F=None, u_in=None):
+    q = O.make_params(nx=p.nx, ny=p.ny, nz=p.nz, qh=p.qh, hkind=p.hkind, periodic_x=bool(p.periodic_x), nu=p.nu,
+                      k=p.k, F=tuple(p.F) if F is None else F, u_in=tuple(p.u_in) if u_in is None else u_in,
+                      T_in=p.T_in, wall_bc=p.wall_bc)
+    return _J(w, q, Tw, w["theta"], fpost, hpost, nsteps, window, obj)
+
+
+def _replace(vec, d, x):
+    v = list(vec)
+    v[d] = x
+    return tuple(v)
+
+
+@pytest.mark.parametrize("case,kind,qh", [("plate", "trt", 27), ("plate", "cum1st", 27), ("channel", "trt", 27),
+                                          ("channel", "srt", 7)])
+def test_flow_adjoint_matches_finite_differences(case, kind, qh):
+    # Eq. hydro_cu_collision + Eq. H_cm_collision (or H_cu_collision) coupled
+    # through u: dJ/dF and dJ/du_in against Richardson-extrapolated central
+    # differences of the nonlinear J; the theta and T_w gradients equal the
+    # h-only adjoint's
+    if case == "plate":
+        w, p = _plate_case(qh, kind)
+        Tw, obj, (nsteps, window) = [1.0, 0.1], ("surface", 1, 0.7), (8, (3, 8))
+    else:
+        w, p = _channel_case(qh, kind)
+        Tw, obj, (nsteps, window) = [1.0], ("surface", 0, 1.0), (9, (3, 9))
+    o, fpost, hpost = _setup(w, p, Tw)
+    J, dth, dTw, dF, duin = o.adjoint_flow(fpost, hpost, nsteps, window, obj, nwalls=len(Tw))
+    J0, dth0, dTw0 = o.adjoint(fpost, hpost, nsteps, window, obj, nwalls=len(Tw))
+    assert abs(J - J0) <= 1e-14 * abs(J0)
+    assert np.abs(dth - dth0).max() <= 1e-9 * np.abs(dth0).max()
+    assert np.abs(dTw - dTw0).max() <= 1e-9 * np.abs(dTw0).max()
+    scale = max(np.abs(dF).max(), np.abs(duin).max())
+    for d in range(3):
+        fd = _richardson(lambda x: _J_flow(w, p, Tw, fpost, hpost, nsteps, window, obj,
+                                           F=_replace(p.F, d, x)), p.F[d], 2e-4)
+        assert abs(dF[d] - fd) <= 1e-7 * max(abs(fd), 1e-3 * scale), (d, dF[d], fd)
+    if case == "channel":
+        for d in range(3):
+            fd = _richardson(lambda x: _J_flow(w, p, Tw, fpost, hpost, nsteps, window, obj,
+                                               u_in=_replace(p.u_in, d, x)), p.u_in[d], 2e-4)
+            assert abs(duin[d] - fd) <= 1e-7 * max(abs(fd), 1e-3 * scale), (d, duin[d], fd)
+    else:
+        assert np.all(duin == 0.0)
