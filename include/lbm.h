@@ -272,6 +272,41 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_ne
 lbm_status lbm_adjoint_step_h(lbm_ctx* ctx, const void* u_level, const void* h_level, const void* mu_next, void* out,
                               const lbm_objective* obj, double* dJ_dtheta);
 
+/* ---- adjoint of the coupled f + h evolution ---------------------------------
+ * Gradients of the same objectives with respect to parameters of the flow,
+ * the body force F (lbm_set_force) and the inlet velocity u_in (the
+ * equilibrium inlet plane of lbm_set_inlet): the h step depends on the flow
+ * through u, so this sweep carries the adjoint of f as well (Eq.
+ * hydro_cu_collision, Eq. IBB) next to that of h (Eq. H_cm_collision or
+ * H_cu_collision, Eq. IABB).  FP32 or FP64 storage only (LBM_ERR_INVALID
+ * otherwise); not with symmetry rows or the Zou-He inlet.  Adjoint arrays:
+ * element type float (FP32) or double (FP64), SoA [27][N] for f and [Q_h][N]
+ * for h. */
+
+/* lbm_step_record with advance_h = 1 that records, for each step k = 1..n,
+ * the pre-collision arrivals of every non-solid, non-inlet node (after
+ * streaming, the walls and the planes) as deviations: f at f_rec + (k-1)*27*N
+ * and h at h_rec + (k-1)*Q_h*N (device). */
+lbm_status lbm_step_record_pre(lbm_ctx* ctx, int n, void* f_rec, void* h_rec);
+
+/* One level k of the coupled adjoint sweep: from the adjoints of the next
+ * level's arrivals (muf_next, muh_next; zeros at the last level) and the
+ * level's records (f_level, h_level from lbm_step_record_pre; both NULL at
+ * the initial level, whose state is given), writes mu^k to muf_out, muh_out,
+ * adds dJ/dtheta to dJ_dtheta[N] (device double, may be NULL), and
+ * accumulates dJ/dF, dJ/du_in (lbm_adjoint_flow_gradient) and dJ/dT_w
+ * (lbm_adjoint_wall_gradient) inside the context.  obj: the objective term of
+ * level k or NULL.  The *_next arrays must be zero at solid and inlet nodes
+ * (true of zero-filled arrays and of every out this call writes); inputs and
+ * outputs must not alias.  Asynchronous. */
+lbm_status lbm_adjoint_flow_step(lbm_ctx* ctx, const void* f_level, const void* h_level, const void* muf_next,
+                                 const void* muh_next, void* muf_out, void* muh_out, const lbm_objective* obj,
+                                 double* dJ_dtheta);
+
+/* dJ/dF[3] and dJ/du_in[3] (host double) accumulated by lbm_adjoint_flow_step
+ * since the last reset; reset = 1 clears the accumulators.  Synchronises. */
+lbm_status lbm_adjoint_flow_gradient(lbm_ctx* ctx, double* dJ_dF, double* dJ_duin, int reset);
+
 /* dJ/dT_w accumulated by lbm_adjoint_step since the last reset, per wall
  * (host double[n_walls]); reset = 1 clears the accumulators.  Synchronises. */
 lbm_status lbm_adjoint_wall_gradient(lbm_ctx* ctx, double* dJ_dTwall, int reset);

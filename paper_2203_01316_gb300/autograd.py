@@ -94,3 +94,83 @@ def thermal_objective(theta, T_wall, solver, state0, nsteps, window, objective, 
     """J(theta, T_wall) with gradients by the adjoint (see module docstring).
     state0: CUDA uint8 tensor from solver.save_state(out=...)."""
     return ThermalObjective.apply(theta, T_wall, solver, state0, nsteps, window, objective, every)
+
+
+class FlowObjective(torch.autograd.Function):
+    """The same objective as ThermalObjective, differentiable also with
+    respect to the flow's parameters: the body force F[3] and the inlet
+    velocity u_in[3] (equilibrium inlet plane).  The backward runs the
+    adjoint of the coupled f + h evolution (include/lbm.h, "adjoint of the
+    coupled f + h evolution"): per segment it restores the checkpoint,
+    recomputes the segment recording each level's pre-collision arrivals, and
+    runs the coupled adjoint level by level.  FP32 or FP64 storage."""
+
+    @staticmethod
+    def forward(ctx, theta, T_wall, F, u_in, solver: Solver, state0, nsteps: int, window, objective, every: int):
+        if every < 1:
+            raise ValueError("checkpoint interval must be >= 1")
+        dev = state0.device
+        torch.cuda.synchronize(dev)
+        solver.set_source(theta.detach().to(device=dev, dtype=torch.float32))
+        torch.cuda.synchronize(dev)
+        for w, T in enumerate(T_wall.detach().cpu().tolist()):
+            solver.set_bc(w, T)
+        solver.set_force(F.detach().cpu().tolist())
+        T_in = solver.inlet[1] if getattr(solver, "inlet", None) else 0.0
+        solver.set_inlet(u_in.detach().cpu().tolist(), T_in)
+        solver.load_state(state0)
+        J = torch.zeros(1, dtype=torch.float64, device=dev)
+        ckpts = {}
+        for k in range(nsteps + 1):
+            if k % every == 0 and k < nsteps:
+                ckpts[k] = solver.save_state(torch.empty_like(state0))
+            if window[0] <= k <= window[1]:
+                solver.objective_accumulate(objective, J)
+            if k < nsteps:
+                solver.step(1)
+        solver.sync()
+        ctx.solver, ctx.ckpts, ctx.nsteps, ctx.window = solver, ckpts, nsteps, window
+        ctx.objective, ctx.every, ctx.n_walls = objective, every, T_wall.numel()
+        ctx.meta = [(t.dtype, t.device) for t in (theta, T_wall, F, u_in)]
+        return J[0]
+
+    @staticmethod
+    def backward(ctx, gJ):
+        s: Solver = ctx.solver
+        N, qh = s.N, s.qh
+        dev = next(iter(ctx.ckpts.values())).device if ctx.ckpts else torch.device("cuda")
+        rdt = torch.float64 if s.params.storage == 1 else torch.float32
+        muf = [torch.zeros(27 * N, dtype=rdt, device=dev), torch.empty(27 * N, dtype=rdt, device=dev)]
+        muh = [torch.zeros(qh * N, dtype=rdt, device=dev), torch.empty(qh * N, dtype=rdt, device=dev)]
+        dtheta = torch.zeros(N, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        s.adjoint_wall_gradient(ctx.n_walls, reset=True)
+        s.adjoint_flow_gradient(reset=True)
+        lo, hi = ctx.window
+        cur = 0
+        for seg_start in sorted(ctx.ckpts, reverse=True):
+            seg_end = min(seg_start + ctx.every, ctx.nsteps)
+            L = seg_end - seg_start
+            s.load_state(ctx.ckpts[seg_start])
+            frec = torch.empty(L * 27 * N, dtype=rdt, device=dev)
+            hrec = torch.empty(L * qh * N, dtype=rdt, device=dev)
+            s.step_record_pre(L, frec, hrec)
+            for k in range(seg_end, seg_start, -1):
+                obj = ctx.objective if lo <= k <= hi else None
+                j = k - seg_start - 1
+                s.adjoint_flow_step(frec[j * 27 * N:(j + 1) * 27 * N], hrec[j * qh * N:(j + 1) * qh * N],
+                                    muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj, dtheta)
+                cur = 1 - cur
+        obj0 = ctx.objective if lo <= 0 <= hi else None
+        s.adjoint_flow_step(None, None, muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj0, None)
+        dTw = s.adjoint_wall_gradient(ctx.n_walls, reset=True)
+        dF, duin = s.adjoint_flow_gradient(reset=True)  # synchronises the solver's stream
+        gJ = gJ.detach().to(torch.float64).cpu()
+        grads = [dtheta.cpu(), torch.from_numpy(dTw), torch.from_numpy(dF), torch.from_numpy(duin)]
+        out = [(gJ * g).to(dtype=dt, device=dv) for g, (dt, dv) in zip(grads, ctx.meta)]
+        return out[0], out[1], out[2], out[3], None, None, None, None, None, None
+
+
+def flow_objective(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every=50):
+    """J(theta, T_wall, F, u_in) with gradients by the coupled adjoint."""
+    return FlowObjective.apply(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every)

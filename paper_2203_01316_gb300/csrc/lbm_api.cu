@@ -44,6 +44,9 @@ struct lbm_ctx {
     int32_t* d_roff = nullptr;
     int32_t* d_rlink = nullptr;
     double* d_dlink = nullptr;      // adjoint: per link dJ/dT_w accumulators
+    double* d_flowacc = nullptr;    // coupled adjoint: per node (dJ/dF, dJ/du_in) accumulators, [N][6]
+    void* d_din = nullptr;          // coupled adjoint: d(inlet state)/du_in, R[3][27 + qh]
+    std::vector<double> h_din;      // the uploaded copy of d_din
     int n_walls = 1;
     float* d_Twall = nullptr;
     std::vector<float> Twall{0.0f};
@@ -142,6 +145,33 @@ Buffers buffers(const lbm_ctx* c) {
 double w1eq(int e, double u) {
     const double cs2 = 1.0 / 3.0;
     return e == 0 ? 1.0 - u * u - cs2 : 0.5 * (u * u + e * u + cs2);
+}
+
+// derivative of w1eq with respect to u
+double dw1eq(int e, double u) { return e == 0 ? -2.0 * u : u + 0.5 * e; }
+
+// d(inlet post-collision state)/du_in,d for d = 0, 1, 2: [3][27 + qh]
+std::vector<double> inlet_derivative(const lbm_ctx* c) {
+    const int qh = c->qh;
+    std::vector<double> v((size_t)3 * (27 + qh), 0.0);
+    const double* u = c->dp.uin;
+    const double T = c->dp.Tin;
+    for (int d = 0; d < 3; ++d) {
+        double* row = v.data() + (size_t)d * (27 + qh);
+        for (int a = 0; a < 27; ++a) {
+            const int e[3] = {lbmd::EX(a), lbmd::EY(a), lbmd::EZ(a)};
+            double prod = 1.0;
+            for (int k = 0; k < 3; ++k) prod *= (k == d) ? dw1eq(e[k], u[k]) : w1eq(e[k], u[k]);
+            row[a] = prod;
+            if (qh == 27) row[27 + a] = T * prod;
+        }
+        if (qh == 7) {
+            row[27] = -2.0 * T * u[d];
+            row[28 + d] = 0.5 * T * (2.0 * u[d] + 1.0);
+            row[31 + d] = 0.5 * T * (2.0 * u[d] - 1.0);
+        }
+    }
+    return v;
 }
 
 // inlet post-collision deviations (f^eq(1, u_in) - w rho0, h^eq(T_in, u_in) - w Tref)
@@ -350,6 +380,8 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_stage);
     cudaFree(c->d_Twall);
     cudaFree(c->d_theta);
+    cudaFree(c->d_flowacc);
+    cudaFree(c->d_din);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
@@ -1090,6 +1122,118 @@ static lbm_status adjoint_step_impl(lbm_ctx* c, const void* u_level, const void*
 lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next, void* out,
                             const lbm_objective* obj, double* dJ_dtheta) {
     return adjoint_step_impl(c, u_level, nullptr, mu_next, out, obj, dJ_dtheta);
+}
+
+lbm_status lbm_step_record_pre(lbm_ctx* c, int n, void* f_rec, void* h_rec) {
+    if (!c) return LBM_ERR_INVALID;
+    if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
+    if (n > 0 && (!f_rec || !h_rec)) return fail(c, LBM_ERR_INVALID, "null f or h record");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    if (c->p.storage != LBM_F32 && c->p.storage != LBM_F64)
+        return fail(c, LBM_ERR_INVALID, "pre-collision records need FP32 or FP64 storage");
+    DeviceGuard g(c->device);
+    const size_t rsize = c->ssize;
+    for (int i = 0; i < n; ++i) {
+        Buffers b = buffers(c);
+        c->dp.step += 1;
+        const DevParams p = c->dp;
+        b.frec = (char*)f_rec + (size_t)i * 27 * c->N * rsize;
+        b.hrec = (char*)h_rec + (size_t)i * c->qh * c->N * rsize;
+        cudaError_t e = fill_mirror(c, b, p);
+        if (e != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
+        e = dispatch(c, [&](auto tag) {
+            using Tg = decltype(tag);
+            return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream, true);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        if ((e = zou_he_inlet(c, b, p, true)) != cudaSuccess) return cuda_fail(c, e, "inlet launch");
+        c->cur_f = 1 - c->cur_f;
+        c->cur_h = 1 - c->cur_h;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_flow_step(lbm_ctx* c, const void* f_level, const void* h_level, const void* muf_next,
+                                 const void* muh_next, void* muf_out, void* muh_out, const lbm_objective* obj,
+                                 double* dJ_dtheta) {
+    if (!c || !muf_next || !muh_next || !muf_out || !muh_out) return LBM_ERR_INVALID;
+    if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
+    if (c->p.storage != LBM_F32 && c->p.storage != LBM_F64)
+        return fail(c, LBM_ERR_INVALID, "the coupled adjoint needs FP32 or FP64 storage");
+    if (c->dp.mirror_lo || c->dp.mirror_hi)
+        return fail(c, LBM_ERR_INVALID, "the adjoint does not cover symmetry rows");
+    if (c->dp.zou_he) return fail(c, LBM_ERR_INVALID, "the adjoint does not cover the Zou-He inlet");
+    if ((f_level == nullptr) != (h_level == nullptr))
+        return fail(c, LBM_ERR_INVALID, "give both level records or neither (initial level)");
+    lbm_status st = check_objective(c, obj);
+    if (st != LBM_OK) return st;
+    DeviceGuard g(c->device);
+    const size_t rsize = c->ssize;
+    if (!c->d_flowacc) {
+        if (cudaMalloc(&c->d_flowacc, (size_t)c->N * 6 * sizeof(double)) != cudaSuccess)
+            return fail(c, LBM_ERR_NOMEM, "coupled adjoint accumulators");
+        CK(cudaMemsetAsync(c->d_flowacc, 0, (size_t)c->N * 6 * sizeof(double), c->stream), "accumulators");
+    }
+    if (!c->d_din && cudaMalloc(&c->d_din, (size_t)3 * (27 + c->qh) * rsize) != cudaSuccess)
+        return fail(c, LBM_ERR_NOMEM, "inlet derivative table");
+    std::vector<double> din = inlet_derivative(c);
+    if (din != c->h_din) {
+        CK(cudaStreamSynchronize(c->stream), "inlet derivative table");
+        if (c->p.storage == LBM_F64) {
+            CK(cudaMemcpy(c->d_din, din.data(), din.size() * sizeof(double), cudaMemcpyHostToDevice),
+               "inlet derivative table");
+        } else {
+            std::vector<float> df(din.begin(), din.end());
+            CK(cudaMemcpy(c->d_din, df.data(), df.size() * sizeof(float), cudaMemcpyHostToDevice),
+               "inlet derivative table");
+        }
+        c->h_din = din;
+    }
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    const lbmd::AdjObjective a = to_adj(obj);
+    cudaError_t e;
+    if (c->p.storage == LBM_F64) {
+        using R = double;
+        e = c->qh == 27 ? lbmd::launch_adjoint_flow<R, 27>(b, p, (const R*)f_level, (const R*)h_level,
+                                                          (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
+                                                          (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
+                                                          (const R*)c->d_din, c->stream)
+                        : lbmd::launch_adjoint_flow<R, 7>(b, p, (const R*)f_level, (const R*)h_level,
+                                                         (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
+                                                         (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
+                                                         (const R*)c->d_din, c->stream);
+    } else {
+        using R = float;
+        e = c->qh == 27 ? lbmd::launch_adjoint_flow<R, 27>(b, p, (const R*)f_level, (const R*)h_level,
+                                                          (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
+                                                          (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
+                                                          (const R*)c->d_din, c->stream)
+                        : lbmd::launch_adjoint_flow<R, 7>(b, p, (const R*)f_level, (const R*)h_level,
+                                                         (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
+                                                         (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
+                                                         (const R*)c->d_din, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "coupled adjoint launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_flow_gradient(lbm_ctx* c, double* dJ_dF, double* dJ_duin, int reset) {
+    if (!c || !dJ_dF || !dJ_duin) return LBM_ERR_INVALID;
+    DeviceGuard g(c->device);
+    for (int d = 0; d < 3; ++d) dJ_dF[d] = dJ_duin[d] = 0.0;
+    if (!c->d_flowacc) return LBM_OK;
+    CK(lbmd::launch_reduce6(c->d_flowacc, c->N, c->d_scratch, c->stream), "flow gradient reduction");
+    double out[6];
+    CK(cudaMemcpyAsync(out, c->d_scratch, sizeof(out), cudaMemcpyDeviceToHost, c->stream), "flow gradient copy");
+    if (reset)
+        CK(cudaMemsetAsync(c->d_flowacc, 0, (size_t)c->N * 6 * sizeof(double), c->stream), "flow gradient reset");
+    CK(cudaStreamSynchronize(c->stream), "flow gradient");
+    for (int d = 0; d < 3; ++d) {
+        dJ_dF[d] = out[d];
+        dJ_duin[d] = out[3 + d];
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_adjoint_step_h(lbm_ctx* c, const void* u_level, const void* h_level, const void* mu_next, void* out,

@@ -143,6 +143,33 @@ __device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t step) {
 // ---- moment algebra --------------------------------------------------------
 template <typename R> __device__ __forceinline__ constexpr R cs2() { return R(1) / R(3); }
 
+// forward-mode dual number v + d eps: runs the collision functions (templated
+// on the arithmetic type) to give directional derivatives for the coupled
+// adjoint
+template <typename T> struct Dual {
+    T v, d;
+    __host__ __device__ constexpr Dual() : v(0), d(0) {}
+    __host__ __device__ constexpr Dual(double x) : v((T)x), d(0) {}
+    __host__ __device__ constexpr Dual(T x, T dx, int) : v(x), d(dx) {}
+    friend __host__ __device__ constexpr Dual operator+(const Dual& a, const Dual& b) {
+        return Dual(a.v + b.v, a.d + b.d, 0);
+    }
+    friend __host__ __device__ constexpr Dual operator-(const Dual& a, const Dual& b) {
+        return Dual(a.v - b.v, a.d - b.d, 0);
+    }
+    friend __host__ __device__ constexpr Dual operator*(const Dual& a, const Dual& b) {
+        return Dual(a.v * b.v, a.d * b.v + a.v * b.d, 0);
+    }
+    friend __host__ __device__ constexpr Dual operator/(const Dual& a, const Dual& b) {
+        return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v), 0);
+    }
+    friend __host__ __device__ constexpr Dual operator-(const Dual& a) { return Dual(-a.v, -a.d, 0); }
+    __host__ __device__ constexpr Dual& operator+=(const Dual& b) { return *this = *this + b; }
+    __host__ __device__ constexpr Dual& operator-=(const Dual& b) { return *this = *this - b; }
+    __host__ __device__ constexpr Dual& operator*=(const Dual& b) { return *this = *this * b; }
+    __host__ __device__ constexpr Dual& operator/=(const Dual& b) { return *this = *this / b; }
+};
+
 // slot of moment mno in the cube after the forward passes
 __host__ __device__ __forceinline__ constexpr int MIDX(int m, int n, int o) { return o * 9 + n * 3 + m; }
 
@@ -248,8 +275,11 @@ struct DevParams {
 // central moments about the new mean mu* = mu + F/rho are those of a
 // distribution whose cumulants stop at order two (Isserlis' products).
 // Returns u = mu + F/(2 rho) (velocity that shifts h) and rho.
+// collide_f with the body force as an argument (the coupled adjoint passes a
+// dual-number F to differentiate with respect to it)
 template <typename R>
-__device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& uy, R& uz, R& rho_out) {
+__device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const R Fx, const R Fy, const R Fz, R& ux,
+                                                R& uy, R& uz, R& rho_out) {
     R drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
@@ -286,7 +316,6 @@ __device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& u
     const R syy = sxx - dxy;
     const R szz = sxx - dxz;
     // shifts: mean after collision, velocity for h
-    const R Fx = (R)p.F[0], Fy = (R)p.F[1], Fz = (R)p.F[2];
     const R vx = mux + Fx * irho, vy = muy + Fy * irho, vz = muz + Fz * irho;
     ux = mux + R(0.5) * Fx * irho;
     uy = muy + R(0.5) * Fy * irho;
@@ -333,6 +362,11 @@ __device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& u
     inverse_cube<R>(cb, vx, vy, vz);
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = cb[CUBE(a)];
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& uy, R& uz, R& rho_out) {
+    collide_f_force<R>(fd, p, (R)p.F[0], (R)p.F[1], (R)p.F[2], ux, uy, uz, rho_out);
 }
 
 // ---- h: central-moment collision (Eq. H_cm_collision + App. D source) ----

@@ -34,6 +34,8 @@ struct Buffers {
     const int32_t* rlink;     // link index (into lq / lwall) of each entry
     double* dlink;            // per link accumulator of dJ/dT_w terms
     void* urec;               // recorded velocities of a step (3N, R) or nullptr
+    void* frec;               // recorded pre-collision f arrivals (27N, R; coupled adjoint) or nullptr
+    void* hrec;               // recorded pre-collision h arrivals (Q_h N, R) or nullptr
 };
 
 // objective of the adjoint: a linear flux of the post-collision h state
@@ -78,6 +80,15 @@ cudaError_t launch_inlet(const Buffers& b, const DevParams& p, cudaStream_t s, b
 // symmetry rows: fill them in the post-collision arrays before a step
 template <typename S, int QH>
 cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s);
+// out[0..5] = sum over the n nodes of acc[n * 6 + k] (the coupled adjoint's
+// per-node dJ/dF, dJ/du_in accumulators)
+cudaError_t launch_reduce6(const double* acc, int n, double* out, cudaStream_t s);
+// adjoint of one level of the coupled f + h evolution (records of the level's
+// pre-collision arrivals; f_level NULL at the initial level)
+template <typename R, int QH>
+cudaError_t launch_adjoint_flow(const Buffers& b, const DevParams& p, const R* f_level, const R* h_level,
+                                const R* muf_next, const R* muh_next, R* muf_out, R* muh_out, AdjObjective obj,
+                                double* dtheta, double* acc6, const R* din, cudaStream_t s);
 // rec[i * N + n] = post-collision h deviation of population i at node n (type R)
 template <typename S, int QH>
 cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s);
@@ -222,7 +233,7 @@ template <typename S, int QH> constexpr int step_min_blocks() {
 
 // EQ: the BB + EQ wall rule (compile time, so the default rules keep their
 // register allocation); CUM: the Cumulants-1st h kind
-template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false>
+template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false, bool PRE = false>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const S* __restrict__ fA, S* __restrict__ fB,
                                                   const S* __restrict__ hA, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags,
@@ -234,7 +245,9 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
                                                   const float* __restrict__ lq,
                                                   const int32_t* __restrict__ lwall,
                                                   const float* __restrict__ Twall,
-                                                  typename Acc<S>::R* __restrict__ urec, const DevParams p) {
+                                                  typename Acc<S>::R* __restrict__ urec,
+                                                  void* __restrict__ frec, void* __restrict__ hrec,
+                                                  const DevParams p) {
     using R = typename Acc<S>::R;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in_range = n < p.N;
@@ -292,6 +305,10 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
         }
     }
     R ux, uy, uz;
+    if constexpr (PRE) {  // pre-collision arrivals for the coupled adjoint
+#pragma unroll
+        for (int a = 0; a < 27; ++a) ((R*)frec)[a * N + n] = fd[a];
+    }
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
     if (REC) {
         urec[n] = ux;
@@ -329,6 +346,10 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
         }
     }
     const R Q = theta ? (R)__ldg(theta + n) : R(0);
+    if constexpr (PRE) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) ((R*)hrec)[i * N + n] = hd[i];
+    }
     collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
     }
 }
@@ -580,8 +601,22 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
     R* urec = (R*)b.urec;
 #define LBM_STEP_ARGS                                                                                            \
     (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, b.seg_base, \
-        b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, p
+        b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, b.frec, b.hrec, p
     const bool cum = p.hkind == 3, eq = p.wall_bc == 1;
+    if (b.frec) {  // pre-collision records for the coupled adjoint (R-typed storage only)
+        if constexpr (sizeof(S) == sizeof(R)) {
+            const int v = (cum ? 2 : 0) | (eq ? 1 : 0);
+            switch (v) {
+                case 0: k_step<S, QH, true, false, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+                case 1: k_step<S, QH, true, false, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+                case 2: k_step<S, QH, true, false, true, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+                default: k_step<S, QH, true, false, true, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (advance_h) {
         const int v = (urec ? 4 : 0) | (cum ? 2 : 0) | (eq ? 1 : 0);
         switch (v) {
@@ -1312,6 +1347,279 @@ template <typename S, int QH>
 cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s) {
     const int total = 2 * p.nx * p.nz;
     k_mirror<S, QH><<<(total + kBlock - 1) / kBlock, kBlock, 0, s>>>((S*)b.fA, (S*)b.hA, p);
+    return cudaGetLastError();
+}
+
+// ---- adjoint of the coupled f + h evolution -------------------------------
+// The h step depends on the flow through u = U(g_f; F), so gradients with
+// respect to flow parameters (the body force F, the inlet velocity u_in) need
+// the adjoint of f as well.  Per node and level, from the recorded
+// pre-collision arrivals g_f, g_h (Eq. hydro_cu_collision, Eq. H_cm_collision
+// or H_cu_collision):
+//   lambda = P^T mu^{k+1} + dJ/ds^k            (f: Eq. IBB; h: Eq. IABB)
+//   w      = (dC_h/du)^T lambda_h
+//   mu_h   = (dC_h/dg_h)^T lambda_h,   dJ/dQ += (dC_h/dQ)^T lambda_h
+//   mu_f   = (dC_f/dg_f)^T lambda_f + (dU/dg_f)^T w
+//   dJ/dF += (dC_f/dF)^T lambda_f + (dU/dF)^T w
+// and at inlet nodes (equilibria at u_in) dJ/du_in += (ds_in/du_in)^T lambda.
+// The collision derivatives are forward-mode passes of the collision
+// functions in dual numbers.  The f collision reads g_f only through its
+// mass, momentum and second moments (m = P g_f, ten numbers), so
+// (dC_f/dg_f)^T lambda_f = P^T G with G_k = lambda_f . (dC_f/dg_f) d_k for ten
+// perturbations d_k with P d_k = unit_k.
+
+// Eq. IBB: derivative of the arrival f_abar(x_b) with respect to f*_a(x_b)
+// and f*_abar(x_b) (the x_f term goes through the reverse-link table)
+template <typename R>
+__device__ __forceinline__ void ibb_partials(float q, bool thin, R& d_ab, R& d_abb) {
+    if (q <= 0.5f && !thin) {
+        d_ab = R(2) * (R)q;
+        d_abb = R(0);
+    } else {
+        const R qq = (R)fmaxf(q, 0.5f);
+        d_ab = R(1) / (R(2) * qq);
+        d_abb = (R(2) * qq - R(1)) / (R(2) * qq);
+    }
+}
+
+// perturbation d_k of direction a whose moments (rho, j, second moments) are unit_k
+__device__ __forceinline__ float moment_dir(int k, int a) {
+    const int ex = EX(a), ey = EY(a), ez = EZ(a);
+    switch (k) {
+        case 0: return (ex == 0 && ey == 0 && ez == 0) ? 1.0f : 0.0f;
+        case 1: return (ey == 0 && ez == 0) ? 0.5f * ex : 0.0f;
+        case 2: return (ex == 0 && ez == 0) ? 0.5f * ey : 0.0f;
+        case 3: return (ex == 0 && ey == 0) ? 0.5f * ez : 0.0f;
+        case 4: return (ey == 0 && ez == 0) ? (ex == 0 ? -1.0f : 0.5f) : 0.0f;
+        case 5: return (ex == 0 && ez == 0) ? (ey == 0 ? -1.0f : 0.5f) : 0.0f;
+        case 6: return (ex == 0 && ey == 0) ? (ez == 0 ? -1.0f : 0.5f) : 0.0f;
+        case 7: return ez == 0 ? 0.25f * ex * ey : 0.0f;
+        case 8: return ey == 0 ? 0.25f * ex * ez : 0.0f;
+        default: return ex == 0 ? 0.25f * ey * ez : 0.0f;
+    }
+}
+
+template <typename R, int QH, bool CUM>
+__global__ void __launch_bounds__(kBlock) k_adjoint_flow(
+    const R* __restrict__ muf_next, const R* __restrict__ muh_next, R* __restrict__ muf_out, R* __restrict__ muh_out,
+    const R* __restrict__ gf, const R* __restrict__ gh, const float* __restrict__ theta,
+    double* __restrict__ dtheta, double* __restrict__ acc6, const R* __restrict__ din,
+    const uint8_t* __restrict__ flags, const int32_t* __restrict__ seg_base, const uint32_t* __restrict__ wmask,
+    const int32_t* __restrict__ woff, const float* __restrict__ lq, const int32_t* __restrict__ lwall,
+    const int32_t* __restrict__ rseg_base, const uint32_t* __restrict__ rmask, const int32_t* __restrict__ roff,
+    const int32_t* __restrict__ rlink, double* __restrict__ dlink, const AdjObjective obj, const DevParams p) {
+    using D = Dual<R>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = n < p.N;
+    const uint8_t fl = in_range ? flags[n] : (uint8_t)T_SOLID;
+    const bool is_wall = (fl & F_WALL) != 0, is_rw = (fl & F_RWALL) != 0;
+    const uint32_t bal_w = __ballot_sync(0xffffffffu, is_wall);
+    const uint32_t bal_r = __ballot_sync(0xffffffffu, is_rw);
+    if (!in_range) return;
+    const int N = p.N;
+    const int type = fl & 3;
+    if (type == T_SOLID) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int x, y, z;
+    node_xyz(n, p, x, y, z);
+    int xt[3] = {x - 1, x, x + 1};
+    if (p.periodic_x) {
+        if (xt[0] < 0) xt[0] += p.nx;
+        if (xt[2] >= p.nx) xt[2] -= p.nx;
+    } else {
+        if (xt[0] < 0) xt[0] = -1;
+        if (xt[2] >= p.nx) xt[2] = -1;
+    }
+    const int yt[3] = {((y == 0) ? p.ny - 1 : y - 1) * p.nx, y * p.nx, ((y == p.ny - 1) ? 0 : y + 1) * p.nx};
+    const int pl = p.nx * p.ny;
+    const int zt[3] = {((z == 0) ? p.nz - 1 : z - 1) * pl, z * pl, ((z == p.nz - 1) ? 0 : z + 1) * pl};
+    const R wsurf = (obj.kind == 0) ? (R)obj.weight : R(0);
+    // lambda = P^T mu^{k+1} (+ the objective's terms for h)
+    R lf[27], lh[QH];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const int xx = xt[EX(a) + 1];
+        lf[a] = (xx < 0) ? R(0) : muf_next[a * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+    }
+#pragma unroll
+    for (int i = 0; i < QH; ++i) {
+        const int a = HDIR<QH>(i);
+        const int xx = xt[EX(a) + 1];
+        lh[i] = (xx < 0) ? R(0) : muh_next[i * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+    }
+    if (!p.periodic_x && x == p.nx - 1) {
+#pragma unroll
+        for (int a = 0; a < 27; ++a) {
+            if (EX(a) != -1) continue;
+            lf[a] += muf_next[a * N + x + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+        }
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            if (EX(a) != -1) continue;
+            lh[i] += muh_next[i * N + x + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+        }
+    }
+    if (is_rw) {
+        // this node is x_f of links (t = y + e_a, a) with q <= 1/2
+        const int idx = __ldg(rseg_base + (n >> 5)) + __popc(bal_r & lt);
+        const uint32_t rm = __ldg(rmask + idx);
+        const int ro = __ldg(roff + idx);
+#pragma unroll
+        for (int a = 0; a < 27; ++a) {
+            if (!(rm & (1u << a))) continue;
+            const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
+            const float q = __ldg(lq + l);
+            const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
+            lf[a] += (R(1) - R(2) * (R)q) * muf_next[OPP(a) * N + t];
+        }
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            if (!(rm & (1u << a))) continue;
+            const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
+            const float q = __ldg(lq + l);
+            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+            const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
+            lh[i] -= (R(1) - R(2) * (R)q) * (muh_next[HOPP<QH>(i) * N + t] + cw);
+        }
+    }
+    if (is_wall) {
+        const int idx = __ldg(seg_base + (n >> 5)) + __popc(bal_w & lt);
+        const uint32_t mask = __ldg(wmask + idx);
+        const int off = __ldg(woff + idx);
+#pragma unroll
+        for (int b = 0; b < 27; ++b) {
+            if (!(mask & (1u << b))) continue;
+            const int ib = OPP(b);
+            const float q = __ldg(lq + off + __popc(mask & ((1u << b) - 1u)));
+            const bool thin = (mask >> ib) & 1u;
+            R d_ab, d_abb;
+            ibb_partials<R>(q, thin, d_ab, d_abb);
+            const R m = muf_next[ib * N + n];
+            lf[b] += d_ab * m;
+            lf[ib] += d_abb * m;
+        }
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int b = HDIR<QH>(i);
+            if (!(mask & (1u << b))) continue;
+            const int ib = HOPP<QH>(i);
+            const int l = off + __popc(mask & ((1u << b) - 1u));
+            const float q = __ldg(lq + l);
+            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+            const bool thin = (mask >> HDIR<QH>(ib)) & 1u;
+            R d_ab, d_abb, d_T;
+            iabb_partials<R>(q, thin, p.wall_bc, d_ab, d_abb, d_T);
+            const R m = muh_next[ib * N + n] + cw;
+            lh[i] += d_ab * m - cw;
+            lh[ib] += d_abb * m;
+            dlink[l] += (double)d_T * HW<QH>(i) * (double)m;
+        }
+    }
+    if (obj.kind == 1 && x == obj.plane) {
+#pragma unroll
+        for (int i = 0; i < QH; ++i) lh[i] += (R)obj.weight * (R)EX(HDIR<QH>(i));
+    }
+    if (!gf) {  // the initial level: its state is given; write lambda
+#pragma unroll
+        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = lf[a];
+#pragma unroll
+        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = lh[i];
+        return;
+    }
+    if (type == T_INLET) {
+        // the inlet holds the equilibria at u_in: din[d * (27 + QH) + .] = d s_in / d u_in,d
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            double acc = 0.0;
+#pragma unroll
+            for (int a = 0; a < 27; ++a) acc += (double)(din[d * (27 + QH) + a] * lf[a]);
+#pragma unroll
+            for (int i = 0; i < QH; ++i) acc += (double)(din[d * (27 + QH) + 27 + i] * lh[i]);
+            acc6[(size_t)n * 6 + 3 + d] += acc;
+        }
+#pragma unroll
+        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+        return;
+    }
+    R g[27], hpre[QH];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) g[a] = gf[a * N + n];
+#pragma unroll
+    for (int i = 0; i < QH; ++i) hpre[i] = gh[i * N + n];
+    const R Q = theta ? (R)__ldg(theta + n) : R(0);
+    R ux, uy, uz, rho;
+    {
+        R fv[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) fv[a] = g[a];
+        collide_f<R>(fv, p, ux, uy, uz, rho);
+    }
+    // w = (dC_h/du)^T lambda_h (passes 0..2); mu_h (passes 3..2+QH); dJ/dQ (pass 3+QH)
+    R w[3];
+    double dth = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < QH + 4; ++k) {
+        D hd[QH];
+#pragma unroll
+        for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i], (k >= 3 && k - 3 == i) ? R(1) : R(0), 0);
+        const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0), vz(uz, k == 2 ? R(1) : R(0), 0);
+        const D Qd(Q, k == QH + 3 ? R(1) : R(0), 0);
+        collide_h<D, QH, CUM>(hd, vx, vy, vz, Qd, p);
+        R acc = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
+        if (k < 3) w[k] = acc;
+        else if (k < QH + 3) muh_out[(k - 3) * N + n] = acc;
+        else dth = (double)acc;
+    }
+    // G_k for the ten moment perturbations (passes 0..9) and the force (10..12)
+    R G[10];
+#pragma unroll 1
+    for (int k = 0; k < 13; ++k) {
+        D fd[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) fd[a] = D(g[a], k < 10 ? (R)moment_dir(k, a) : R(0), 0);
+        const D Fx((R)p.F[0], k == 10 ? R(1) : R(0), 0), Fy((R)p.F[1], k == 11 ? R(1) : R(0), 0),
+            Fz((R)p.F[2], k == 12 ? R(1) : R(0), 0);
+        D vx, vy, vz, vr;
+        collide_f_force<D>(fd, p, Fx, Fy, Fz, vx, vy, vz, vr);
+        R acc = w[0] * vx.d + w[1] * vy.d + w[2] * vz.d;
+#pragma unroll
+        for (int a = 0; a < 27; ++a) acc += lf[a] * fd[a].d;
+        if (k < 10) G[k] = acc;
+        else acc6[(size_t)n * 6 + (k - 10)] += (double)acc;
+    }
+#pragma unroll
+    for (int b = 0; b < 27; ++b) {
+        const R ex = (R)EX(b), ey = (R)EY(b), ez = (R)EZ(b);
+        muf_out[b * N + n] = G[0] + ex * G[1] + ey * G[2] + ez * G[3] + ex * ex * G[4] + ey * ey * G[5] +
+                             ez * ez * G[6] + ex * ey * G[7] + ex * ez * G[8] + ey * ez * G[9];
+    }
+    if (dtheta) dtheta[n] += dth;
+}
+
+template <typename R, int QH>
+cudaError_t launch_adjoint_flow(const Buffers& b, const DevParams& p, const R* f_level, const R* h_level,
+                                const R* muf_next, const R* muh_next, R* muf_out, R* muh_out, AdjObjective obj,
+                                double* dtheta, double* acc6, const R* din, cudaStream_t s) {
+    const int grid = (p.N + kBlock - 1) / kBlock;
+#define LBM_ADJF_ARGS                                                                                            \
+    muf_next, muh_next, muf_out, muh_out, f_level, h_level, b.theta, dtheta, acc6, din, b.flags, b.seg_base,    \
+        b.wmask, b.woff, b.lq, b.lwall, b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p
+    if (p.hkind == 3) k_adjoint_flow<R, QH, true><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+    else k_adjoint_flow<R, QH, false><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+#undef LBM_ADJF_ARGS
     return cudaGetLastError();
 }
 

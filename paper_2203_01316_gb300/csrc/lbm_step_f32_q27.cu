@@ -20,6 +20,9 @@ template cudaError_t launch_surface_flux<float, 27>(const Buffers&, const DevPar
 template cudaError_t launch_step_staged<float, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&, const float*, const float*,
                                            const float*, float*, AdjObjective, double*, cudaStream_t);
+template cudaError_t launch_adjoint_flow<float, 27>(const Buffers&, const DevParams&, const float*, const float*,
+                                                const float*, const float*, float*, float*, AdjObjective, double*,
+                                                double*, const float*, cudaStream_t);
 
 // streaming map of the step kernels (storage independent)
 __global__ void k_stream_map(const uint8_t* __restrict__ flags, const int32_t* __restrict__ wnode,
@@ -54,6 +57,11 @@ cudaError_t launch_stream_map(const Buffers& b, const DevParams& p, int qh, int3
     (void)qh;
     const int grid = (p.N + kBlock - 1) / kBlock;
     k_stream_map<<<grid, kBlock, 0, s>>>(b.flags, b.wnode, b.wmask, b.nw, src, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce6(const double* acc, int n, double* out, cudaStream_t s) {
+    k_reduce_partials<6><<<1, 1024, 0, s>>>(acc, n, out);
     return cudaGetLastError();
 }
 }  // namespace lbmd

@@ -26,7 +26,8 @@ SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_s
            "lbm_surface_flux", "lbm_nusselt", "lbm_state_size", "lbm_save_state", "lbm_load_state",
            "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
            "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
-           "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h"]
+           "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h", "lbm_step_record_pre",
+           "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient"]
 OBJ_SURFACE, OBJ_SECTION = 0, 1
 
 
@@ -91,6 +92,9 @@ def lib():
         "lbm_step_record": [vp, i32, vp, i32],
         "lbm_adjoint_step": [vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_step_record_h": [vp, i32, vp, vp],
+        "lbm_step_record_pre": [vp, i32, vp, vp],
+        "lbm_adjoint_flow_step": [vp, vp, vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
+        "lbm_adjoint_flow_gradient": [vp, C.POINTER(dbl), C.POINTER(dbl), i32],
         "lbm_adjoint_step_h": [vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_adjoint_wall_gradient": [vp, C.POINTER(dbl), i32],
         "lbm_stream_map": [vp, vp, i32],
@@ -206,6 +210,7 @@ class Solver:
 
     def set_inlet(self, u, T):
         self._check(self.L.lbm_set_inlet(self._h, float(u[0]), float(u[1]), float(u[2]), float(T)))
+        self.inlet = (tuple(float(v) for v in u), float(T))
 
     def set_force(self, F):
         self._check(self.L.lbm_set_force(self._h, float(F[0]), float(F[1]), float(F[2])))
@@ -324,6 +329,28 @@ class Solver:
                                                   h_level.data_ptr() if h_level is not None else None, *args[1:]))
         else:
             self._check(self.L.lbm_adjoint_step(self._h, *args))
+
+    def step_record_pre(self, n, f_rec, h_rec):
+        """n steps recording each level's pre-collision arrivals into f_rec
+        ([n, 27, N]) and h_rec ([n, Q_h, N]) device tensors (FP32/FP64)."""
+        self._check(self.L.lbm_step_record_pre(self._h, int(n), f_rec.data_ptr() if n > 0 else None,
+                                               h_rec.data_ptr() if n > 0 else None))
+
+    def adjoint_flow_step(self, f_level, h_level, muf_next, muh_next, muf_out, muh_out, obj=None, dtheta=None):
+        """One level of the coupled f + h adjoint (f_level, h_level None at
+        the initial level)."""
+        self._check(self.L.lbm_adjoint_flow_step(
+            self._h, f_level.data_ptr() if f_level is not None else None,
+            h_level.data_ptr() if h_level is not None else None, muf_next.data_ptr(), muh_next.data_ptr(),
+            muf_out.data_ptr(), muh_out.data_ptr(), C.byref(obj) if obj is not None else None,
+            dtheta.data_ptr() if dtheta is not None else None))
+
+    def adjoint_flow_gradient(self, reset=True):
+        """(dJ/dF[3], dJ/du_in[3]) accumulated by adjoint_flow_step."""
+        dF = (C.c_double * 3)()
+        du = (C.c_double * 3)()
+        self._check(self.L.lbm_adjoint_flow_gradient(self._h, dF, du, 1 if reset else 0))
+        return np.array(dF[:]), np.array(du[:])
 
     def adjoint_wall_gradient(self, n_walls, reset=True):
         g = (C.c_double * n_walls)()
