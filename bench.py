@@ -322,6 +322,56 @@ def measure_adjoint(w, stream, fwd_ms, steps=200, every=50):
             "dJ_dTwall": float(Tw.grad[0]), "grad_theta_norm": float(theta.grad.norm())}
 
 
+def measure_flow_adjoint(w, stream, fwd_ms, steps=100, every=25):
+    """Cost of the coupled f + h adjoint (gradients also with respect to the
+    body force and the inlet velocity) on the same objective as
+    measure_adjoint: backward time per step against the forward step."""
+    import torch
+    from paper_2203_01316_gb300.autograd import flow_objective
+    s = make_solver(w, "f32", stream=stream.cuda_stream)
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    N = w["flags"].size
+    state0 = s.save_state(torch.empty(s.state_size(), dtype=torch.uint8, device="cuda"))
+    theta = torch.zeros(N, dtype=torch.float64, device="cuda", requires_grad=True)
+    Tw = torch.tensor([WORKLOAD["T_wall"]], dtype=torch.float64, requires_grad=True)
+    F = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+    uin = torch.tensor(w["u_in"], dtype=torch.float64, requires_grad=True)
+    obj = s.objective("surface", 0, 1.0)
+    window = (steps - steps // 5, steps)
+    Jw = flow_objective(theta, Tw, F, uin, s, state0, 10, (8, 10), obj, every=5)  # warm-up
+    Jw.backward()
+    for t in (theta, Tw, F, uin):
+        t.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = flow_objective(theta, Tw, F, uin, s, state0, steps, window, obj, every=every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    bwd = (t2 - t1) / steps * 1e3
+    return {"steps": steps, "checkpoint_every": every, "objective": "sphere surface heat flux, last 20% of steps",
+            "backward_ms_per_step": bwd, "forward_ms_per_step": fwd_ms, "ratio": bwd / fwd_ms,
+            "dJ_du_in": uin.grad.tolist(), "dJ_dF": F.grad.tolist(),
+            "dJ_dTwall": float(Tw.grad[0])}
+
+
+def flow_adjoint_study(args):
+    import torch
+    from paper_2203_01316_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream()
+    w = make_workload(args.scale)
+    s = make_solver(w, "f32", stream=stream.cuda_stream)
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    dt = time_steps(s, 200, 20, stream)
+    s.close()
+    r = measure_flow_adjoint(w, stream, dt / 200 * 1e3, steps=args.adjoint_steps)
+    print(json.dumps({"flow_adjoint": r, "workload": _config(w, "f32")["workload"]}), flush=True)
+
+
 def precision_study(args):
     """Precision form of the heated sphere (Pr = 1000): populations stored
     in FP16 / BF16 (stochastic and nearest rounding) / FP32 with FP32
@@ -752,6 +802,8 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--flow-adjoint", action="store_true",
+                    help="time the coupled f + h adjoint (gradients for F and u_in) on the workload")
     ap.add_argument("--storages", default="", help="validation hill: comma-separated storages (f64, f32)")
     ap.add_argument("--kinds", default="", help="validation confined: comma-separated h kinds")
     ap.add_argument("--prs", default="", help="validation confined: comma-separated Prandtl numbers")
@@ -773,7 +825,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.validation == "cylinders":
+    if args.flow_adjoint:
+        flow_adjoint_study(args)
+    elif args.validation == "cylinders":
         validation_cylinders(args)
     elif args.validation == "hill":
         validation_hill(args)

@@ -947,6 +947,163 @@ __device__ __forceinline__ void iabb_partials(float q, bool thin, int wall_bc, R
     }
 }
 
+// The transposed Jacobian of one node's h collision at velocity u (fixed):
+// mu = (dC_h/dg)^T lambda and dth = (dC_h/dQ)^T lambda.  Central-moment kinds:
+// C_h = L(u) g + e(u) Q (Eq. H_cm_collision, App. D source), transposed
+// exactly; Cumulants-1st: the Jacobian of (H + Q) M(v) at the state whose
+// post-collision deviations are hpost (Eq. H_cu_collision).
+template <typename R, int QH, bool CUM>
+__device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpost, const R ux, const R uy,
+                                                      const R uz, const R Q, const DevParams& p, R* mu,
+                                                      double& dth) {
+    dth = 0.0;
+    if constexpr (CUM) {
+        // Cumulants-1st (Eq. H_cu_collision): s^k = (H + Q) M(v), M the unit
+        // equilibrium at v = (1 - s) m + s u, m = sum e g / H, H = sum g of the
+        // arrivals g.  From the recorded s^k: A = H + Q = sum s^k and
+        // v = sum e s^k / A, and (1 - s) m = v - s u.  The transposed Jacobian
+        //   mu_b = L0 + A/H sum_d ((1 - s) e_bd - (v_d - s u_d)) G_d,
+        //   L0 = sum_a lambda_a M_a(v),  G_d = sum_a lambda_a dM_a/dv_d,
+        // and dJ/dQ += L0.
+        R A = (R)p.Tref, jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            const R g = hpost[i];
+            A += g;
+            if (EX(a) != 0) jx += EX(a) * g;
+            if (EY(a) != 0) jy += EY(a) * g;
+            if (EZ(a) != 0) jz += EZ(a) * g;
+        }
+        const R iA = R(1) / A;
+        const R v[3] = {jx * iA, jy * iA, jz * iA};
+        const R u[3] = {ux, uy, uz};
+        const R c = cs2<R>();
+        // per axis: unit-equilibrium factors and their v-derivatives at c = -1, 0, +1
+        R W[3][3], D[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R a2 = c + v[d] * v[d];
+            W[d][0] = R(0.5) * (a2 - v[d]);
+            W[d][1] = R(1) - a2;
+            W[d][2] = R(0.5) * (a2 + v[d]);
+            D[d][0] = v[d] - R(0.5);
+            D[d][1] = R(-2) * v[d];
+            D[d][2] = v[d] + R(0.5);
+        }
+        R L0 = R(0), G[3] = {R(0), R(0), R(0)};
+        if constexpr (QH == 27) {
+#pragma unroll
+            for (int a = 0; a < 27; ++a) {
+                const int cx = EX(a) + 1, cy = EY(a) + 1, cz = EZ(a) + 1;
+                const R l = lam[a];
+                L0 += l * W[0][cx] * W[1][cy] * W[2][cz];
+                G[0] += l * D[0][cx] * W[1][cy] * W[2][cz];
+                G[1] += l * W[0][cx] * D[1][cy] * W[2][cz];
+                G[2] += l * W[0][cx] * W[1][cy] * D[2][cz];
+            }
+        } else {
+            // D3Q7 unit equilibrium: rest 1 - sum_d a2_d, arms (a2_d +- v_d) / 2
+            R rest = R(1);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) rest -= c + v[d] * v[d];
+            L0 = lam[0] * rest;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                L0 += lam[1 + d] * W[d][2] + lam[4 + d] * W[d][0];
+                G[d] = lam[0] * D[d][1] + lam[1 + d] * D[d][2] + lam[4 + d] * D[d][0];
+            }
+        }
+        const R s = (R)p.sh[1];
+        const R kap = A / (A - Q);
+        R base = L0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) base -= kap * (v[d] - s * u[d]) * G[d];
+        const R c1 = kap * (R(1) - s);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) {
+            const int a = HDIR<QH>(i);
+            mu[i] = base + c1 * (EX(a) * G[0] + EY(a) * G[1] + EZ(a) * G[2]);
+        }
+        dth = (double)L0;
+    } else if constexpr (QH == 27) {
+        R cb[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) cb[CUBE(a)] = lam[a];
+        // z = T^-T lambda
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+        for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+            for (int xx = 0; xx < 3; ++xx) inv3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+        R rank = R(0);
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int nn = 0; nn < 3; ++nn)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const R E = Eq<R>(m, nn, o);
+                    const R sr = (R)p.sh[m + nn + o];
+                    R& v = cb[MIDX(m, nn, o)];
+                    if (E != R(0)) {
+                        dth += (double)(E * v);
+                        rank += E * sr * v;
+                    }
+                    v *= (R(1) - sr);
+                }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+        for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+            for (int xx = 0; xx < 3; ++xx) fwd3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+#pragma unroll
+        for (int a = 0; a < 27; ++a) mu[a] = cb[CUBE(a)] + rank;
+    } else {
+        // D3Q7: moments 000, 100/010/001, 200/020/002
+        const R u[3] = {ux, uy, uz};
+        const R c = cs2<R>();
+        // z = T^-T lambda (transpose of the D3Q7 inverse transform of collide_h7)
+        R z0 = lam[0], z1[3], z2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R mb2 = R(0.5) * (lam[1 + d] + lam[4 + d]) - lam[0];
+            const R mb1 = R(0.5) * (lam[1 + d] - lam[4 + d]);
+            z2[d] = mb2;
+            z1[d] = mb1 + R(2) * u[d] * mb2;
+            z0 += u[d] * mb1 + u[d] * u[d] * mb2;
+        }
+        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+        dth = (double)z0 + (double)(c * (z2[0] + z2[1] + z2[2]));
+        const R rank = s0 * z0 + s2 * c * (z2[0] + z2[1] + z2[2]);
+        z0 *= (R(1) - s0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            z1[d] *= (R(1) - s1);
+            z2[d] *= (R(1) - s2);
+        }
+        // T^T z: population i gets z0 + sum_d (e_id - u_d) z1_d + (e_id - u_d)^2 z2_d
+        R base = z0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) base += -u[d] * z1[d] + u[d] * u[d] * z2[d];
+        mu[0] = base + rank;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R rest_d = -u[d] * z1[d] + u[d] * u[d] * z2[d];
+            const R plus = (R(1) - u[d]) * z1[d] + (R(1) - u[d]) * (R(1) - u[d]) * z2[d];
+            const R minus = (R(-1) - u[d]) * z1[d] + (R(1) + u[d]) * (R(1) + u[d]) * z2[d];
+            mu[1 + d] = base - rest_d + plus + rank;
+            mu[4 + d] = base - rest_d + minus + rank;
+        }
+    }
+}
+
 template <typename R, int QH, bool CUM = false>
 __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_next, R* __restrict__ out,
                                                      const R* __restrict__ uk, const R* __restrict__ hk,
@@ -1059,151 +1216,16 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     }
     const R ux = uk[n], uy = uk[N + n], uz = uk[2 * N + n];
     double dth = 0.0;
-    if constexpr (CUM) {
-        // Cumulants-1st (Eq. H_cu_collision): s^k = (H + Q) M(v), M the unit
-        // equilibrium at v = (1 - s) m + s u, m = sum e g / H, H = sum g of the
-        // arrivals g.  From the recorded s^k: A = H + Q = sum s^k and
-        // v = sum e s^k / A, and (1 - s) m = v - s u.  The transposed Jacobian
-        //   mu_b = L0 + A/H sum_d ((1 - s) e_bd - (v_d - s u_d)) G_d,
-        //   L0 = sum_a lambda_a M_a(v),  G_d = sum_a lambda_a dM_a/dv_d,
-        // and dJ/dQ += L0.
-        R A = (R)p.Tref, jx = R(0), jy = R(0), jz = R(0);
+    {
+        R mu[QH], hp[QH];
+        if constexpr (CUM) {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) {
-            const int a = HDIR<QH>(i);
-            const R g = hk[i * N + n];
-            A += g;
-            if (EX(a) != 0) jx += EX(a) * g;
-            if (EY(a) != 0) jy += EY(a) * g;
-            if (EZ(a) != 0) jz += EZ(a) * g;
+            for (int i = 0; i < QH; ++i) hp[i] = hk[i * N + n];
         }
         const R Q = theta ? (R)__ldg(theta + n) : R(0);
-        const R iA = R(1) / A;
-        const R v[3] = {jx * iA, jy * iA, jz * iA};
-        const R u[3] = {ux, uy, uz};
-        const R c = cs2<R>();
-        // per axis: unit-equilibrium factors and their v-derivatives at c = -1, 0, +1
-        R W[3][3], D[3][3];
+        h_collision_transpose<R, QH, CUM>(lam, hp, ux, uy, uz, Q, p, mu, dth);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const R a2 = c + v[d] * v[d];
-            W[d][0] = R(0.5) * (a2 - v[d]);
-            W[d][1] = R(1) - a2;
-            W[d][2] = R(0.5) * (a2 + v[d]);
-            D[d][0] = v[d] - R(0.5);
-            D[d][1] = R(-2) * v[d];
-            D[d][2] = v[d] + R(0.5);
-        }
-        R L0 = R(0), G[3] = {R(0), R(0), R(0)};
-        if constexpr (QH == 27) {
-#pragma unroll
-            for (int a = 0; a < 27; ++a) {
-                const int cx = EX(a) + 1, cy = EY(a) + 1, cz = EZ(a) + 1;
-                const R l = lam[a];
-                L0 += l * W[0][cx] * W[1][cy] * W[2][cz];
-                G[0] += l * D[0][cx] * W[1][cy] * W[2][cz];
-                G[1] += l * W[0][cx] * D[1][cy] * W[2][cz];
-                G[2] += l * W[0][cx] * W[1][cy] * D[2][cz];
-            }
-        } else {
-            // D3Q7 unit equilibrium: rest 1 - sum_d a2_d, arms (a2_d +- v_d) / 2
-            R rest = R(1);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) rest -= c + v[d] * v[d];
-            L0 = lam[0] * rest;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                L0 += lam[1 + d] * W[d][2] + lam[4 + d] * W[d][0];
-                G[d] = lam[0] * D[d][1] + lam[1 + d] * D[d][2] + lam[4 + d] * D[d][0];
-            }
-        }
-        const R s = (R)p.sh[1];
-        const R kap = A / (A - Q);
-        R base = L0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) base -= kap * (v[d] - s * u[d]) * G[d];
-        const R c1 = kap * (R(1) - s);
-#pragma unroll
-        for (int i = 0; i < QH; ++i) {
-            const int a = HDIR<QH>(i);
-            out[i * N + n] = base + c1 * (EX(a) * G[0] + EY(a) * G[1] + EZ(a) * G[2]);
-        }
-        dth = (double)L0;
-    } else if constexpr (QH == 27) {
-        R cb[27];
-#pragma unroll
-        for (int a = 0; a < 27; ++a) cb[CUBE(a)] = lam[a];
-        // z = T^-T lambda
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
-#pragma unroll
-        for (int zz = 0; zz < 3; ++zz)
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) inv3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
-        R rank = R(0);
-#pragma unroll
-        for (int o = 0; o < 3; ++o)
-#pragma unroll
-            for (int nn = 0; nn < 3; ++nn)
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const R E = Eq<R>(m, nn, o);
-                    const R sr = (R)p.sh[m + nn + o];
-                    R& v = cb[MIDX(m, nn, o)];
-                    if (E != R(0)) {
-                        dth += (double)(E * v);
-                        rank += E * sr * v;
-                    }
-                    v *= (R(1) - sr);
-                }
-#pragma unroll
-        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
-#pragma unroll
-        for (int zz = 0; zz < 3; ++zz)
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) fwd3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
-#pragma unroll
-        for (int a = 0; a < 27; ++a) out[a * N + n] = cb[CUBE(a)] + rank;
-    } else {
-        // D3Q7: moments 000, 100/010/001, 200/020/002
-        const R u[3] = {ux, uy, uz};
-        const R c = cs2<R>();
-        // z = T^-T lambda (transpose of the D3Q7 inverse transform of collide_h7)
-        R z0 = lam[0], z1[3], z2[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const R mb2 = R(0.5) * (lam[1 + d] + lam[4 + d]) - lam[0];
-            const R mb1 = R(0.5) * (lam[1 + d] - lam[4 + d]);
-            z2[d] = mb2;
-            z1[d] = mb1 + R(2) * u[d] * mb2;
-            z0 += u[d] * mb1 + u[d] * u[d] * mb2;
-        }
-        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
-        dth = (double)z0 + (double)(c * (z2[0] + z2[1] + z2[2]));
-        const R rank = s0 * z0 + s2 * c * (z2[0] + z2[1] + z2[2]);
-        z0 *= (R(1) - s0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            z1[d] *= (R(1) - s1);
-            z2[d] *= (R(1) - s2);
-        }
-        // T^T z: population i gets z0 + sum_d (e_id - u_d) z1_d + (e_id - u_d)^2 z2_d
-        R base = z0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) base += -u[d] * z1[d] + u[d] * u[d] * z2[d];
-        out[n] = base + rank;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const R rest_d = -u[d] * z1[d] + u[d] * u[d] * z2[d];
-            const R plus = (R(1) - u[d]) * z1[d] + (R(1) - u[d]) * (R(1) - u[d]) * z2[d];
-            const R minus = (R(-1) - u[d]) * z1[d] + (R(1) + u[d]) * (R(1) + u[d]) * z2[d];
-            out[(1 + d) * N + n] = base - rest_d + plus + rank;
-            out[(4 + d) * N + n] = base - rest_d + minus + rank;
-        }
+        for (int i = 0; i < QH; ++i) out[i * N + n] = mu[i];
     }
     if (dtheta) dtheta[n] += dth;
 }
@@ -1362,8 +1384,9 @@ cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s) 
 //   mu_f   = (dC_f/dg_f)^T lambda_f + (dU/dg_f)^T w
 //   dJ/dF += (dC_f/dF)^T lambda_f + (dU/dF)^T w
 // and at inlet nodes (equilibria at u_in) dJ/du_in += (ds_in/du_in)^T lambda.
-// The collision derivatives are forward-mode passes of the collision
-// functions in dual numbers.  The f collision reads g_f only through its
+// mu_h and dJ/dQ use the h-only adjoint's exact transpose; the other collision
+// derivatives are forward-mode passes of the collision functions in dual
+// numbers.  The f collision reads g_f only through its
 // mass, momentum and second moments (m = P g_f, ten numbers), so
 // (dC_f/dg_f)^T lambda_f = P^T G with G_k = lambda_f . (dC_f/dg_f) d_k for ten
 // perturbations d_k with P d_k = unit_k.
@@ -1565,23 +1588,33 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
         for (int a = 0; a < 27; ++a) fv[a] = g[a];
         collide_f<R>(fv, p, ux, uy, uz, rho);
     }
-    // w = (dC_h/du)^T lambda_h (passes 0..2); mu_h (passes 3..2+QH); dJ/dQ (pass 3+QH)
+    // w = (dC_h/du)^T lambda_h: three forward-mode passes in u
     R w[3];
-    double dth = 0.0;
 #pragma unroll 1
-    for (int k = 0; k < QH + 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         D hd[QH];
 #pragma unroll
-        for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i], (k >= 3 && k - 3 == i) ? R(1) : R(0), 0);
+        for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i]);
         const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0), vz(uz, k == 2 ? R(1) : R(0), 0);
-        const D Qd(Q, k == QH + 3 ? R(1) : R(0), 0);
-        collide_h<D, QH, CUM>(hd, vx, vy, vz, Qd, p);
+        collide_h<D, QH, CUM>(hd, vx, vy, vz, D(Q), p);
         R acc = R(0);
 #pragma unroll
         for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
-        if (k < 3) w[k] = acc;
-        else if (k < QH + 3) muh_out[(k - 3) * N + n] = acc;
-        else dth = (double)acc;
+        w[k] = acc;
+    }
+    // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the h-only
+    // adjoint's code; Cumulants-1st needs the post-collision state)
+    double dth = 0.0;
+    {
+        R hp[QH], mu[QH];
+        if constexpr (CUM) {
+#pragma unroll
+            for (int i = 0; i < QH; ++i) hp[i] = hpre[i];
+            collide_h<R, QH, true>(hp, ux, uy, uz, Q, p);
+        }
+        h_collision_transpose<R, QH, CUM>(lh, hp, ux, uy, uz, Q, p, mu, dth);
+#pragma unroll
+        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = mu[i];
     }
     // G_k for the ten moment perturbations (passes 0..9) and the force (10..12)
     R G[10];
