@@ -1384,12 +1384,13 @@ cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s) 
 //   mu_f   = (dC_f/dg_f)^T lambda_f + (dU/dg_f)^T w
 //   dJ/dF += (dC_f/dF)^T lambda_f + (dU/dF)^T w
 // and at inlet nodes (equilibria at u_in) dJ/du_in += (ds_in/du_in)^T lambda.
-// mu_h and dJ/dQ use the h-only adjoint's exact transpose; the other collision
-// derivatives are forward-mode passes of the collision functions in dual
-// numbers.  The f collision reads g_f only through its
-// mass, momentum and second moments (m = P g_f, ten numbers), so
-// (dC_f/dg_f)^T lambda_f = P^T G with G_k = lambda_f . (dC_f/dg_f) d_k for ten
-// perturbations d_k with P d_k = unit_k.
+// mu_h and dJ/dQ use the h-only adjoint's exact transpose, the u derivative
+// of the h collision three forward-mode passes in dual numbers.  The f
+// collision reads g_f only through its mass, momentum and second moments
+// (m = P g_f, ten numbers), so (dC_f/dg_f)^T lambda_f = P^T G with
+// G_k = lambda_f . (dC_f/dg_f) d_k for perturbations d_k with P d_k = unit_k
+// (collide_f_adjoint: reverse mode through the synthesis, forward mode
+// through the front part).
 
 // Eq. IBB: derivative of the arrival f_abar(x_b) with respect to f*_a(x_b)
 // and f*_abar(x_b) (the x_f term goes through the reverse-link table)
@@ -1405,20 +1406,193 @@ __device__ __forceinline__ void ibb_partials(float q, bool thin, R& d_ab, R& d_a
     }
 }
 
-// perturbation d_k of direction a whose moments (rho, j, second moments) are unit_k
-__device__ __forceinline__ float moment_dir(int k, int a) {
-    const int ex = EX(a), ey = EY(a), ez = EZ(a);
-    switch (k) {
-        case 0: return (ex == 0 && ey == 0 && ez == 0) ? 1.0f : 0.0f;
-        case 1: return (ey == 0 && ez == 0) ? 0.5f * ex : 0.0f;
-        case 2: return (ex == 0 && ez == 0) ? 0.5f * ey : 0.0f;
-        case 3: return (ex == 0 && ey == 0) ? 0.5f * ez : 0.0f;
-        case 4: return (ey == 0 && ez == 0) ? (ex == 0 ? -1.0f : 0.5f) : 0.0f;
-        case 5: return (ex == 0 && ez == 0) ? (ey == 0 ? -1.0f : 0.5f) : 0.0f;
-        case 6: return (ex == 0 && ey == 0) ? (ez == 0 ? -1.0f : 0.5f) : 0.0f;
-        case 7: return ez == 0 ? 0.25f * ex * ey : 0.0f;
-        case 8: return ey == 0 ? 0.25f * ex * ez : 0.0f;
-        default: return ex == 0 ? 0.25f * ey * ez : 0.0f;
+// front part of the f collision (Eq. hydro_cu_collision, collide_f_force):
+// from the ten moments m = (drho, j, second moments) and F to the relaxed
+// second central moments s (diagonal) and k (off-diagonal), 1/rho, the mean
+// after collision v and the velocity u for h
+template <typename T> struct FFront {
+    T drho, irho, sxx, syy, szz, kxy, kxz, kyz, v[3], u[3];
+};
+template <typename T>
+__device__ __forceinline__ FFront<T> f_front(const T* m, const T Fx, const T Fy, const T Fz, const DevParams& p) {
+    FFront<T> o;
+    const T c = cs2<T>();
+    const T drho = m[0], jx = m[1], jy = m[2], jz = m[3];
+    const T rho = (T)p.rho0 + drho;
+    const T irho = T(1) / rho;
+    const T mux = jx * irho, muy = jy * irho, muz = jz * irho;
+    const T axx = m[4] - drho * c - jx * mux;
+    const T ayy = m[5] - drho * c - jy * muy;
+    const T azz = m[6] - drho * c - jz * muz;
+    const T om1 = T(1) - (T)p.omega1;
+    const T omb = T(1) - (T)p.omega_bulk;
+    const T dxy = (axx - ayy) * om1, dxz = (axx - azz) * om1, tr = (axx + ayy + azz) * omb;
+    o.kxy = (m[7] - jx * muy) * om1;
+    o.kxz = (m[8] - jx * muz) * om1;
+    o.kyz = (m[9] - jy * muz) * om1;
+    o.sxx = (tr + dxy + dxz) * (T(1) / T(3));
+    o.syy = o.sxx - dxy;
+    o.szz = o.sxx - dxz;
+    o.drho = drho;
+    o.irho = irho;
+    o.v[0] = mux + Fx * irho;
+    o.v[1] = muy + Fy * irho;
+    o.v[2] = muz + Fz * irho;
+    o.u[0] = mux + T(0.5) * Fx * irho;
+    o.u[1] = muy + T(0.5) * Fy * irho;
+    o.u[2] = muz + T(0.5) * Fz * irho;
+    return o;
+}
+
+// Adjoint of the f collision of one node at its pre-collision arrivals g:
+// G[k] = lambda . (dC_f/dg) d_k + w . (dU/dg) d_k for the ten unit-moment
+// perturbations d_k (k < 10) and the same for the three components of F
+// (k = 10..12).  The synthesis (central moments -> populations through the
+// inverse transform at the mean v) is differentiated in reverse mode once:
+// z = T(v)^-T lambda, the adjoints of s, k, 1/rho, drho by hand, and of v
+// through both the equilibrium part of the moments and the transform, whose
+// derivative is d/dv_x T(v)^-1 kappa = T(v)^-1 (S_x kappa), (S_x kappa)_mno =
+// m kappa_(m-1)no (exact on the three-point lattice).  The front part (ten
+// moments and F -> s, k, 1/rho, v, u) runs in forward mode per direction.
+template <typename R>
+__device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p, const R* lam, const R* w, R* G) {
+    R m[10] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const R val = g[a];
+        m[0] += val;
+        if (EX(a) != 0) { m[1] += EX(a) * val; m[4] += val; }
+        if (EY(a) != 0) { m[2] += EY(a) * val; m[5] += val; }
+        if (EZ(a) != 0) { m[3] += EZ(a) * val; m[6] += val; }
+        if (EX(a) * EY(a) != 0) m[7] += (EX(a) * EY(a)) * val;
+        if (EX(a) * EZ(a) != 0) m[8] += (EX(a) * EZ(a)) * val;
+        if (EY(a) * EZ(a) != 0) m[9] += (EY(a) * EZ(a)) * val;
+    }
+    const FFront<R> S = f_front<R>(m, (R)p.F[0], (R)p.F[1], (R)p.F[2], p);
+    const R c = cs2<R>();
+    const R sxx = S.sxx, syy = S.syy, szz = S.szz, kxy = S.kxy, kxz = S.kxz, kyz = S.kyz, irho = S.irho;
+    const R vx = S.v[0], vy = S.v[1], vz = S.v[2];
+    const R rho0 = (R)p.rho0;
+    // post-collision central moments kappa (as in collide_f_force)
+    R K[27];
+    {
+        const R n220 = c * (sxx + syy) + (sxx * syy + R(2) * kxy * kxy) * irho;
+        const R n202 = c * (sxx + szz) + (sxx * szz + R(2) * kxz * kxz) * irho;
+        const R n022 = c * (syy + szz) + (syy * szz + R(2) * kyz * kyz) * irho;
+        const R n211 = c * kyz + (sxx * kyz + R(2) * kxy * kxz) * irho;
+        const R n121 = c * kxz + (syy * kxz + R(2) * kxy * kyz) * irho;
+        const R n112 = c * kxy + (szz * kxy + R(2) * kxz * kyz) * irho;
+        const R n222 = c * c * (sxx + syy + szz) +
+                       (c * (sxx * syy + sxx * szz + syy * szz) + R(2) * c * (kxy * kxy + kxz * kxz + kyz * kyz)) * irho +
+                       (sxx * syy * szz + R(2) * (sxx * kyz * kyz + syy * kxz * kxz + szz * kxy * kxy) +
+                        R(8) * kxy * kxz * kyz) * irho * irho;
+        const R tx = vx * vx, ty = vy * vy, tz = vz * vz;
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int n = 0; n < 3; ++n)
+#pragma unroll
+                for (int mm = 0; mm < 3; ++mm) {
+                    R neq = R(0);
+                    if (mm == 1 && n == 1 && o == 0) neq = kxy;
+                    if (mm == 1 && n == 0 && o == 1) neq = kxz;
+                    if (mm == 0 && n == 1 && o == 1) neq = kyz;
+                    if (mm == 2 && n == 0 && o == 0) neq = sxx;
+                    if (mm == 0 && n == 2 && o == 0) neq = syy;
+                    if (mm == 0 && n == 0 && o == 2) neq = szz;
+                    if (mm == 2 && n == 2 && o == 0) neq = n220;
+                    if (mm == 2 && n == 0 && o == 2) neq = n202;
+                    if (mm == 0 && n == 2 && o == 2) neq = n022;
+                    if (mm == 2 && n == 1 && o == 1) neq = n211;
+                    if (mm == 1 && n == 2 && o == 1) neq = n121;
+                    if (mm == 1 && n == 1 && o == 2) neq = n112;
+                    if (mm == 2 && n == 2 && o == 2) neq = n222;
+                    K[MIDX(mm, n, o)] = neq + S.drho * Eq<R>(mm, n, o) + rho0 * Dm<R>(mm, n, o, vx, vy, vz, tx, ty, tz);
+                }
+    }
+    // z = T(v)^-T lambda (the transposed passes in reverse order)
+    R Z[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) Z[CUBE(a)] = lam[a];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3T<R>(Z[3 * j], Z[3 * j + 1], Z[3 * j + 2], vx);
+#pragma unroll
+    for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx) inv3T<R>(Z[9 * zz + xx], Z[9 * zz + 3 + xx], Z[9 * zz + 6 + xx], vy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3T<R>(Z[j], Z[9 + j], Z[18 + j], vz);
+    // adjoints of the synthesis inputs
+    R bsxx = Z[MIDX(2, 0, 0)], bsyy = Z[MIDX(0, 2, 0)], bszz = Z[MIDX(0, 0, 2)];
+    R bkxy = Z[MIDX(1, 1, 0)], bkxz = Z[MIDX(1, 0, 1)], bkyz = Z[MIDX(0, 1, 1)];
+    R birho = R(0), bdrho = R(0);
+    {
+        R t = Z[MIDX(2, 2, 0)];
+        bsxx += t * (c + syy * irho); bsyy += t * (c + sxx * irho); bkxy += t * R(4) * kxy * irho;
+        birho += t * (sxx * syy + R(2) * kxy * kxy);
+        t = Z[MIDX(2, 0, 2)];
+        bsxx += t * (c + szz * irho); bszz += t * (c + sxx * irho); bkxz += t * R(4) * kxz * irho;
+        birho += t * (sxx * szz + R(2) * kxz * kxz);
+        t = Z[MIDX(0, 2, 2)];
+        bsyy += t * (c + szz * irho); bszz += t * (c + syy * irho); bkyz += t * R(4) * kyz * irho;
+        birho += t * (syy * szz + R(2) * kyz * kyz);
+        t = Z[MIDX(2, 1, 1)];
+        bkyz += t * (c + sxx * irho); bsxx += t * kyz * irho; bkxy += t * R(2) * kxz * irho;
+        bkxz += t * R(2) * kxy * irho; birho += t * (sxx * kyz + R(2) * kxy * kxz);
+        t = Z[MIDX(1, 2, 1)];
+        bkxz += t * (c + syy * irho); bsyy += t * kxz * irho; bkxy += t * R(2) * kyz * irho;
+        bkyz += t * R(2) * kxy * irho; birho += t * (syy * kxz + R(2) * kxy * kyz);
+        t = Z[MIDX(1, 1, 2)];
+        bkxy += t * (c + szz * irho); bszz += t * kxy * irho; bkxz += t * R(2) * kyz * irho;
+        bkyz += t * R(2) * kxz * irho; birho += t * (szz * kxy + R(2) * kxz * kyz);
+        t = Z[MIDX(2, 2, 2)];
+        const R P2 = sxx * syy + sxx * szz + syy * szz, Q2 = kxy * kxy + kxz * kxz + kyz * kyz;
+        const R P3 = sxx * syy * szz + R(2) * (sxx * kyz * kyz + syy * kxz * kxz + szz * kxy * kxy) +
+                     R(8) * kxy * kxz * kyz;
+        const R i2 = irho * irho;
+        bsxx += t * (c * c + c * (syy + szz) * irho + (syy * szz + R(2) * kyz * kyz) * i2);
+        bsyy += t * (c * c + c * (sxx + szz) * irho + (sxx * szz + R(2) * kxz * kxz) * i2);
+        bszz += t * (c * c + c * (sxx + syy) * irho + (sxx * syy + R(2) * kxy * kxy) * i2);
+        bkxy += t * (R(4) * c * kxy * irho + (R(4) * szz * kxy + R(8) * kxz * kyz) * i2);
+        bkxz += t * (R(4) * c * kxz * irho + (R(4) * syy * kxz + R(8) * kxy * kyz) * i2);
+        bkyz += t * (R(4) * c * kyz * irho + (R(4) * sxx * kyz + R(8) * kxy * kxz) * i2);
+        birho += t * ((c * P2 + R(2) * c * Q2) + R(2) * P3 * irho);
+    }
+    R bv[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm) {
+                const R zz = Z[MIDX(mm, n, o)];
+                bdrho += zz * Eq<R>(mm, n, o);
+                // the equilibrium part rho0 (E - K(v)) of the moments
+                const R kx = Kd<R>(mm, vx), ky = Kd<R>(n, vy), kz = Kd<R>(o, vz);
+                const R dkx = mm == 0 ? R(0) : (mm == 1 ? R(-1) : R(2) * vx);
+                const R dky = n == 0 ? R(0) : (n == 1 ? R(-1) : R(2) * vy);
+                const R dkz = o == 0 ? R(0) : (o == 1 ? R(-1) : R(2) * vz);
+                bv[0] -= zz * rho0 * dkx * ky * kz;
+                bv[1] -= zz * rho0 * kx * dky * kz;
+                bv[2] -= zz * rho0 * kx * ky * dkz;
+                // the transform: d/dv T(v)^-1 kappa = T(v)^-1 (S kappa)
+                if (mm >= 1) bv[0] += zz * R(mm) * K[MIDX(mm - 1, n, o)];
+                if (n >= 1) bv[1] += zz * R(n) * K[MIDX(mm, n - 1, o)];
+                if (o >= 1) bv[2] += zz * R(o) * K[MIDX(mm, n, o - 1)];
+            }
+    // forward mode through the front part, one direction at a time
+    using D = Dual<R>;
+#pragma unroll 1
+    for (int k = 0; k < 13; ++k) {
+        D md[10];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) md[i] = D(m[i], (k == i) ? R(1) : R(0), 0);
+        const D Fx((R)p.F[0], k == 10 ? R(1) : R(0), 0), Fy((R)p.F[1], k == 11 ? R(1) : R(0), 0),
+            Fz((R)p.F[2], k == 12 ? R(1) : R(0), 0);
+        const FFront<D> T = f_front<D>(md, Fx, Fy, Fz, p);
+        G[k] = bsxx * T.sxx.d + bsyy * T.syy.d + bszz * T.szz.d + bkxy * T.kxy.d + bkxz * T.kxz.d +
+               bkyz * T.kyz.d + birho * T.irho.d + bdrho * T.drho.d + bv[0] * T.v[0].d + bv[1] * T.v[1].d +
+               bv[2] * T.v[2].d + w[0] * T.u[0].d + w[1] * T.u[1].d + w[2] * T.u[2].d;
     }
 }
 
@@ -1616,23 +1790,11 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
 #pragma unroll
         for (int i = 0; i < QH; ++i) muh_out[i * N + n] = mu[i];
     }
-    // G_k for the ten moment perturbations (passes 0..9) and the force (10..12)
-    R G[10];
-#pragma unroll 1
-    for (int k = 0; k < 13; ++k) {
-        D fd[27];
+    // G_k for the ten unit-moment perturbations (k < 10) and the force (10..12)
+    R G[13];
+    collide_f_adjoint<R>(g, p, lf, w, G);
 #pragma unroll
-        for (int a = 0; a < 27; ++a) fd[a] = D(g[a], k < 10 ? (R)moment_dir(k, a) : R(0), 0);
-        const D Fx((R)p.F[0], k == 10 ? R(1) : R(0), 0), Fy((R)p.F[1], k == 11 ? R(1) : R(0), 0),
-            Fz((R)p.F[2], k == 12 ? R(1) : R(0), 0);
-        D vx, vy, vz, vr;
-        collide_f_force<D>(fd, p, Fx, Fy, Fz, vx, vy, vz, vr);
-        R acc = w[0] * vx.d + w[1] * vy.d + w[2] * vz.d;
-#pragma unroll
-        for (int a = 0; a < 27; ++a) acc += lf[a] * fd[a].d;
-        if (k < 10) G[k] = acc;
-        else acc6[(size_t)n * 6 + (k - 10)] += (double)acc;
-    }
+    for (int d = 0; d < 3; ++d) acc6[(size_t)n * 6 + d] += (double)G[10 + d];
 #pragma unroll
     for (int b = 0; b < 27; ++b) {
         const R ex = (R)EX(b), ey = (R)EY(b), ez = (R)EZ(b);
