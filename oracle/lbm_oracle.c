@@ -944,6 +944,38 @@ double orc_surface_flux(orc_sim* s, int wall) {
     return flux;
 }
 
+/* Force on wall `wall` by momentum exchange (reading R21; not in the paper:
+ * Ladd 1994, Mei et al. 2002) over the transition from the post-collision
+ * state in s->fs: every link (x_b, a) of the wall carries e_a f*_a(x_b) into
+ * the wall and takes back e_a f_abar(x_b, t+1) from Eq. IBB, so
+ *     F = sum over the links of e_a (f*_a(x_b) + f_abar(x_b, t+1)). */
+static void wall_force_post(const orc_sim* s, int wall, double* F) {
+    const int N = s->N;
+    const lattice_t* L = lattice(27);
+    F[0] = F[1] = F[2] = 0.0;
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_FLUID) continue;
+        for (int a = 1; a < 27; ++a) {
+            float q = s->qtab[(size_t)n * 27 + a];
+            if (q < 0.0f || s->wtab[(size_t)n * 27 + a] != wall) continue;
+            int ab = L->opp[a];
+            int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+            int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+            double fa_f = thin ? 0.0 : s->fs[(size_t)a * N + xf];
+            double fin = ibb(q_eff(s, q), s->fs[(size_t)a * N + n], s->fs[(size_t)ab * N + n], fa_f, thin);
+            double carried = s->fs[(size_t)a * N + n] + fin;
+            for (int d = 0; d < 3; ++d) F[d] += L->e[a][d] * carried;
+        }
+    }
+}
+
+/* The wall force for the transition t -> t+1 from the current state:
+ * collide, then wall_force_post. */
+void orc_wall_force(orc_sim* s, int wall, double* F) {
+    orc_collide(s);
+    wall_force_post(s, wall, F);
+}
+
 /* ---- single-node entry points (used by the pin tests) ---- */
 void orc_lattice(int Q, int* e, double* w, int* opp, int* mom) {
     const lattice_t* L = lattice(Q);
@@ -1089,12 +1121,40 @@ static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, 
     }
 }
 
-/* lam += weight * dF/ds and dTw += weight * dF/dT_w for the objective flux F */
-static void objective_gradient(const orc_sim* s, int kind, int wall, int plane, double weight, double* lam,
-                               double* dTw) {
+/* lam += weight * dF/ds_h, lamf += weight * dF/ds_f and dTw += weight *
+ * dF/dT_w for the objective F.  Kinds: 0 surface heat flux of `wall`, 1
+ * section flux through x = plane, 2 component comp of the force on `wall`
+ * (wall_force_post; lamf must be given). */
+static void objective_gradient(const orc_sim* s, int kind, int wall, int plane, int comp, double weight,
+                               double* lamf, double* lam, double* dTw) {
     const int N = s->N, qh = s->p.qh, nx = s->p.nx;
     const lattice_t* L = lattice(27);
     const lattice_t* Lh = lattice(qh);
+    if (kind == 2) { /* F = sum e_a,comp (f*_a(x_b) + ibb(...)), ibb affine in fs */
+        for (int n = 0; n < N; ++n) {
+            if (s->flags[n] != FL_FLUID) continue;
+            for (int a = 1; a < 27; ++a) {
+                float qf = s->qtab[(size_t)n * 27 + a];
+                if (qf < 0.0f || s->wtab[(size_t)n * 27 + a] != wall) continue;
+                const double c = weight * L->e[a][comp];
+                if (c == 0.0) continue;
+                int ab = L->opp[a];
+                int xf = neighbour(s, n, -L->e[a][0], -L->e[a][1], -L->e[a][2]);
+                int thin = (xf < 0 || s->flags[xf] == FL_SOLID);
+                const double q = q_eff(s, qf);
+                lamf[(size_t)a * N + n] += c;
+                if (q <= 0.5 && !thin) {
+                    lamf[(size_t)a * N + n] += c * 2.0 * q;
+                    lamf[(size_t)a * N + xf] += c * (1.0 - 2.0 * q);
+                } else {
+                    const double qq = q <= 0.5 ? 0.5 : q;
+                    lamf[(size_t)a * N + n] += c / (2.0 * qq);
+                    lamf[(size_t)ab * N + n] += c * (2.0 * qq - 1.0) / (2.0 * qq);
+                }
+            }
+        }
+        return;
+    }
     if (kind == 1) { /* section flux sum e_x h over the plane x = plane */
         for (int n = 0; n < N; ++n) {
             if (n % nx != plane || s->flags[n] == FL_SOLID) continue;
@@ -1122,12 +1182,17 @@ static void objective_gradient(const orc_sim* s, int kind, int wall, int plane, 
     }
 }
 
-/* the objective flux F(s) of the post-collision state in s->hs */
-static double objective_value(orc_sim* s, int kind, int wall, int plane) {
+/* the objective F(s) of the post-collision state in s->fs, s->hs */
+static double objective_value(orc_sim* s, int kind, int wall, int plane, int comp) {
     const int N = s->N, qh = s->p.qh, nx = s->p.nx;
     const lattice_t* L = lattice(27);
     const lattice_t* Lh = lattice(qh);
     double F = 0.0;
+    if (kind == 2) {
+        double Fw[3];
+        wall_force_post(s, wall, Fw);
+        return Fw[comp];
+    }
     if (kind == 1) {
         for (int n = 0; n < N; ++n) {
             if (n % nx != plane || s->flags[n] == FL_SOLID) continue;
@@ -1158,26 +1223,29 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane) {
 /* Forward run from the post-collision state (f_post, h_post) = s^0 over
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
- * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, or -3 for a
+ * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, -3 for a
  * geometry with symmetry rows or a Zou-He inlet (their transposes are not
- * built).
+ * built), or -4 for gradients of a force objective (kind 2; orc_adjoint_flow
+ * carries the f part they need).
  * The Cumulants-1st collision is not affine in h: for that kind the forward
  * keeps the pre-collision h of every level and the reverse sweep applies the
  * transpose of the collision's Jacobian there (cum_jacobian); streaming and
  * the walls stay affine. */
 int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
-                int wall, int plane, double weight, double* J, double* dtheta, double* dTw) {
+                int wall, int plane, int comp, double weight, double* J, double* dtheta, double* dTw) {
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
     const int cum = s->p.hkind == KIND_CUM1;
     /* the transposes of the symmetry rows and of the Zou-He inlet are not built */
     if (dtheta && (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x))) return -3;
+    /* a force objective depends on f: only the coupled adjoint carries it */
+    if (dtheta && kind == 2) return -4;
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
     double* hrec = (dtheta && cum) ? (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double)) : NULL;
     orc_set_post(s, f_post, h_post);
     double Jv = 0.0;
     for (int k = 0; k <= nsteps; ++k) {
-        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane);
+        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane, comp);
         if (k == nsteps) break;
         if (orc_stream(s) != 0) { free(urec); free(hrec); return -1; }
         if (hrec) memcpy(hrec + (size_t)(k + 1) * HN, s->h, HN * sizeof(double));
@@ -1192,7 +1260,7 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     for (int k = nsteps; k >= 0; --k) {
         for (size_t i = 0; i < HN; ++i) lam[i] = 0.0;
         if (k < nsteps) stream_transpose_h(s, mu, lam, dTw);
-        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, weight, lam, dTw);
+        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, comp, weight, NULL, lam, dTw);
         for (size_t i = 0; i < HN; ++i) mu[i] = 0.0;
         if (k == 0) break;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -1301,8 +1369,8 @@ static void stream_transpose_f(const orc_sim* s, const double* mu, double* lam) 
 /* Returns 0, -1 on a streaming error, -3 for a geometry with symmetry rows or
  * a Zou-He inlet.  dF[3] and duin[3] (and dtheta[N], dTw[nwalls]) are added to. */
 int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
-                     int wall, int plane, double weight, double* J, double* dtheta, double* dTw, double* dF,
-                     double* duin) {
+                     int wall, int plane, int comp, double weight, double* J, double* dtheta, double* dTw,
+                     double* dF, double* duin) {
     const int N = s->N, qh = s->p.qh;
     const size_t FN = (size_t)27 * N, HN = (size_t)qh * N;
     if (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x)) return -3;
@@ -1311,7 +1379,7 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
     orc_set_post(s, f_post, h_post);
     double Jv = 0.0;
     for (int k = 0; k <= nsteps; ++k) {
-        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane);
+        if (k >= t0 && k <= t1) Jv += weight * objective_value(s, kind, wall, plane, comp);
         if (k == nsteps) break;
         if (orc_stream(s) != 0) { free(frec); free(hrec); return -1; }
         memcpy(frec + (size_t)(k + 1) * FN, s->f, FN * sizeof(double));
@@ -1350,7 +1418,7 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
             stream_transpose_f(s, muf, lamf);
             stream_transpose_h(s, muh, lamh, dTw);
         }
-        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, weight, lamh, dTw);
+        if (k >= t0 && k <= t1) objective_gradient(s, kind, wall, plane, comp, weight, lamf, lamh, dTw);
         for (size_t i = 0; i < FN; ++i) muf[i] = 0.0;
         for (size_t i = 0; i < HN; ++i) muh[i] = 0.0;
         if (k == 0) break;

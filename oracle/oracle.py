@@ -109,12 +109,13 @@ def lib():
         L.orc_num_threads.restype = C.c_int
         L.orc_adjoint.restype = C.c_int
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                  C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
+                                  C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
                                   C.c_void_p]
         L.orc_adjoint_flow.restype = C.c_int
         L.orc_adjoint_flow.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                       C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
+                                       C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_wall_force.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     return _lib
 
 
@@ -183,6 +184,19 @@ def num_threads() -> int:
 
 
 # ---- simulation ----------------------------------------------------------
+def _objective_args(objective):
+    """(kind, wall, plane, component) of an objective tuple: ("surface", wall,
+    weight), ("section", plane_x, weight) or ("force", wall, weight, component)."""
+    name = objective[0]
+    if name == "surface":
+        return 0, int(objective[1]), 0, 0
+    if name == "section":
+        return 1, 0, int(objective[1]), 0
+    if name == "force":
+        return 2, int(objective[1]), 0, int(objective[3])
+    raise ValueError(f"unknown objective {name!r}")
+
+
 class OracleError(RuntimeError):
     pass
 
@@ -279,25 +293,32 @@ class Oracle:
     def surface_flux(self, wall):
         return float(lib().orc_surface_flux(self._h, int(wall)))
 
+    def wall_force(self, wall):
+        """Momentum-exchange force on a wall for the next transition (collides
+        the current state first, like surface_flux)."""
+        F = np.zeros(3)
+        lib().orc_wall_force(self._h, int(wall), F.ctypes.data)
+        return F
+
     def adjoint(self, f_post, h_post, nsteps, window, objective, nwalls=1, gradients=True):
         """J = weight * sum over levels k in window of the flux F(s^k), from the
         post-collision state (f_post, h_post) = s^0 over nsteps steps.
-        objective: ("surface", wall, weight) or ("section", plane_x, weight).
+        objective: ("surface", wall, weight), ("section", plane_x, weight) or
+        ("force", wall, weight, component) (the last for J only here; its
+        gradients need adjoint_flow).
         Returns (J, dJ/dtheta[N], dJ/dT_w[nwalls]) (gradients None if not asked)."""
-        kind = 0 if objective[0] == "surface" else 1
-        wall = int(objective[1]) if kind == 0 else 0
-        plane = int(objective[1]) if kind == 1 else 0
+        kind, wall, plane, comp = _objective_args(objective)
         f_post = np.ascontiguousarray(f_post, dtype=np.float64)
         h_post = np.ascontiguousarray(h_post, dtype=np.float64)
         J = C.c_double()
         dth = np.zeros(self.N) if gradients else None
         dTw = np.zeros(nwalls) if gradients else None
         rc = lib().orc_adjoint(self._h, f_post.ctypes.data, h_post.ctypes.data, int(nsteps), int(window[0]),
-                               int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
+                               int(window[1]), kind, wall, plane, comp, float(objective[2]), C.byref(J),
                                dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
         if rc != 0:
-            raise OracleError("orc_adjoint: " + ("no adjoint with symmetry rows or a Zou-He inlet" if rc == -3
-                                                 else "streaming error"))
+            raise OracleError("orc_adjoint: " + {-3: "no adjoint with symmetry rows or a Zou-He inlet",
+                                                 -4: "force objectives need adjoint_flow"}.get(rc, "streaming error"))
         return J.value, dth, dTw
 
     def adjoint_flow(self, f_post, h_post, nsteps, window, objective, nwalls=1):
@@ -305,9 +326,7 @@ class Oracle:
         dJ/dT_w[nwalls], dJ/dF[3], dJ/du_in[3]) for the objective of
         adjoint() (F: body force; u_in: inlet velocity of the equilibrium
         inlet plane)."""
-        kind = 0 if objective[0] == "surface" else 1
-        wall = int(objective[1]) if kind == 0 else 0
-        plane = int(objective[1]) if kind == 1 else 0
+        kind, wall, plane, comp = _objective_args(objective)
         f_post = np.ascontiguousarray(f_post, dtype=np.float64)
         h_post = np.ascontiguousarray(h_post, dtype=np.float64)
         J = C.c_double()
@@ -316,7 +335,7 @@ class Oracle:
         dF = np.zeros(3)
         duin = np.zeros(3)
         rc = lib().orc_adjoint_flow(self._h, f_post.ctypes.data, h_post.ctypes.data, int(nsteps), int(window[0]),
-                                    int(window[1]), kind, wall, plane, float(objective[2]), C.byref(J),
+                                    int(window[1]), kind, wall, plane, comp, float(objective[2]), C.byref(J),
                                     dth.ctypes.data, dTw.ctypes.data, dF.ctypes.data, duin.ctypes.data)
         if rc != 0:
             raise OracleError("orc_adjoint_flow: " + ("no adjoint with symmetry rows or a Zou-He inlet"
