@@ -197,6 +197,16 @@ lbm_status lbm_nusselt(lbm_ctx* ctx, int wall_id, double length, double area, do
  * state, FP64.  Synchronises. */
 lbm_status lbm_section_flux(lbm_ctx* ctx, int plane_x, double* flux);
 
+/* Force on wall wall_id by momentum exchange (not in the paper: Ladd 1994,
+ * Mei et al. 2002), for the transition from the current post-collision state
+ * to the next step: force[d] = sum over the wall's links (x_b, a) of
+ * e_a,d (f*_a(x_b) + f_abar(x_b, t+1)), with f_abar from Eq. IBB exactly as
+ * lbm_step applies it and full populations (the storage shift included).
+ * force: host double[3].  In a periodic box the forces on all walls add up to
+ * N_fluid F minus the change of the fluid's momentum over the step.
+ * LBM_ERR_INVALID for a wall id out of range.  Synchronises. */
+lbm_status lbm_wall_force(lbm_ctx* ctx, int wall_id, double* force);
+
 /* Bytes needed by lbm_save_state. */
 lbm_status lbm_state_size(lbm_ctx* ctx, size_t* bytes);
 
@@ -219,15 +229,17 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes, int is_de
  * (s^k: post-collision h of level k, g: arrivals after streaming and walls,
  * L, e from Eq. H_cm_collision).  The Cumulants-1st collision is nonlinear in
  * g; its adjoint uses the Jacobian at recorded states (lbm_step_record_h,
- * lbm_adjoint_step_h).  An objective is a linear flux F of s^k summed with a
- * weight over a window of levels; the adjoint runs the transposed steps
+ * lbm_adjoint_step_h).  An objective is a linear function F of s^k (a heat
+ * flux of h; for the coupled adjoint below also a wall force of f) summed
+ * with a weight over a window of levels; the adjoint runs the transposed steps
  * backwards.  Velocity records, adjoint arrays: element type
  * float, or double for LBM_F64 contexts; SoA [3][N] and [Q_h][N]. */
-typedef enum { LBM_OBJ_SURFACE_FLUX = 0, LBM_OBJ_SECTION_FLUX = 1 } lbm_objective_kind;
+typedef enum { LBM_OBJ_SURFACE_FLUX = 0, LBM_OBJ_SECTION_FLUX = 1, LBM_OBJ_WALL_FORCE = 2 } lbm_objective_kind;
 typedef struct {
     int kind;       /* lbm_objective_kind */
-    int wall_id;    /* SURFACE_FLUX: the wall (lbm_surface_flux's flux) */
+    int wall_id;    /* SURFACE_FLUX, WALL_FORCE: the wall */
     int plane_x;    /* SECTION_FLUX: the plane (lbm_section_flux's flux) */
+    int component;  /* WALL_FORCE: 0, 1, 2 for the x, y, z component of lbm_wall_force */
     double weight;  /* J += weight * F(level) */
 } lbm_objective;
 
@@ -260,6 +272,9 @@ lbm_status lbm_step_record_h(lbm_ctx* ctx, int n, void* u_rec, void* h_rec);
  * Asynchronous. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_next, void* out,
                             const lbm_objective* obj, double* dJ_dtheta);
+/* (A WALL_FORCE objective depends on f: lbm_adjoint_step and
+ * lbm_adjoint_step_h return LBM_ERR_INVALID for it; lbm_adjoint_flow_step
+ * takes it.) */
 
 /* lbm_adjoint_step for every h kind, given also h_level, the level's
  * post-collision h record from lbm_step_record_h (ignored by the

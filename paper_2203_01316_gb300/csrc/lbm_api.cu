@@ -898,6 +898,24 @@ lbm_status lbm_surface_flux(lbm_ctx* c, int wall_id, double* flux) {
     return LBM_OK;
 }
 
+lbm_status lbm_wall_force(lbm_ctx* c, int wall_id, double* force) {
+    if (!c || !force) return LBM_ERR_INVALID;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
+    if (wall_id < 0 || wall_id >= c->n_walls) return fail(c, LBM_ERR_INVALID, "wall id out of range");
+    DeviceGuard g(c->device);
+    const Buffers b = buffers(c);
+    const DevParams p = c->dp;
+    double* out = c->d_scratch + 3 * lbmd::kRedBlocks;
+    CK(dispatch(c, [&](auto tag) {
+           using Tg = decltype(tag);
+           return lbmd::launch_wall_force<typename Tg::S, Tg::Q>(b, p, wall_id, c->d_scratch, out, c->stream);
+       }),
+       "wall force launch");
+    CK(cudaMemcpyAsync(force, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "wall force copy");
+    CK(cudaStreamSynchronize(c->stream), "wall force");
+    return LBM_OK;
+}
+
 lbm_status lbm_nusselt(lbm_ctx* c, int wall_id, double length, double area, double dT, double* nu_out) {
     if (!c || !nu_out) return LBM_ERR_INVALID;
     if (!(area > 0.0) || dT == 0.0 || !(length > 0.0)) return fail(c, LBM_ERR_INVALID, "length, area must be > 0, dT != 0");
@@ -1019,6 +1037,7 @@ static lbmd::AdjObjective to_adj(const lbm_objective* o) {
     a.kind = o ? o->kind : 0;
     a.wall = o ? o->wall_id : -1;
     a.plane = o ? o->plane_x : -1;
+    a.comp = o ? o->component : 0;
     a.weight = o ? o->weight : 0.0;
     if (!o) a.kind = 0, a.wall = -1;
     return a;
@@ -1030,6 +1049,9 @@ static lbm_status check_objective(lbm_ctx* c, const lbm_objective* o) {
         if (o->wall_id < 0 || o->wall_id >= c->n_walls) return fail(c, LBM_ERR_INVALID, "objective wall id out of range");
     } else if (o->kind == LBM_OBJ_SECTION_FLUX) {
         if (o->plane_x < 0 || o->plane_x >= c->p.nx) return fail(c, LBM_ERR_INVALID, "objective plane out of range");
+    } else if (o->kind == LBM_OBJ_WALL_FORCE) {
+        if (o->wall_id < 0 || o->wall_id >= c->n_walls) return fail(c, LBM_ERR_INVALID, "objective wall id out of range");
+        if (o->component < 0 || o->component > 2) return fail(c, LBM_ERR_INVALID, "force component must be 0, 1 or 2");
     } else {
         return fail(c, LBM_ERR_INVALID, "unknown objective kind");
     }
@@ -1097,6 +1119,8 @@ static lbm_status adjoint_step_impl(lbm_ctx* c, const void* u_level, const void*
                     "the Cumulants-1st adjoint needs the level's h record (lbm_step_record_h, lbm_adjoint_step_h)");
     lbm_status st = check_objective(c, obj);
     if (st != LBM_OK) return st;
+    if (obj && obj->kind == LBM_OBJ_WALL_FORCE)
+        return fail(c, LBM_ERR_INVALID, "a wall-force objective needs the coupled adjoint (lbm_adjoint_flow_step)");
     DeviceGuard g(c->device);
     const Buffers b = buffers(c);
     const DevParams p = c->dp;
@@ -1274,7 +1298,7 @@ lbm_status lbm_objective_accumulate(lbm_ctx* c, const lbm_objective* obj, double
 
 lbm_status lbm_section_flux(lbm_ctx* c, int plane_x, double* flux) {
     if (!c || !flux) return LBM_ERR_INVALID;
-    lbm_objective o{LBM_OBJ_SECTION_FLUX, 0, plane_x, 1.0};
+    lbm_objective o{LBM_OBJ_SECTION_FLUX, 0, plane_x, 0, 1.0};
     double* acc = c->d_scratch + 3 * lbmd::kRedBlocks + 3;
     DeviceGuard g(c->device);
     CK(cudaMemsetAsync(acc, 0, sizeof(double), c->stream), "section flux");

@@ -38,10 +38,11 @@ struct Buffers {
     void* hrec;               // recorded pre-collision h arrivals (Q_h N, R) or nullptr
 };
 
-// objective of the adjoint: a linear flux of the post-collision h state
+// objective of the adjoint: a linear function of the post-collision state
 struct AdjObjective {
-    int kind;       // 0: surface heat flux of `wall`; 1: sum e_x h over the plane x = plane
-    int wall, plane;
+    int kind;       // 0: surface heat flux of `wall`; 1: sum e_x h over the plane x = plane;
+                    // 2: component `comp` of the momentum-exchange force on `wall` (f only)
+    int wall, plane, comp;
     double weight;  // 0: no objective term at this level
 };
 
@@ -92,7 +93,8 @@ cudaError_t launch_adjoint_flow(const Buffers& b, const DevParams& p, const R* f
 // rec[i * N + n] = post-collision h deviation of population i at node n (type R)
 template <typename S, int QH>
 cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s);
-// *acc += weight * F(current level) (F: surface flux of a wall or section flux of a plane)
+// *acc += weight * F(current level) (F: surface flux of a wall, section flux of a plane or one
+// component of a wall's force)
 template <typename S, int QH>
 cudaError_t launch_objective(const Buffers& b, const DevParams& p, AdjObjective obj, double* scratch, double* acc,
                              cudaStream_t s);
@@ -109,6 +111,10 @@ cudaError_t launch_balances(const Buffers& b, const DevParams& p, double* scratc
 template <typename S, int QH>
 cudaError_t launch_surface_flux(const Buffers& b, const DevParams& p, int wall, double* scratch, double* out,
                                 cudaStream_t s);
+// partial sums: scratch[3*kRedBlocks] -> out[3] = momentum-exchange force on the wall
+template <typename S, int QH>
+cudaError_t launch_wall_force(const Buffers& b, const DevParams& p, int wall, double* scratch, double* out,
+                              cudaStream_t s);
 cudaError_t launch_stream_map(const Buffers& b, const DevParams& p, int qh, int32_t* src, cudaStream_t s);
 
 #ifdef LBM_KERNEL_TU
@@ -904,6 +910,68 @@ cudaError_t launch_surface_flux(const Buffers& b, const DevParams& p, int wall, 
     return cudaGetLastError();
 }
 
+// force on one wall by momentum exchange (Ladd 1994, Mei et al. 2002; not in
+// the paper): every link (x_b, a) of the wall carries e_a f*_a(x_b, t) into
+// the wall and takes back e_a f_abar(x_b, t+1) from Eq. IBB, exactly as the
+// step applies it; the stored deviations add 2 w_a rho0 per link
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_wall_force(const S* __restrict__ fA,
+                                                            const int32_t* __restrict__ wnode,
+                                                            const uint32_t* __restrict__ wmask,
+                                                            const int32_t* __restrict__ woff,
+                                                            const float* __restrict__ lq,
+                                                            const int32_t* __restrict__ lwall, int nw, int wall,
+                                                            double* __restrict__ part, const DevParams p) {
+    using R = typename Acc<S>::R;
+    __shared__ double sh[3 * 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    const size_t N = (size_t)p.N;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        const int n = wnode[w];
+        const uint32_t mask = wmask[w];
+        const int off = woff[w];
+        int x, y, z;
+        node_xyz(n, p, x, y, z);
+        const Nbr nb = make_nbr(x, y, z, p);
+#pragma unroll
+        for (int a = 1; a < 27; ++a) {
+            if (!(mask & (1u << a))) continue;
+            const int l = off + __popc(mask & ((1u << a) - 1u));
+            if (lwall[l] != wall) continue;
+            const int b = OPP(a);
+            const float q = lq[l];
+            const bool thin = (mask >> b) & 1u;  // x_f = x_b - e_a is solid
+            const R fa_b = ld<R>(fA + a * N + n);
+            R fin;
+            if (q <= 0.5f && !thin) {
+                fin = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * ld<R>(fA + a * N + src_of(nb, a));
+            } else {
+                const R qq = (R)fmaxf(q, 0.5f);
+                fin = (fa_b + (R(2) * qq - R(1)) * ld<R>(fA + b * N + n)) / (R(2) * qq);
+            }
+            const double carried = (double)fa_b + (double)fin + 2.0 * W27(a) * p.rho0;
+            v[0] += EX(a) * carried;
+            v[1] += EY(a) * carried;
+            v[2] += EZ(a) * carried;
+        }
+    }
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = v[0];
+        part[3 * blockIdx.x + 1] = v[1];
+        part[3 * blockIdx.x + 2] = v[2];
+    }
+}
+
+template <typename S, int QH>
+cudaError_t launch_wall_force(const Buffers& b, const DevParams& p, int wall, double* scratch, double* out,
+                              cudaStream_t s) {
+    k_wall_force<S><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.fA, b.wnode, b.wmask, b.woff, b.lq, b.lwall,
+                                                      b.nw, wall, scratch, p);
+    k_reduce_partials<3><<<1, 1024, 0, s>>>(scratch, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
 // ---- adjoint of the h evolution --------------------------------------------
 // With u fixed (one-way coupling), one step is g^{k+1} = P s^k + b(T_w) and
 // s^{k+1} = L(u^{k+1}) g^{k+1} + e(u^{k+1}) theta, with
@@ -1394,6 +1462,9 @@ cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s) 
 
 // Eq. IBB: derivative of the arrival f_abar(x_b) with respect to f*_a(x_b)
 // and f*_abar(x_b) (the x_f term goes through the reverse-link table)
+// component d of e_a
+__device__ __forceinline__ int ecomp(int a, int d) { return d == 0 ? EX(a) : (d == 1 ? EY(a) : EZ(a)); }
+
 template <typename R>
 __device__ __forceinline__ void ibb_partials(float q, bool thin, R& d_ab, R& d_abb) {
     if (q <= 0.5f && !thin) {
@@ -1638,7 +1709,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
     const int pl = p.nx * p.ny;
     const int zt[3] = {((z == 0) ? p.nz - 1 : z - 1) * pl, z * pl, ((z == p.nz - 1) ? 0 : z + 1) * pl};
     const R wsurf = (obj.kind == 0) ? (R)obj.weight : R(0);
-    // lambda = P^T mu^{k+1} (+ the objective's terms for h)
+    // force objective: d/ds_f of weight * e_a,comp (f*_a(x_b) + f_abar(x_b)) per link of obj.wall
+    const R wforce = (obj.kind == 2) ? (R)obj.weight : R(0);
+    // lambda = P^T mu^{k+1} (+ the objective's terms)
     R lf[27], lh[QH];
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
@@ -1675,7 +1748,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
             const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
             const float q = __ldg(lq + l);
             const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
-            lf[a] += (R(1) - R(2) * (R)q) * muf_next[OPP(a) * N + t];
+            const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(a, obj.comp) : R(0);
+            lf[a] += (R(1) - R(2) * (R)q) * (muf_next[OPP(a) * N + t] + cf);
         }
 #pragma unroll
         for (int i = 0; i < QH; ++i) {
@@ -1696,12 +1770,14 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
         for (int b = 0; b < 27; ++b) {
             if (!(mask & (1u << b))) continue;
             const int ib = OPP(b);
-            const float q = __ldg(lq + off + __popc(mask & ((1u << b) - 1u)));
+            const int l = off + __popc(mask & ((1u << b) - 1u));
+            const float q = __ldg(lq + l);
             const bool thin = (mask >> ib) & 1u;
             R d_ab, d_abb;
             ibb_partials<R>(q, thin, d_ab, d_abb);
-            const R m = muf_next[ib * N + n];
-            lf[b] += d_ab * m;
+            const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(b, obj.comp) : R(0);
+            const R m = muf_next[ib * N + n] + cf;
+            lf[b] += d_ab * m + cf;
             lf[ib] += d_abb * m;
         }
 #pragma unroll
@@ -1836,7 +1912,7 @@ cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cud
 }
 
 template <int NV>
-__global__ void k_reduce_accumulate(const double* __restrict__ part, int nparts, double weight,
+__global__ void k_reduce_accumulate(const double* __restrict__ part, int nparts, int pick, double weight,
                                     double* __restrict__ acc) {
     __shared__ double sh[32 * NV];
     double v[NV];
@@ -1846,7 +1922,7 @@ __global__ void k_reduce_accumulate(const double* __restrict__ part, int nparts,
 #pragma unroll
         for (int k = 0; k < NV; ++k) v[k] += part[i * NV + k];
     block_sum<NV>(v, sh);
-    if (threadIdx.x == 0) acc[0] += weight * v[0];
+    if (threadIdx.x == 0) acc[0] += weight * v[pick];
 }
 
 // x-flux sum e_x h through the plane x = plane (Sec. 4.4 section flux; the
@@ -1876,12 +1952,18 @@ __global__ void __launch_bounds__(kRedThreads) k_section_flux(const S* __restric
 template <typename S, int QH>
 cudaError_t launch_objective(const Buffers& b, const DevParams& p, AdjObjective obj, double* scratch, double* acc,
                              cudaStream_t s) {
+    if (obj.kind == 2) {
+        k_wall_force<S><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.fA, b.wnode, b.wmask, b.woff, b.lq, b.lwall,
+                                                          b.nw, obj.wall, scratch, p);
+        k_reduce_accumulate<3><<<1, 1024, 0, s>>>(scratch, kRedBlocks, obj.comp, obj.weight, acc);
+        return cudaGetLastError();
+    }
     if (obj.kind == 0)
         k_surface_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.wnode, b.wmask, b.woff, b.lq,
                                                                 b.lwall, b.Twall, b.nw, obj.wall, scratch, p);
     else
         k_section_flux<S, QH><<<kRedBlocks, kRedThreads, 0, s>>>((const S*)b.hA, b.flags, obj.plane, scratch, p);
-    k_reduce_accumulate<1><<<1, 1024, 0, s>>>(scratch, kRedBlocks, obj.weight, acc);
+    k_reduce_accumulate<1><<<1, 1024, 0, s>>>(scratch, kRedBlocks, 0, obj.weight, acc);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@ template cudaError_t launch_inlet<float, 7>(const Buffers&, const DevParams&, cu
 template cudaError_t launch_balances<float, 7>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
+template cudaError_t launch_wall_force<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
+                                               cudaStream_t);
 template cudaError_t launch_step_staged<float, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*,
                                            const float*, float*, AdjObjective, double*, cudaStream_t);

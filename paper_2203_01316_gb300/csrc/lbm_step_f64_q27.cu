@@ -17,6 +17,8 @@ template cudaError_t launch_inlet<double, 27>(const Buffers&, const DevParams&, 
 template cudaError_t launch_balances<double, 27>(const Buffers&, const DevParams&, double*, double*, cudaStream_t);
 template cudaError_t launch_surface_flux<double, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                  cudaStream_t);
+template cudaError_t launch_wall_force<double, 27>(const Buffers&, const DevParams&, int, double*, double*,
+                                               cudaStream_t);
 template cudaError_t launch_adjoint<double, 27>(const Buffers&, const DevParams&, const double*, const double*,
                                            const double*, double*, AdjObjective, double*, cudaStream_t);
 template cudaError_t launch_adjoint_flow<double, 27>(const Buffers&, const DevParams&, const double*, const double*,

@@ -27,14 +27,15 @@ SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_s
            "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
            "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
            "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h", "lbm_step_record_pre",
-           "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient"]
-OBJ_SURFACE, OBJ_SECTION = 0, 1
+           "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient", "lbm_wall_force"]
+OBJ_SURFACE, OBJ_SECTION, OBJ_FORCE = 0, 1, 2
 
 
 class Objective(C.Structure):
-    """lbm_objective: J += weight * F(level), F the surface flux of a wall or
-    the section flux of a plane."""
-    _fields_ = [("kind", C.c_int), ("wall_id", C.c_int), ("plane_x", C.c_int), ("weight", C.c_double)]
+    """lbm_objective: J += weight * F(level), F the surface flux of a wall,
+    the section flux of a plane or one component of a wall's force."""
+    _fields_ = [("kind", C.c_int), ("wall_id", C.c_int), ("plane_x", C.c_int), ("component", C.c_int),
+                ("weight", C.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -88,6 +89,7 @@ def lib():
         "lbm_save_state": [vp, vp, C.POINTER(C.c_size_t), i32],
         "lbm_load_state": [vp, vp, C.c_size_t, i32],
         "lbm_section_flux": [vp, i32, C.POINTER(dbl)],
+        "lbm_wall_force": [vp, i32, vp],
         "lbm_objective_accumulate": [vp, C.POINTER(Objective), vp],
         "lbm_step_record": [vp, i32, vp, i32],
         "lbm_adjoint_step": [vp, vp, vp, vp, C.POINTER(Objective), vp],
@@ -295,13 +297,22 @@ class Solver:
         self._check(self.L.lbm_section_flux(self._h, int(plane_x), C.byref(q)))
         return q.value
 
+    def wall_force(self, wall):
+        """Momentum-exchange force on a wall (numpy float64[3])."""
+        F = np.zeros(3)
+        self._check(self.L.lbm_wall_force(self._h, int(wall), F.ctypes.data))
+        return F
+
     # -- adjoint (device tensors; see include/lbm.h) --
     @staticmethod
-    def objective(kind, index, weight=1.0):
+    def objective(kind, index, weight=1.0, component=0):
+        """kind "surface" (index: wall), "section" (index: plane x) or
+        "force" (index: wall; component 0, 1, 2)."""
         o = Objective()
-        o.kind = OBJ_SURFACE if kind == "surface" else OBJ_SECTION
-        o.wall_id = int(index) if o.kind == OBJ_SURFACE else 0
+        o.kind = {"surface": OBJ_SURFACE, "section": OBJ_SECTION, "force": OBJ_FORCE}[kind]
+        o.wall_id = int(index) if o.kind != OBJ_SECTION else 0
         o.plane_x = int(index) if o.kind == OBJ_SECTION else 0
+        o.component = int(component)
         o.weight = float(weight)
         return o
 

@@ -32,7 +32,7 @@ def _box_case(seed=11, wall_bc="iabb", nx=12, ny=10, nz=8):
     N = flags.size
     u = I.uniform(seed, 3 * N, -0.04, 0.04).reshape(3, N)
     u[:, flags == I.SOLID] = 0.0
-    w = {"dims": (nx, ny, nz), "flags": flags, "links": links, "nwalls": 3,
+    w = {"dims": (nx, ny, nz), "flags": flags, "links": links, "nwalls": 3, "periodic_x": True,
          "rho": 1.0 + I.uniform(seed + 1, N, -0.02, 0.02), "u": u,
          "T": I.uniform(seed + 2, N, 0.2, 1.0), "theta": np.zeros(N)}
     p = O.make_params(nx=nx, ny=ny, nz=nz, qh=27, hkind="trt", nu=0.05, k=0.01, F=(3e-4, -1e-4, 2e-4),
