@@ -111,10 +111,27 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def _between(text, start, end):
+    i = text.index(start)
+    return text[i:text.index(end, i)]
+
+
+def kernel_source_hash(csrc=None):
+    """Hash of the source the timed step kernel is built from: all of
+    lbm_device.cuh, and from lbm_kernels.cuh the block size, the step kernel
+    with its helpers and launch_step.  Recorded DRAM traffic is reported only
+    while this is unchanged."""
+    csrc = csrc or os.path.join(ROOT, "paper_2203_01316_gb300", "csrc")
+    dev = open(os.path.join(csrc, "lbm_device.cuh")).read()
+    ker = open(os.path.join(csrc, "lbm_kernels.cuh")).read()
+    parts = [dev,
+             _between(ker, "constexpr int kBlock", "\n"),
+             _between(ker, "#ifdef LBM_KERNEL_TU", "// ---- staged step"),
+             _between(ker, "cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h) {",
+                      "\n}\n")]
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh", "lbm_kernels.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2203_01316_gb300", "csrc", f), "rb").read())
+    for t in parts:
+        h.update(t.encode())
     return h.hexdigest()[:16]
 
 
