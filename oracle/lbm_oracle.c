@@ -714,17 +714,17 @@ static double iabb(double q, double ha_b, double hab_b, double ha_f, int thin, d
  * and N_d = sum_{e_x=0} e_d (f - f^eq) / 6 so that the transverse momentum is
  * rho u_d exactly (the six unknowns with e_d != 0 share the correction).
  * h: the unknowns take the shape of the equilibrium at u_in with the amplitude
- * that makes the zeroth moment rho T_in. */
-static void zou_he_inlet(orc_sim* s, int n) {
-    const int N = s->N, qh = s->p.qh;
+ * that makes the zeroth moment rho T_in.
+ * zou_he_local applies the rule to one node's arrivals f[27], h[qh] (the
+ * e_x = +1 entries are outputs only); for fixed u_in it is affine in (f, h). */
+static void zou_he_local(const orc_params* p, const double* u, double* f, double* h) {
+    const int qh = p->qh;
     const lattice_t* L = lattice(27);
     const lattice_t* Lh = lattice(qh);
-    const double* u = s->p.u_in;
     double known0 = 0.0, known_out = 0.0;
     for (int a = 0; a < 27; ++a) {
-        double v = s->fn[(size_t)a * N + n];
-        if (L->e[a][0] == 0) known0 += v;
-        else if (L->e[a][0] < 0) known_out += v;
+        if (L->e[a][0] == 0) known0 += f[a];
+        else if (L->e[a][0] < 0) known_out += f[a];
     }
     const double rho = (known0 + 2.0 * known_out) / (1.0 - u[0]);
     double feq[27];
@@ -732,24 +732,33 @@ static void zou_he_inlet(orc_sim* s, int n) {
     double Nt[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 27; ++a) {
         if (L->e[a][0] != 0) continue;
-        for (int d = 1; d < 3; ++d) Nt[d] += L->e[a][d] * (s->fn[(size_t)a * N + n] - feq[a]);
+        for (int d = 1; d < 3; ++d) Nt[d] += L->e[a][d] * (f[a] - feq[a]);
     }
     for (int d = 1; d < 3; ++d) Nt[d] /= 6.0;
     for (int a = 0; a < 27; ++a) {
         if (L->e[a][0] != 1) continue;
         int ab = L->opp[a];
-        s->fn[(size_t)a * N + n] = s->fn[(size_t)ab * N + n] + feq[a] - feq[ab] - L->e[a][1] * Nt[1] -
-                                   L->e[a][2] * Nt[2];
+        f[a] = f[ab] + feq[a] - feq[ab] - L->e[a][1] * Nt[1] - L->e[a][2] * Nt[2];
     }
     double M[27], known_h = 0.0, unknown_w = 0.0;
     equilibrium(Lh, 1.0, u, M);
     for (int a = 0; a < qh; ++a) {
         if (Lh->e[a][0] == 1) unknown_w += M[a];
-        else known_h += s->hn[(size_t)a * N + n];
+        else known_h += h[a];
     }
-    const double amp = (rho * s->p.T_in - known_h) / unknown_w;
+    const double amp = (rho * p->T_in - known_h) / unknown_w;
     for (int a = 0; a < qh; ++a)
-        if (Lh->e[a][0] == 1) s->hn[(size_t)a * N + n] = amp * M[a];
+        if (Lh->e[a][0] == 1) h[a] = amp * M[a];
+}
+
+static void zou_he_inlet(orc_sim* s, int n) {
+    const int N = s->N, qh = s->p.qh;
+    double f[27], h[27];
+    for (int a = 0; a < 27; ++a) f[a] = s->fn[(size_t)a * N + n];
+    for (int a = 0; a < qh; ++a) h[a] = s->hn[(size_t)a * N + n];
+    zou_he_local(&s->p, s->p.u_in, f, h);
+    for (int a = 0; a < 27; ++a) s->fn[(size_t)a * N + n] = f[a];
+    for (int a = 0; a < qh; ++a) s->hn[(size_t)a * N + n] = h[a];
 }
 
 /* Streaming of fs, hs (push, Sec. 2.1 evolution equation) with Eq. (IBB),
@@ -1076,6 +1085,79 @@ static void cum_jacobian(const orc_params* p, const double* h, const double u[3]
         }
 }
 
+
+/* whether node t keeps what streaming delivers to it: not outside the box,
+ * not solid (symmetry nodes included), not an equilibrium inlet node (which
+ * overwrites its arrivals; a Zou-He inlet node keeps the known ones) */
+static int receives(const orc_sim* s, int t) {
+    if (t < 0 || s->flags[t] == FL_SOLID) return 0;
+    if (s->flags[t] == FL_INLET && !s->p.inlet_bc) return 0;
+    return 1;
+}
+
+static double cd4(double fp1, double fm1, double fp2, double fm2, double e);
+
+/* Adjoint of the Zou-He rule (zou_he_local, reading R20) at every inlet
+ * node, in place: mu (the adjoint of the state after the rule) becomes the
+ * adjoint of the arrivals, mu_arr = A^T mu with A = d out / d in.  The rule
+ * is affine in the arrivals for fixed u_in, so A's columns are the images of
+ * unit arrivals minus the image of zero.  muf NULL: the h-only adjoint (f is
+ * fixed there, so only the h block of A enters).  With duin non-NULL also
+ * duin += (d out / d u_in)^T mu, by 4-point differences at the level's
+ * arrivals (frec, hrec: the level's state after the rule, whose known
+ * entries are the arrivals). */
+static void zou_he_transpose(const orc_sim* s, double* muf, double* muh, const double* frec, const double* hrec,
+                             double* duin) {
+    const int N = s->N, qh = s->p.qh, M = 27 + qh;
+    double* A = (double*)malloc((size_t)M * M * sizeof(double));
+    double z_f[27] = {0}, z_h[27] = {0}, c[54];
+    zou_he_local(&s->p, s->p.u_in, z_f, z_h);
+    for (int i = 0; i < 27; ++i) c[i] = z_f[i];
+    for (int i = 0; i < qh; ++i) c[27 + i] = z_h[i];
+    for (int j = 0; j < M; ++j) {
+        double f[27] = {0}, h[27] = {0};
+        if (j < 27) f[j] = 1.0; else h[j - 27] = 1.0;
+        zou_he_local(&s->p, s->p.u_in, f, h);
+        for (int i = 0; i < 27; ++i) A[(size_t)i * M + j] = f[i] - c[i];
+        for (int i = 0; i < qh; ++i) A[(size_t)(27 + i) * M + j] = h[i] - c[27 + i];
+    }
+    for (int n = 0; n < N; ++n) {
+        if (s->flags[n] != FL_INLET) continue;
+        double m[54], out[54];
+        for (int i = 0; i < 27; ++i) m[i] = muf ? muf[(size_t)i * N + n] : 0.0;
+        for (int i = 0; i < qh; ++i) m[27 + i] = muh[(size_t)i * N + n];
+        if (duin) {
+            const double e = 1e-3;
+            const double off[4] = {e, -e, 2 * e, -2 * e};
+            for (int d = 0; d < 3; ++d) {
+                double v[4];
+                for (int k = 0; k < 4; ++k) {
+                    double u[3] = {s->p.u_in[0], s->p.u_in[1], s->p.u_in[2]}, f[27], h[27];
+                    u[d] += off[k];
+                    for (int i = 0; i < 27; ++i) f[i] = frec[(size_t)i * N + n];
+                    for (int i = 0; i < qh; ++i) h[i] = hrec[(size_t)i * N + n];
+                    zou_he_local(&s->p, u, f, h);
+                    double dot = 0.0;
+                    for (int i = 0; i < 27; ++i) dot += f[i] * m[i];
+                    for (int i = 0; i < qh; ++i) dot += h[i] * m[27 + i];
+                    v[k] = dot;
+                }
+                duin[d] += cd4(v[0], v[1], v[2], v[3], e);
+            }
+        }
+        const int j0 = muf ? 0 : 27;
+        for (int j = j0; j < M; ++j) {
+            double acc = 0.0;
+            for (int i = (muf ? 0 : 27); i < M; ++i) acc += A[(size_t)i * M + j] * m[i];
+            out[j] = acc;
+        }
+        if (muf)
+            for (int i = 0; i < 27; ++i) muf[(size_t)i * N + n] = out[i];
+        for (int i = 0; i < qh; ++i) muh[(size_t)i * N + n] = out[27 + i];
+    }
+    free(A);
+}
+
 /* lam += P^T mu (transpose of the h part of orc_stream), dTw += (db/dT_w)^T mu.
  * mu is zero at solid and inlet nodes. */
 static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, double* dTw) {
@@ -1083,11 +1165,14 @@ static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, 
     const lattice_t* L = lattice(27);
     const lattice_t* Lh = lattice(qh);
     for (int n = 0; n < N; ++n) {
-        if (s->flags[n] == FL_SOLID) continue;
+        if (s->flags[n] == FL_SOLID && s->mirror[n] < 0) continue;
         for (int a = 0; a < qh; ++a) {
             int t = neighbour(s, n, Lh->e[a][0], Lh->e[a][1], Lh->e[a][2]);
-            if (t < 0 || s->flags[t] == FL_SOLID || s->flags[t] == FL_INLET) continue;
-            lam[(size_t)a * N + n] += mu[(size_t)a * N + t];
+            if (!receives(s, t)) continue;
+            /* a symmetry node pushes the mirrored node's population with e_y reversed */
+            int src = n, b = a;
+            if (s->mirror[n] >= 0) { src = s->mirror[n]; b = flip_y(Lh, a); }
+            lam[(size_t)b * N + src] += mu[(size_t)a * N + t];
         }
     }
     for (int n = 0; n < N; ++n) {
@@ -1115,7 +1200,9 @@ static void stream_transpose_h(const orc_sim* s, const double* mu, double* lam, 
             for (int a = 0; a < qh; ++a) {
                 if (Lh->e[a][0] >= 0) continue;
                 int src = neighbour(s, n, 0, -Lh->e[a][1], -Lh->e[a][2]);
-                lam[(size_t)a * N + src] += mu[(size_t)a * N + n];
+                int b = a;
+                if (s->mirror[src] >= 0) { b = flip_y(Lh, a); src = s->mirror[src]; } /* a symmetry node's copy */
+                lam[(size_t)b * N + src] += mu[(size_t)a * N + n];
             }
         }
     }
@@ -1223,10 +1310,13 @@ static double objective_value(orc_sim* s, int kind, int wall, int plane, int com
 /* Forward run from the post-collision state (f_post, h_post) = s^0 over
  * nsteps steps; returns J = weight * sum_{k=t0..t1} F(s^k).  With dtheta /
  * dTw non-NULL it also runs the reverse sweep and adds dJ/dtheta[N] and
- * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, -3 for a
- * geometry with symmetry rows or a Zou-He inlet (their transposes are not
- * built), or -4 for gradients of a force objective (kind 2; orc_adjoint_flow
- * carries the f part they need).
+ * dJ/dT_w[nwalls] to them.  Returns 0, -1 on a streaming error, or -4 for
+ * gradients of a force objective (kind 2; orc_adjoint_flow carries the f part
+ * they need).  Symmetry rows enter through the streaming transpose (a
+ * symmetry node pushes its mirrored node's populations with e_y reversed); a
+ * Zou-He inlet through zou_he_transpose (h block: f, hence rho, is fixed
+ * here) after each level's collision transposes, its nodes colliding like
+ * fluid nodes.
  * The Cumulants-1st collision is not affine in h: for that kind the forward
  * keeps the pre-collision h of every level and the reverse sweep applies the
  * transpose of the collision's Jacobian there (cum_jacobian); streaming and
@@ -1236,8 +1326,7 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
     const int N = s->N, qh = s->p.qh;
     const size_t HN = (size_t)qh * N;
     const int cum = s->p.hkind == KIND_CUM1;
-    /* the transposes of the symmetry rows and of the Zou-He inlet are not built */
-    if (dtheta && (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x))) return -3;
+    const int zou_he = s->p.inlet_bc && !s->p.periodic_x;
     /* a force objective depends on f: only the coupled adjoint carries it */
     if (dtheta && kind == 2) return -4;
     double* urec = dtheta ? (double*)malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double)) : NULL;
@@ -1265,7 +1354,7 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
         if (k == 0) break;
 #pragma omp parallel for schedule(dynamic, 16)
         for (int n = 0; n < N; ++n) {
-            if (s->flags[n] == FL_SOLID || s->flags[n] == FL_INLET) continue;
+            if (s->flags[n] == FL_SOLID || (s->flags[n] == FL_INLET && !zou_he)) continue;
             double u[3], Lm[27 * 27], col[27], unit[27], e[27], zero[27];
             for (int d = 0; d < 3; ++d) u[d] = urec[(size_t)k * 3 * N + (size_t)d * N + n];
             if (cum) {
@@ -1290,6 +1379,8 @@ int orc_adjoint(orc_sim* s, const double* f_post, const double* h_post, int nste
                 mu[(size_t)j * N + n] = v;
             }
         }
+        /* the Zou-He inlet built the inlet nodes' state of level k from their arrivals */
+        if (zou_he) zou_he_transpose(s, NULL, mu, NULL, NULL, NULL);
     }
     free(mu);
     free(lam);
@@ -1327,11 +1418,13 @@ static void stream_transpose_f(const orc_sim* s, const double* mu, double* lam) 
     const int N = s->N, nx = s->p.nx;
     const lattice_t* L = lattice(27);
     for (int n = 0; n < N; ++n) {
-        if (s->flags[n] == FL_SOLID) continue;
+        if (s->flags[n] == FL_SOLID && s->mirror[n] < 0) continue;
         for (int a = 0; a < 27; ++a) {
             int t = neighbour(s, n, L->e[a][0], L->e[a][1], L->e[a][2]);
-            if (t < 0 || s->flags[t] == FL_SOLID || s->flags[t] == FL_INLET) continue;
-            lam[(size_t)a * N + n] += mu[(size_t)a * N + t];
+            if (!receives(s, t)) continue;
+            int src = n, b = a;
+            if (s->mirror[n] >= 0) { src = s->mirror[n]; b = flip_y(L, a); }
+            lam[(size_t)b * N + src] += mu[(size_t)a * N + t];
         }
     }
     for (int n = 0; n < N; ++n) { /* Eq. IBB: the arrival ab at n from the link (n, a) */
@@ -1360,20 +1453,24 @@ static void stream_transpose_f(const orc_sim* s, const double* mu, double* lam) 
             for (int a = 0; a < 27; ++a) {
                 if (L->e[a][0] >= 0) continue;
                 int src = neighbour(s, n, 0, -L->e[a][1], -L->e[a][2]);
-                lam[(size_t)a * N + src] += mu[(size_t)a * N + n];
+                int b = a;
+                if (s->mirror[src] >= 0) { b = flip_y(L, a); src = s->mirror[src]; } /* a symmetry node's copy */
+                lam[(size_t)b * N + src] += mu[(size_t)a * N + n];
             }
         }
     }
 }
 
-/* Returns 0, -1 on a streaming error, -3 for a geometry with symmetry rows or
- * a Zou-He inlet.  dF[3] and duin[3] (and dtheta[N], dTw[nwalls]) are added to. */
+/* Returns 0 or -1 on a streaming error.  dF[3] and duin[3] (and dtheta[N],
+ * dTw[nwalls]) are added to.  Symmetry rows enter through the streaming
+ * transposes; a Zou-He inlet through zou_he_transpose after each level's
+ * collision transposes (its nodes collide like fluid nodes). */
 int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int nsteps, int t0, int t1, int kind,
                      int wall, int plane, int comp, double weight, double* J, double* dtheta, double* dTw,
                      double* dF, double* duin) {
     const int N = s->N, qh = s->p.qh;
     const size_t FN = (size_t)27 * N, HN = (size_t)qh * N;
-    if (s->has_mirror || (s->p.inlet_bc && !s->p.periodic_x)) return -3;
+    const int zou_he = s->p.inlet_bc && !s->p.periodic_x;
     double* frec = (double*)malloc((size_t)(nsteps + 1) * FN * sizeof(double));
     double* hrec = (double*)malloc((size_t)(nsteps + 1) * HN * sizeof(double));
     orc_set_post(s, f_post, h_post);
@@ -1422,8 +1519,8 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
         for (size_t i = 0; i < FN; ++i) muf[i] = 0.0;
         for (size_t i = 0; i < HN; ++i) muh[i] = 0.0;
         if (k == 0) break;
-        /* inlet nodes hold the equilibria at u_in */
-        if (!s->p.periodic_x && duin) {
+        /* equilibrium inlet: its nodes hold the equilibria at u_in */
+        if (!s->p.periodic_x && !zou_he && duin) {
             for (int n = 0; n < N; ++n) {
                 if (s->flags[n] != FL_INLET) continue;
                 for (int d = 0; d < 3; ++d) {
@@ -1436,7 +1533,7 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
         }
 #pragma omp parallel for schedule(dynamic, 8)
         for (int n = 0; n < N; ++n) {
-            if (s->flags[n] == FL_SOLID || s->flags[n] == FL_INLET) continue;
+            if (s->flags[n] == FL_SOLID || (s->flags[n] == FL_INLET && !zou_he)) continue;
             double g[27], gh[27], u[3], fs0[27], hs0[27];
             for (int a = 0; a < 27; ++a) g[a] = frec[(size_t)k * FN + (size_t)a * N + n];
             for (int a = 0; a < qh; ++a) gh[a] = hrec[(size_t)k * HN + (size_t)a * N + n];
@@ -1524,6 +1621,8 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
                 }
             }
         }
+        if (zou_he)
+            zou_he_transpose(s, muf, muh, frec + (size_t)k * FN, hrec + (size_t)k * HN, duin);
     }
     if (dF)
         for (int d = 0; d < 3; ++d) {

@@ -317,8 +317,7 @@ class Oracle:
                                int(window[1]), kind, wall, plane, comp, float(objective[2]), C.byref(J),
                                dth.ctypes.data if gradients else None, dTw.ctypes.data if gradients else None)
         if rc != 0:
-            raise OracleError("orc_adjoint: " + {-3: "no adjoint with symmetry rows or a Zou-He inlet",
-                                                 -4: "force objectives need adjoint_flow"}.get(rc, "streaming error"))
+            raise OracleError("orc_adjoint: " + {-4: "force objectives need adjoint_flow"}.get(rc, "streaming error"))
         return J.value, dth, dTw
 
     def adjoint_flow(self, f_post, h_post, nsteps, window, objective, nwalls=1):
@@ -338,6 +337,5 @@ class Oracle:
                                     int(window[1]), kind, wall, plane, comp, float(objective[2]), C.byref(J),
                                     dth.ctypes.data, dTw.ctypes.data, dF.ctypes.data, duin.ctypes.data)
         if rc != 0:
-            raise OracleError("orc_adjoint_flow: " + ("no adjoint with symmetry rows or a Zou-He inlet"
-                                                      if rc == -3 else "streaming error"))
+            raise OracleError("orc_adjoint_flow: streaming error")
         return J.value, dth, dTw, dF, duin
