@@ -1,5 +1,5 @@
-"""The multi-GPU path of bench.py runs independent replicas (the method has
-no exchange step on one grid in this build): every rank advances its own
+"""The multi-GPU path of bench.py runs independent replicas (one grid lives
+on one GPU, so no rank exchanges data with another): every rank advances its own
 grid, the job time is the slowest rank's, and the whole-job value counts the
 units of every rank.  Exercised here with two gloo ranks on the CPU."""
 import os
