@@ -15,7 +15,7 @@ import pytest
 from oracle import oracle as O
 from paper_2203_01316_gb300 import inputs as I
 
-from _cases import make_pair, rel_l2, small_channel
+from _cases import box_one_step, make_pair, rel_l2, small_channel
 
 pytestmark = pytest.mark.gpu
 
@@ -180,6 +180,27 @@ def test_full_size_heated_sphere_one_step():
     s, o = make_pair(w, nu=0.016, k=1.6e-5, storage="f32", wall_T=(1.0,))
     s.step(20)
     _one_step_parity(s, o, TOL1["f32"], 27)
+
+
+def test_bench_workload_full_size_sampled_boxes():
+    # the benchmark's workload (384 x 128 x 128 heated sphere, D = 32,
+    # Pr = 1000, FP32 storage, T_ref = 0.5) in the launch configuration the
+    # benchmark times, too large for the oracle to step whole: after 20
+    # steps, one GPU step of every node in two boxes (around the sphere and
+    # in its wake) against the oracle stepping those boxes (box_one_step)
+    w = I.heated_sphere(384, 128, 128, D=32.0, cx=96.0, seed=1234, u_in=0.02, T_in=0.0)
+    nu = 0.032
+    k = nu / 1000.0
+    s, _ = make_pair(w, nu=nu, k=k, storage="f32", wall_T=(1.0,), T_ref=0.5, oracle=False)
+    s.step(20)
+    f0, h0 = s.populations()
+    s.step(1)
+    f1, h1 = s.populations()
+    c = np.floor(w["centre"]).astype(int)
+    for box in ((c[0] - 20, c[0] + 21, c[1] - 20, c[1] + 21, c[2] - 20, c[2] + 21), (240, 262, 50, 78, 50, 78)):
+        idx, fo, ho = box_one_step(f0, h0, w, box, nu=nu, k=k, wall_T=(1.0,))
+        assert np.abs(f1[:, idx] - fo).max() < TOL1["f32"]
+        assert np.abs(h1[:, idx] - ho).max() < TOL1["f32"]
 
 
 def test_zero_steps_and_determinism():
