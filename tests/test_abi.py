@@ -62,3 +62,18 @@ def test_invalid_parameters_rejected_without_gpu(L, bad):
 def test_null_handles_are_rejected(L):
     assert L.lbm_step(None, 1) == lbm.LBM_ERR_INVALID
     assert L.lbm_destroy(None) == lbm.LBM_OK
+
+
+def test_every_entry_point_rejects_a_null_context_without_gpu(L):
+    # every call that takes a context returns LBM_ERR_INVALID for a null one
+    # (null pointers and zeros for the other arguments) before any CUDA call
+    scalars = (C.c_int, C.c_int64, C.c_double, C.c_size_t)
+    checked = 0
+    for name in lbm.SYMBOLS:
+        if name in ("lbm_create", "lbm_destroy", "lbm_last_error"):
+            continue
+        fn = getattr(L, name)
+        args = [0 if t in scalars else None for t in fn.argtypes]
+        assert fn(*args) == lbm.LBM_ERR_INVALID, name
+        checked += 1
+    assert checked == len(lbm.SYMBOLS) - 3
