@@ -570,7 +570,10 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
             rsegbase[sgm] = (int32_t)k;
         }
     }
-    // upload
+    // upload; until it completes the context has no geometry (a failure part
+    // way through must not leave tables that later kernels would read)
+    c->geometry = false;
+    c->initialised = false;
     free_geometry(c);
     c->nw = (int)wnode.size();
     c->nl = n_links;
