@@ -43,3 +43,21 @@ def test_recorded_traffic_matches_the_current_step_kernel():
     # profiles/traffic.json was taken on the current step-kernel source
     t = bench.recorded_traffic("k_step_f32_q27_384x128x128")
     assert t is not None and 2.6e9 < t < 2.8e9
+
+
+def test_clock_summary_parses_samples_and_reasons():
+    cs = bench.ClockSampler(0)
+    cs.lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2062, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2062.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.lines = ["0, 1500, 2070, 700.0, 0x8, Active, Not Active, Active, Not Active"]
+    assert bench.ClockSampler.summary(cs)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    cs.lines = []
+    assert bench.ClockSampler.summary(cs)["reasons"] == ["no samples"]
