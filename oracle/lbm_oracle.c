@@ -52,7 +52,15 @@
  *      D3Q27 list), moments {000,100,010,001,200,020,002}, cs^2 = 1/3.
  *   R8 surface heat flux of one wall: sum over its IABB links of
  *      h_abar(x_b, t+1) - h*_a(x_b, t).
- *   R15 first-order walls (Sec. 3): BB = Eq. IBB at q = 1/2, ABB = Eq. IABB
+ *   R15 symmetry planes (Sec. 4.4): specular reflection (e_y reversed) at the
+ *      plane halfway between a symmetry row and its neighbour row.
+ *   R19 Cumulants-1st with the App. D source: order 0 -> H + Q, order 1
+ *      relaxed to u with s^H, second-order diagonal cs^2, all else 0.
+ *   R20 Zou-He inlet (Sec. 4.4): non-equilibrium bounce-back for f at u_in,
+ *      the unknown h in the equilibrium shape with sum h = rho T_in.
+ *   R21 force on a wall (not in the paper): momentum exchange over the links
+ *      of Eq. IBB.
+ *   R23 first-order walls (Sec. 3): BB = Eq. IBB at q = 1/2, ABB = Eq. IABB
  *      at q = 1/2, EQ: the population arriving from the wall is the wall
  *      equilibrium w_i T_w.
  *
