@@ -18,8 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_noalloc.cu"] + [f"lbm_step_{s}_q{q}.cu" for s in ("f32", "f64", "f16", "bf16")
-                                              for q in (27, 7)]
+SOURCES = (["lbm_api.cu", "lbm_noalloc.cu"]
+           + [f"lbm_step_{s}_q{q}.cu" for s in ("f32", "f64", "f16", "bf16") for q in (27, 7)]
+           + [f"lbm_adjoint_{s}_q{q}.cu" for s in ("f32", "f64") for q in (27, 7)])
 HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v",

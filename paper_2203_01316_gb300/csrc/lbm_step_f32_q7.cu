@@ -20,9 +20,4 @@ template cudaError_t launch_surface_flux<float, 7>(const Buffers&, const DevPara
 template cudaError_t launch_wall_force<float, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                cudaStream_t);
 template cudaError_t launch_step_staged<float, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
-template cudaError_t launch_adjoint<float, 7>(const Buffers&, const DevParams&, const float*, const float*,
-                                           const float*, float*, AdjObjective, double*, cudaStream_t);
-template cudaError_t launch_adjoint_flow<float, 7>(const Buffers&, const DevParams&, const float*, const float*,
-                                                const float*, const float*, float*, float*, AdjObjective, double*,
-                                                double*, const float*, cudaStream_t);
 }  // namespace lbmd

@@ -19,9 +19,4 @@ template cudaError_t launch_surface_flux<double, 7>(const Buffers&, const DevPar
                                                  cudaStream_t);
 template cudaError_t launch_wall_force<double, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                cudaStream_t);
-template cudaError_t launch_adjoint<double, 7>(const Buffers&, const DevParams&, const double*, const double*,
-                                           const double*, double*, AdjObjective, double*, cudaStream_t);
-template cudaError_t launch_adjoint_flow<double, 7>(const Buffers&, const DevParams&, const double*, const double*,
-                                                const double*, const double*, double*, double*, AdjObjective, double*,
-                                                double*, const double*, cudaStream_t);
 }  // namespace lbmd
