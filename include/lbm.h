@@ -344,23 +344,32 @@ lbm_status lbm_get_links(lbm_ctx* ctx, int64_t* n_links, int32_t* node, int32_t*
  * inside a host framework that owns every device buffer and passes them in
  * (a plugin or custom-call interface with no allocator), or an application
  * whose device memory budget is fixed at start-up.
- * f: device float[27 * n_nodes], h: device float[q_h * n_nodes] (SoA, as the
- * library stores them with LBM_F32); values are taken as deviations from
- * w*rho0 and w*T_ref (pass rho0 = T_ref = 0 for plain populations).
- * flags: device uint8[n_nodes] (1 = solid, skipped) or NULL for all nodes.
- * totals: device double[3] written with (sum rho, sum H, number of nodes
- * holding a non-finite value).  Runs asynchronously on cuda_stream (NULL =
- * default stream) of the calling thread's current device; all pointers must
- * belong to that device.
+ * f: device float[27 * n_nodes], h: device float[q_h * n_nodes], each SoA
+ * [Q][n_nodes] (all values of velocity 0, then velocity 1, ...), holding a
+ * post-collision state as deviations from w*rho0 and w*T_ref (pass
+ * rho0 = T_ref = 0 for plain populations).
+ * flags: device uint8[n_nodes] with the flag values of lbm_set_geometry, or
+ * NULL for all nodes; solid (1) and symmetry-row (4) nodes are skipped, as
+ * lbm_balances skips them.  theta: device float[n_nodes], the App. D source
+ * of lbm_set_source, or NULL; each counted node's energy is then
+ * sum(h) - theta/2 (the energy lbm_balances and lbm_macros report).
+ * totals: device double[3] written with (sum rho, sum H, number of counted
+ * nodes holding a non-finite value).  Runs asynchronously on cuda_stream
+ * (NULL = default stream) of the calling thread's current device; all
+ * pointers must belong to that device.
  * Scratch lives in a fixed 64 KiB device array inside the library, so
- * n_nodes is limited to 33,554,432 (LBM_ERR_INVALID beyond).  The first call
- * on a device looks up that array's address: make it before any stream
- * capture.  Calls whose kernels overlap on the GPU share the array and race;
- * serialise them.  Errors: LBM_ERR_INVALID, LBM_ERR_CUDA, message in
- * lbm_last_error(NULL). */
+ * n_nodes is limited to 33,554,432 (LBM_ERR_INVALID beyond).  Each call whose
+ * stream is not being captured looks up that array's address in the current
+ * CUDA context; a call made during stream capture reuses the address the
+ * last uncaptured call on that device found (LBM_ERR_STATE if there was
+ * none), so make the first call on a device before any capture, and note
+ * that a context reset after that call invalidates the address a later
+ * capture would record.  Calls whose kernels overlap on the GPU share the
+ * array and race; serialise them.  Errors: LBM_ERR_INVALID, LBM_ERR_STATE,
+ * LBM_ERR_CUDA, message in lbm_last_error(NULL). */
 lbm_status lbm_balances_noalloc(const float* f, const float* h, int q_h, int64_t n_nodes,
-                                const uint8_t* flags, double rho0, double T_ref, double* totals,
-                                void* cuda_stream);
+                                const uint8_t* flags, const float* theta, double rho0, double T_ref,
+                                double* totals, void* cuda_stream);
 
 /* Wait for the context's stream; reports an asynchronous CUDA error. */
 lbm_status lbm_sync(lbm_ctx* ctx);

@@ -11,10 +11,15 @@
 // fixed size (kMaxBlocks x 4 doubles = 64 KiB).  Every GPU that loads this
 // library holds that array until the process exits.  Host code cannot use
 // the array's name as an address (on the host it names a stand-in, not
-// device memory), so the device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made with that device current.
-// Because that first call does the look-up, make it before any stream
-// capture.
+// device memory), so the device address is looked up with
+// cudaGetSymbolAddress with the caller's device current.  The address
+// belongs to the module instance of the current CUDA context, so it is
+// looked up again on every call whose stream is not capturing (a context
+// reset or another context on the same device can move the module); a call
+// made while its stream is being captured into a graph uses the address the
+// last uncaptured call on that device found, so the first call on a device
+// must come before any stream capture, and a context reset between that
+// call and a capture leaves a stale address in the graph.
 //
 // Every call shares the array.  Each call writes every partial slot it later
 // reads, so nothing has to be cleared between calls; but two calls whose
@@ -39,7 +44,10 @@ constexpr int kMaxBlocks = 2048;
 constexpr int64_t kMaxNodes = (int64_t)kMaxBlocks * kThreads * kNodesPerThread;  // 33,554,432
 constexpr int kMaxDevices = 64;
 
-// partial sums per block: (sum f, sum h, non-finite count, non-solid count)
+// public node flags that hold no state of their own (lbm_set_geometry)
+constexpr uint8_t kFlagSolid = 1, kFlagSymmetry = 4;
+
+// partial sums per block: (sum f, sum h, non-finite count, counted nodes)
 static __device__ __align__(256) double g_partials[kMaxBlocks * 4];
 
 std::mutex g_mutex;
@@ -66,14 +74,19 @@ __device__ __forceinline__ void warp_block_sum(double (&v)[4], double* sh) {
     }
 }
 
+// theta: the per-node App. D source Q or NULL.  The arrays hold the
+// post-collision state, which already carries the level's source, so a
+// node's energy is H = sum(h*) - Q/2 (App. D), the same correction as the
+// context's lbm_balances and lbm_macros
 __global__ void __launch_bounds__(kThreads) k_partials(const float* __restrict__ f, const float* __restrict__ h,
                                                        int qh, int n_nodes, const uint8_t* __restrict__ flags,
+                                                       const float* __restrict__ theta,
                                                        double* __restrict__ part) {
     __shared__ double sh[32 * 4];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const size_t N = (size_t)n_nodes;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
-        if (flags && flags[n] == 1) continue;  // solid
+        if (flags && (flags[n] == kFlagSolid || flags[n] == kFlagSymmetry)) continue;
         bool bad = false;
         for (int a = 0; a < 27; ++a) {
             const float x = f[a * N + n];
@@ -85,6 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_partials(const float* __restrict__
             bad |= !isfinite(x);
             v[1] += (double)x;
         }
+        if (theta) v[1] -= 0.5 * (double)theta[n];
         v[2] += bad ? 1.0 : 0.0;
         v[3] += 1.0;
     }
@@ -114,11 +128,31 @@ lbm_status fail(lbm_status s, const std::string& msg) {
     return s;
 }
 
+// device address of g_partials in the current context (see the file header)
+lbm_status scratch_address(int dev, cudaStream_t s, double** out) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("lbm_balances_noalloc: ") + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (cap == cudaStreamCaptureStatusNone) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_partials);
+        if (e != cudaSuccess)
+            return fail(LBM_ERR_CUDA, std::string("lbm_balances_noalloc: scratch address: ") + cudaGetErrorString(e));
+        g_addr[dev] = static_cast<double*>(p);
+    } else if (!g_addr[dev]) {
+        return fail(LBM_ERR_STATE,
+                    "lbm_balances_noalloc: the first call on a device must come before any stream capture");
+    }
+    *out = g_addr[dev];
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" lbm_status lbm_balances_noalloc(const float* f, const float* h, int q_h, int64_t n_nodes,
-                                           const uint8_t* flags, double rho0, double T_ref, double* totals,
-                                           void* cuda_stream) {
+                                           const uint8_t* flags, const float* theta, double rho0, double T_ref,
+                                           double* totals, void* cuda_stream) {
     if (!f || !h || !totals) return fail(LBM_ERR_INVALID, "lbm_balances_noalloc: null pointer");
     if (q_h != 27 && q_h != 7) return fail(LBM_ERR_INVALID, "lbm_balances_noalloc: q_h must be 27 or 7");
     if (n_nodes < 1) return fail(LBM_ERR_INVALID, "lbm_balances_noalloc: n_nodes must be >= 1");
@@ -130,23 +164,13 @@ extern "C" lbm_status lbm_balances_noalloc(const float* f, const float* h, int q
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("lbm_balances_noalloc: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_INVALID, "lbm_balances_noalloc: device index too large");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     double* part = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_partials);
-            if (e != cudaSuccess)
-                return fail(LBM_ERR_CUDA, std::string("lbm_balances_noalloc: scratch address: ") +
-                                              cudaGetErrorString(e));
-            g_addr[dev] = static_cast<double*>(p);
-        }
-        part = g_addr[dev];
-    }
+    const lbm_status st = scratch_address(dev, s, &part);
+    if (st != LBM_OK) return st;
     const int per_block = kThreads * kNodesPerThread;
     const int blocks = (int)((n_nodes + per_block - 1) / per_block);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    k_partials<<<blocks, kThreads, 0, s>>>(f, h, q_h, (int)n_nodes, flags, part);
+    k_partials<<<blocks, kThreads, 0, s>>>(f, h, q_h, (int)n_nodes, flags, theta, part);
     k_final<<<1, 1024, 0, s>>>(part, blocks, rho0, T_ref, totals);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("lbm_balances_noalloc: ") + cudaGetErrorString(e));

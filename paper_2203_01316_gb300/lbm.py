@@ -103,7 +103,7 @@ def lib():
         "lbm_get_links": [vp, C.POINTER(i64), vp, vp, vp, vp],
         "lbm_sync": [vp],
         "lbm_last_error": [vp],
-        "lbm_balances_noalloc": [vp, vp, i32, i64, vp, dbl, dbl, vp, vp],
+        "lbm_balances_noalloc": [vp, vp, i32, i64, vp, vp, dbl, dbl, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
