@@ -126,7 +126,7 @@ def kernel_source_hash(csrc=None):
     ker = open(os.path.join(csrc, "lbm_kernels.cuh")).read()
     parts = [dev,
              _between(ker, "constexpr int kBlock", "\n"),
-             _between(ker, "#ifdef LBM_KERNEL_TU", "// ---- staged step"),
+             _between(ker, "#ifdef LBM_KERNEL_TU", "template <typename S, int QH>\ncudaError_t launch_step("),
              _between(ker, "cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h) {",
                       "\n}\n")]
     h = hashlib.sha256()
@@ -161,7 +161,7 @@ def make_solver(w, storage, stream=None):
     nx, ny, nz = w["dims"]
     W = WORKLOAD
     s = Solver(nx, ny, nz, nu=W["nu"], Pr=W["Pr"], lat_h=27, hkind="trt", storage=storage, periodic_x=False,
-               rho0=1.0, T_ref=0.5, stream=stream)
+               rho0=1.0, T_ref=W["T_in"], stream=stream)
     s.set_geometry(w["flags"], w["links"], n_walls=1)
     s.set_bc(0, W["T_wall"])
     s.set_inlet(w["u_in"], w["T_in"])
@@ -240,6 +240,35 @@ def oracle_rate(budget_s, max_steps=None):
     sample = (f"heated-sphere channel scaled by {scale:.4g}: {nx}x{ny}x{nz} nodes, sphere D="
               f"{WORKLOAD['D'] * scale:.3g}, {steps} oracle steps (FP64, OpenMP)")
     return nx * ny * nz * steps / dt / 1e6, O.num_threads(), sample, steps, dt
+
+
+def oracle_single_thread_rate(budget_s):
+    """The oracle on one host thread (the 1/16-scale heated sphere, 24x8x8,
+    as many steps as fit the budget): MLUPS and the sample."""
+    from oracle import oracle as O
+    w = make_workload(scale=1 / 16)
+    nx, ny, nz = w["dims"]
+    W = WORKLOAD
+    threads = O.num_threads()
+    O.set_num_threads(1)
+    try:
+        p = O.make_params(nx=nx, ny=ny, nz=nz, qh=27, hkind="trt", periodic_x=False, nu=W["nu"],
+                          k=W["nu"] / W["Pr"], u_in=w["u_in"], T_in=w["T_in"])
+        o = O.Oracle(p)
+        o.set_geometry(w["flags"], w["links"], nwalls=1)
+        o.set_wall_temperature(0, W["T_wall"])
+        o.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+        t = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t
+        steps = max(1, int(budget_s / max(one, 1e-6)))
+        t = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t
+        o.close()
+    finally:
+        O.set_num_threads(threads)
+    return nx * ny * nz * steps / dt / 1e6, f"{nx}x{ny}x{nz} nodes, {steps} oracle steps (FP64, 1 thread)"
 
 
 def run_reference(args):
@@ -417,7 +446,7 @@ def precision_study(args):
     def run(storage, round_nearest=False):
         from paper_2203_01316_gb300 import Solver
         s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind="trt", storage=storage, periodic_x=False,
-                   rho0=1.0, T_ref=0.5, stream=stream.cuda_stream, round_nearest=round_nearest)
+                   rho0=1.0, T_ref=WORKLOAD["T_in"], stream=stream.cuda_stream, round_nearest=round_nearest)
         s.set_geometry(w["flags"], w["links"], n_walls=1)
         s.set_bc(0, WORKLOAD["T_wall"])
         s.set_inlet(w["u_in"], w["T_in"])
@@ -494,7 +523,7 @@ def porous_study(args):
            "wall_links": int(len(w["links"]["node"])), "geometry_build_s": t_geom}
     for storage in ("f32", "f16"):
         s = Solver(nx, ny, nz, nu=nu, Pr=Pr, lat_h=7, hkind="trt", storage=storage, periodic_x=False,
-                   T_ref=0.5, stream=stream.cuda_stream)
+                   T_ref=w["T_in"], stream=stream.cuda_stream)
         t0 = time.perf_counter()
         s.set_geometry(w["flags"], w["links"], n_walls=1)
         t_set = time.perf_counter() - t0
@@ -514,22 +543,92 @@ def porous_study(args):
             Tw = torch.tensor([1.0], dtype=torch.float64, requires_grad=True)
             obj = s.objective("section", nx - 2, 1.0)
             n = args.adjoint_steps
+            every = 50
+            torch.cuda.reset_peak_memory_stats()
             tf = time.perf_counter()
-            J = thermal_objective(theta, Tw, s, state0, n, (n - 99, n), obj, every=50)
+            J = thermal_objective(theta, Tw, s, state0, n, (n - 99, n), obj, every=every)
             torch.cuda.synchronize()
             tb = time.perf_counter()
             J.backward()
             torch.cuda.synchronize()
             te = time.perf_counter()
             free, total = torch.cuda.mem_get_info()
+            # memory of the checkpointed adjoint: one saved state per segment,
+            # the velocity records of one segment, the adjoint state (two h
+            # arrays) and the FP64 gradient, against the device's own count
+            ss = s.state_size()
+            plan = {"checkpoints_GB": -(-n // every) * ss / 1e9, "segment_velocity_records_GB": every * 3 * N * 4 / 1e9,
+                    "adjoint_state_GB": (2 * 7 * N * 4 + 8 * N) / 1e9,
+                    "solver_state_GB": 2 * 34 * N * BYTES_PER_VALUE[storage] / 1e9}
+            plan["planned_total_GB"] = sum(plan.values())
+            plan["torch_peak_allocated_GB"] = torch.cuda.max_memory_allocated() / 1e9
+            plan["device_used_GB_mem_get_info"] = (total - free) / 1e9
+            plan["device_total_GB"] = total / 1e9
             r["adjoint"] = {"steps": n, "checkpoint_every": 50, "spin_up_steps": args.spin,
                             "objective": "heat flux through x = nx-2, last 100 levels",
                             "forward_ms_per_step": (tb - tf) / n * 1e3, "backward_ms_per_step": (te - tb) / n * 1e3,
                             "ratio": (te - tb) / n * 1e3 / r["ms_per_step"], "J": float(J.item()),
-                            "grad_theta_norm": float(theta.grad.norm()), "device_mem_used_GB": (total - free) / 1e9,
+                            "grad_theta_norm": float(theta.grad.norm()), "memory": plan,
                             "note": "first (cold) adjoint call: includes allocation of checkpoint buffers"}
         out[storage] = r
         s.close()
+    print(json.dumps(out), flush=True)
+
+
+def sphere_nusselt_study(args):
+    """The heated sphere in a channel (192x64x64, D = 16 with a seeded
+    sub-node centre offset, plug inlet u = 0.02, T_in = 0, T_w = 1, Re = 20:
+    nu = 0.016), D3Q27 cumulant f + D3Q27 CM-TRT h with Eq. IBB / Eq. IABB,
+    for Pr = 10, 100, 1000 over `steps` steps (default 20k): the sphere's
+    Nusselt number Nu = q D / (k pi D^2 (T_w - T_in)) (the Sec. 4.4
+    definition with the sphere's area, reading R10), averaged over the last
+    10% of the steps on the device, in FP32 storage and, as a cross-check, in
+    FP64 storage."""
+    import torch
+    from paper_2203_01316_gb300 import Solver, build, inputs as I
+    build.build()
+    stream = torch.cuda.Stream()
+    D, U, Re = 16.0, 0.02, 20.0
+    nu = U * D / Re
+    w = I.heated_sphere(192, 64, 64, D=D, cx=48.0, seed=WORKLOAD["seed"], u_in=U, T_in=0.0)
+    nx, ny, nz = w["dims"]
+    steps = args.steps
+    win = max(1, steps // 10)
+    out = {"nusselt_study": f"heated sphere {nx}x{ny}x{nz}, D={D:g}, Re={Re:g}, nu={nu:g}, {steps} steps, "
+                            f"Nu averaged over the last {win} steps", "results": {}}
+    for Pr in [float(v) for v in (args.prs or "10,100,1000").split(",")]:
+        k = nu / Pr
+        r = {"k": k}
+        for storage in ("f32", "f64"):
+            s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind="trt", storage=storage, periodic_x=False,
+                       T_ref=w["T_in"], stream=stream.cuda_stream)
+            s.set_geometry(w["flags"], w["links"], n_walls=1)
+            s.set_bc(0, 1.0)
+            s.set_inlet(w["u_in"], w["T_in"])
+            s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+            J = torch.zeros(1, dtype=torch.float64, device="cuda")
+            obj = s.objective("surface", 0, D / (k * math.pi * D * D * 1.0) / win)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(steps - win)
+            half = torch.zeros(1, dtype=torch.float64, device="cuda")
+            for i in range(win):
+                s.objective_accumulate(obj, J)
+                if i == win // 2 - 1:
+                    with torch.cuda.stream(stream):  # ordered after the accumulation
+                        half.copy_(J)
+                s.step(1)
+            mass, energy = s.balances()
+            dt = time.perf_counter() - t0
+            Nu = float(J.item())
+            # drift check: the mean over the window's second half against its first half
+            first, second = 2.0 * float(half.item()), 2.0 * (Nu - float(half.item()))
+            r[storage] = {"Nu": Nu, "Nu_first_half_of_window": first, "Nu_second_half_of_window": second,
+                          "wall_s": dt, "MLUPS": nx * ny * nz * steps / dt / 1e6, "mass": mass}
+            s.close()
+        r["Nu_f32_vs_f64"] = abs(r["f32"]["Nu"] - r["f64"]["Nu"]) / abs(r["f64"]["Nu"])
+        out["results"][f"Pr={Pr:g}"] = r
+        print(json.dumps({f"Pr={Pr:g}": r}), flush=True)
     print(json.dumps(out), flush=True)
 
 
@@ -800,7 +899,9 @@ def run_ours(args):
         from oracle import oracle as O
         O.build()
         v, cores, sample, steps, odt = oracle_rate(budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+        v1, sample1 = oracle_single_thread_rate(budget_s=min(5.0, args.cpu_budget / 3))
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample,
+                                "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "sample": sample1}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -830,6 +931,8 @@ def main():
     ap.add_argument("--validation", choices=["cylinders", "hill", "confined"],
                     help="run one of the paper's validation workloads on the GPU path")
     ap.add_argument("--sizes", default="", help="validation: comma-separated D (cylinders) or k (hill)")
+    ap.add_argument("--nusselt-study", action="store_true",
+                    help="heated sphere 192x64x64 at Pr 10, 100, 1000 (--prs): mean Nu after --steps steps")
     ap.add_argument("--workload", choices=["sphere", "porous"], default="sphere",
                     help="porous: the 512x256x256 porous bed (see porous_study)")
     ap.add_argument("--spin", type=int, default=2000, help="porous: forward steps before the adjoint")
@@ -852,6 +955,8 @@ def main():
         validation_confined(args)
     elif args.precision:
         precision_study(args)
+    elif args.nusselt_study:
+        sphere_nusselt_study(args)
     elif args.workload == "porous":
         porous_study(args)
     elif args.impl == "reference":

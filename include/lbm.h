@@ -101,14 +101,11 @@ typedef enum { LBM_INLET_EQUILIBRIUM = 0, LBM_INLET_ZOU_HE = 1 } lbm_inlet_bc;
  * at q = 1/2). */
 typedef enum { LBM_WALL_IBB_IABB = 0, LBM_WALL_BB_EQ = 1, LBM_WALL_BB_ABB = 2 } lbm_wall_bc;
 
-/* LBM_STEP_AUTO and LBM_STEP_CLASSIC run the classic kernel, which loads
- * each population directly (the faster one on GB300: the step is close to
- * the SM issue limit, and the classic kernel keeps 20 warps per SM).
- * LBM_STEP_STAGED (FP32/FP16/BF16 storage, nx a multiple of 32;
- * LBM_ERR_INVALID otherwise) copies the rows of the pull into shared memory
- * with asynchronous bulk copies three tiles ahead; it computes bit-identical
- * results. */
-typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1, LBM_STEP_STAGED = 2 } lbm_step_kernel;
+/* Implementation of lbm_step.  Both values run the one-node-per-thread
+ * kernel (the fastest measured on GB300: the step sits near the SM issue
+ * limit and gains from the warps its 96-register cap keeps resident); the
+ * field is kept for choosing among implementations. */
+typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1 } lbm_step_kernel;
 
 /* Create a context and allocate its device state.  The populations are zero
  * until lbm_init_fields.  Errors: LBM_ERR_INVALID (parameters), NOMEM, CUDA. */
@@ -134,8 +131,8 @@ lbm_status lbm_destroy(lbm_ctx* ctx);
  * fluid->solid link is listed exactly once; symmetry rows are whole, their
  * neighbour rows hold no solid node and no wall link.  Links may come in any
  * order.  Replaces any earlier geometry; the populations must be
- * (re)initialised afterwards.  The adjoint entry points refuse geometries
- * with symmetry rows and contexts with the Zou-He inlet. */
+ * (re)initialised afterwards.  The coupled adjoint (lbm_adjoint_flow_step)
+ * refuses contexts with the Zou-He inlet. */
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, int64_t n_links,
                             const int32_t* link_node, const int32_t* link_dir,
                             const float* link_q, const int32_t* link_wall, int n_walls,
@@ -267,9 +264,13 @@ lbm_status lbm_step_record_h(lbm_ctx* ctx, int n, void* u_rec, void* h_rec);
  * e(u^k)^T lambda^k to dJ_dtheta[N] (device double, may be NULL); with
  * u_level NULL (the initial level) it writes lambda^0 to out.  The dJ/dT_w
  * terms are accumulated inside the context (lbm_adjoint_wall_gradient).
- * mu_next must be zero at solid and inlet nodes (true of zero-filled arrays
- * and of every out this call writes); mu_next and out must not alias.
- * Asynchronous. */
+ * mu_next must be zero at solid nodes and, with the equilibrium inlet, at
+ * inlet nodes (true of zero-filled arrays and of every out this call
+ * writes); mu_next and out must not alias.  Symmetry rows and the Zou-He
+ * inlet are covered: a symmetry row passes the adjoint back to the row
+ * beside it with e_y reversed, and a Zou-He inlet node collides like a fluid
+ * node whose unknown h arrivals (e_x = +1) depend on its known ones through
+ * the rule sum h = rho T_in, rho held fixed.  Asynchronous. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* u_level, const void* mu_next, void* out,
                             const lbm_objective* obj, double* dJ_dtheta);
 /* (A WALL_FORCE objective depends on f: lbm_adjoint_step and
@@ -294,7 +295,8 @@ lbm_status lbm_adjoint_step_h(lbm_ctx* ctx, const void* u_level, const void* h_l
  * through u, so this sweep carries the adjoint of f as well (Eq.
  * hydro_cu_collision, Eq. IBB) next to that of h (Eq. H_cm_collision or
  * H_cu_collision, Eq. IABB).  FP32 or FP64 storage only (LBM_ERR_INVALID
- * otherwise); not with symmetry rows or the Zou-He inlet.  Adjoint arrays:
+ * otherwise); symmetry rows are covered as in lbm_adjoint_step, the Zou-He
+ * inlet is not (LBM_ERR_INVALID).  Adjoint arrays:
  * element type float (FP32) or double (FP64), SoA [27][N] for f and [Q_h][N]
  * for h. */
 

@@ -1018,6 +1018,14 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+/* threads of the OpenMP loops from now on (timing: single- and multi-thread) */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 /* ---- adjoint of the h evolution (Sec. 2.1 evolution equation, Eq. H_cm_collision,
  * Eq. IABB) ----------------------------------------------------------------

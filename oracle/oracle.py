@@ -107,6 +107,8 @@ def lib():
         L.orc_collide_f.argtypes = [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_collide_h.argtypes = [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_adjoint.restype = C.c_int
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
@@ -181,6 +183,11 @@ def collide_h(params: Params, h, u, Q=0.0):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads used by the oracle's OpenMP loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 # ---- simulation ----------------------------------------------------------

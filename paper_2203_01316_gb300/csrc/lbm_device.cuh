@@ -79,47 +79,15 @@ template <typename R> __device__ __forceinline__ R ld(const double* p) { return 
 template <typename R> __device__ __forceinline__ R ld(const __half* p) { return (R)__half2float(__ldg(p)); }
 template <typename R> __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return (R)__bfloat162float(__ldg(p)); }
 
-// a stored value as arithmetic type (shared-memory reads of staged rows)
-__device__ __forceinline__ float to_acc(float v) { return v; }
-__device__ __forceinline__ double to_acc(double v) { return v; }
-__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
-__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
-
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-// Stochastic rounding of the 16-bit stores: the value is rounded up in
-// magnitude with probability equal to the discarded fraction, so rounding
-// errors have zero mean and do not accumulate into a drift over many steps.
-// Implemented by adding a uniform random integer below the last kept bit to
-// the FP32 bit pattern and truncating (FP32 -> FP16 drops 13 mantissa bits,
-// -> BF16 drops 16).  FP16 subnormals, overflow and non-finite values use
-// round-to-nearest.
-// r: 32 random bits; the top bits supply the random fraction
-__device__ __forceinline__ void st_sr(float* p, float v, uint32_t) { *p = v; }
-__device__ __forceinline__ void st_sr(double* p, double v, uint32_t) { *p = v; }
-__device__ __forceinline__ void st_sr(__half* p, float v, uint32_t r) {
-    const float a = fabsf(v);
-    if (!(a >= 6.103515625e-05f && a < 65504.0f)) {
-        *p = __float2half_rn(v);
-        return;
-    }
-    *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
-}
-__device__ __forceinline__ void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
-    if (!isfinite(v)) {
-        *p = __float2bfloat16_rn(v);
-        return;
-    }
-    *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r >> 16)));
-}
-
-// Random bits of the stores of one node: a strong hash of (node, array,
-// time level) seeds a linear congruential sequence (Numerical Recipes
-// constants) that advances once per store; st_sr uses only its top bits,
-// which are well distributed.  Reproducible, and one multiply-add per store.
+// Random bits of the stochastic rounding of one node's 16-bit stores: a
+// strong hash of (node, array, time level) seeds a linear congruential
+// sequence (Numerical Recipes constants) that advances once per pair of
+// stores.  Reproducible, and one multiply-add per draw.
 struct SrStream {
     uint32_t s;
     __device__ __forceinline__ uint32_t next() {
@@ -141,7 +109,10 @@ __device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t step) {
 }
 
 // ---- moment algebra --------------------------------------------------------
-template <typename R> __device__ __forceinline__ constexpr R cs2() { return R(1) / R(3); }
+// lattice constants are formed in double and converted once, so that they
+// stay compile-time constants for every arithmetic type (1/3 rounds to the
+// same float either way)
+template <typename R> __device__ __forceinline__ constexpr R cs2() { return R(1.0 / 3.0); }
 
 // forward-mode dual number v + d eps: runs the collision functions (templated
 // on the arithmetic type) to give directional derivatives for the coupled
@@ -170,18 +141,24 @@ template <typename T> struct Dual {
     __host__ __device__ constexpr Dual& operator/=(const Dual& b) { return *this = *this / b; }
 };
 
+// scalar type underlying an arithmetic type (constants are formed in it)
+template <typename T> struct ScalarOf { using type = T; };
+template <typename T> struct ScalarOf<Dual<T>> { using type = T; };
+
 // slot of moment mno in the cube after the forward passes
 __host__ __device__ __forceinline__ constexpr int MIDX(int m, int n, int o) { return o * 9 + n * 3 + m; }
 
 // equilibrium central moments for psi = 1 (Sec. 2.1.1): 1 at 000, cs^2 per
-// index 2, zero when any index is 1
+// index 2, zero when any index is 1; formed in the scalar type underlying R
+// (float or double) so that it stays a constant for every arithmetic type
 template <typename R> __device__ __forceinline__ R Eq(int m, int n, int o) {
+    using T = typename ScalarOf<R>::type;
     if (m == 1 || n == 1 || o == 1) return R(0);
-    R v = R(1);
-    if (m == 2) v *= cs2<R>();
-    if (n == 2) v *= cs2<R>();
-    if (o == 2) v *= cs2<R>();
-    return v;
+    T v = T(1);
+    if (m == 2) v *= cs2<T>();
+    if (n == 2) v *= cs2<T>();
+    if (o == 2) v *= cs2<T>();
+    return R(v);
 }
 
 template <typename R> __device__ __forceinline__ R Kd(int m, R v) {
@@ -260,7 +237,7 @@ struct DevParams {
     int wall_bc;         // 0 Eq. IBB + Eq. IABB, 1 BB + EQ, 2 BB + ABB (BB/ABB: q = 1/2 on the device)
     int mirror_lo, mirror_hi;  // rows y = 0 / y = ny-1 are symmetry rows
     int zou_he;                // inlet plane: 0 fixed equilibria, 1 Zou-He (k_inlet after the step)
-    uint32_t step;       // time level being written (random stream of st_sr)
+    uint32_t step;       // time level being written (seeds the stochastic rounding)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6
     double rho0, Tref;
@@ -373,7 +350,11 @@ __device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& u
 // Y* = Y + s (H E - Y) + (1 - s/2) Q E per moment, s = p.sh[order]; with
 // Y = dY + Tref K:  dY* = (1-s) dY + s (dH E + Tref D) + (1 - s/2) Q E,
 // dH = H - Tref, H = sum(h) + Q/2.
-template <typename R>
+// TRT (compile time): the CM-TRT kind, whose even orders relax with rate 1,
+// so they go straight to equilibrium plus half the source and their
+// pre-collision values are never needed (the odd orders, whose equilibrium
+// part E vanishes, keep s^H)
+template <typename R, bool TRT = false>
 __device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
     R cb[27];
 #pragma unroll
@@ -388,11 +369,20 @@ __device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const 
         for (int n = 0; n < 3; ++n)
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const R s = (R)p.sh[m + n + o];
                 const R E = Eq<R>(m, n, o);
                 const R D = Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
                 R& y = cb[MIDX(m, n, o)];
-                y = (R(1) - s) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
+                if constexpr (TRT) {
+                    if ((m + n + o) % 2 == 0) {
+                        y = dH * E + Tref * D + R(0.5) * Q * E;
+                    } else {
+                        const R s = (R)p.sh[1];
+                        y = (R(1) - s) * y + s * (Tref * D);
+                    }
+                } else {
+                    const R s = (R)p.sh[m + n + o];
+                    y = (R(1) - s) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
+                }
             }
     inverse_cube<R>(cb, ux, uy, uz);
 #pragma unroll
@@ -400,26 +390,35 @@ __device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const 
 }
 
 // D3Q7 (pops 0, +x, +y, +z, -x, -y, -z; moments 000, 100, 010, 001, 200, 020, 002)
-template <typename R>
+template <typename R, bool TRT = false>
 __device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
     const R u[3] = {ux, uy, uz};
     const R m0 = hd[0] + hd[1] + hd[2] + hd[3] + hd[4] + hd[5] + hd[6];
     const R Tref = (R)p.Tref;
     const R dH = m0 + R(0.5) * Q;
     const R c = cs2<R>();
-    const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
-    // order 0
-    const R y0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
-    R y1[3], y2[3];
+    const R s1 = (R)p.sh[1];
+    R y0, y1[3], y2[3];
+    if constexpr (TRT) {  // orders 0 and 2 relax with rate 1
+        y0 = dH + R(0.5) * Q;
+    } else {
+        const R s0 = (R)p.sh[0];
+        y0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const R m1 = hd[1 + d] - hd[4 + d];
-        const R m2 = hd[1 + d] + hd[4 + d];
         const R k1 = m1 - u[d] * m0;
-        const R k2 = m2 - u[d] * (m1 + k1);
         // D_1 = u, D_2 = -u^2; E_1 = 0, E_2 = cs^2
         y1[d] = (R(1) - s1) * k1 + s1 * (Tref * u[d]);
-        y2[d] = (R(1) - s2) * k2 + s2 * (dH * c - Tref * u[d] * u[d]) + (R(1) - R(0.5) * s2) * Q * c;
+        if constexpr (TRT) {
+            y2[d] = dH * c - Tref * u[d] * u[d] + R(0.5) * Q * c;
+        } else {
+            const R s2 = (R)p.sh[2];
+            const R m2 = hd[1 + d] + hd[4 + d];
+            const R k2 = m2 - u[d] * (m1 + k1);
+            y2[d] = (R(1) - s2) * k2 + s2 * (dH * c - Tref * u[d] * u[d]) + (R(1) - R(0.5) * s2) * Q * c;
+        }
     }
     R rest = y0;
 #pragma unroll
@@ -466,14 +465,14 @@ __device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, cons
 
 // CUM: the Cumulants-1st kind (compile time, so the central-moment kinds
 // keep their register allocation)
-template <typename R, int QH, bool CUM = false>
+template <typename R, int QH, bool CUM = false, bool TRT = false>
 __device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
     if constexpr (CUM) {
         collide_h_cum<R, QH>(hd, ux, uy, uz, Q, p);
     } else if constexpr (QH == 27) {
-        collide_h27<R>(hd, ux, uy, uz, Q, p);
+        collide_h27<R, TRT>(hd, ux, uy, uz, Q, p);
     } else {
-        collide_h7<R>(hd, ux, uy, uz, Q, p);
+        collide_h7<R, TRT>(hd, ux, uy, uz, Q, p);
     }
 }
 

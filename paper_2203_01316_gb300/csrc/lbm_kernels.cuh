@@ -50,22 +50,6 @@ constexpr int kBlock = 128;
 constexpr int kRedBlocks = 1216;  // 8 x 152 SMs, partial sums of the reductions
 constexpr int kRedThreads = 256;
 
-// Staged variant of the step (FP32 / FP16 / BF16 storage, nx % 32 == 0, the
-// population arrays carrying kGuard elements of slack on both sides): rows
-// of the pull are copied into shared memory by asynchronous bulk copies.
-constexpr int kTile = 128;     // nodes (= threads) per tile, one x-row segment
-constexpr int kStages = 3;     // tiles in flight per CTA
-constexpr int kGuard = 256;    // elements of slack around each population array
-template <typename S> constexpr int stage_pad() { return 16 / (int)sizeof(S); }
-template <typename S, int QH> constexpr int stage_bytes() {
-    return (27 + QH) * (kTile + 2 * stage_pad<S>()) * (int)sizeof(S);
-}
-template <typename S, int QH>
-cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s);
-template <typename S, int QH> bool staged_eligible(const DevParams& p) {
-    return sizeof(S) <= 4 && p.nx % 32 == 0;
-}
-
 // advance_h = false advances f only (velocity recomputation for the adjoint);
 // b.urec non-null records the velocity u used by each node's collision
 template <typename S, int QH>
@@ -160,6 +144,45 @@ __device__ __forceinline__ int src_of(const Nbr& b, int a) {
 }
 
 // ---- collision + store shared by the bulk and the wall kernels ----------------
+// ---- 16-bit stores ------------------------------------------------------------
+// Two values of one node (populations a and a + 1) are converted with one
+// packed conversion and stored as two 16-bit halves.  Stochastic rounding
+// uses the conversion's own random-bits operand (FP16: bits 0-12 round the
+// low value, bits 16-28 the high one; BF16: bits 0-15 and 16-31): the value
+// rounds up in magnitude with probability equal to the discarded fraction,
+// so rounding errors have zero mean.  The 32 bits come from the node's
+// stream, its high half folded onto the low half (the low bits of a linear
+// congruential sequence are weak).
+__device__ __forceinline__ uint32_t sr_pair_bits(SrStream& rs) {
+    const uint32_t r = rs.next();
+    return r ^ (r >> 16);
+}
+template <bool SR> __device__ __forceinline__ uint32_t cvt_pair(__half*, float hi, float lo, uint32_t r) {
+    uint32_t d;
+    if constexpr (SR) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+template <bool SR> __device__ __forceinline__ uint32_t cvt_pair(__nv_bfloat16*, float hi, float lo, uint32_t r) {
+    uint32_t d;
+    if constexpr (SR) asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// v[0..Q) of node n into X[i * N + n] (16-bit storage)
+template <bool SR, typename S, int Q>
+__device__ __forceinline__ void store16(S* __restrict__ X, const float* v, int n, int N, uint32_t key,
+                                        uint32_t step) {
+    SrStream rs{sr_bits(key, step)};
+#pragma unroll
+    for (int i = 0; i < Q; i += 2) {
+        const float hi = (i + 1 < Q) ? v[i + 1] : 0.0f;
+        const uint32_t d = cvt_pair<SR>(X, hi, v[i], SR ? sr_pair_bits(rs) : 0u);
+        *(unsigned short*)(X + i * N + n) = (unsigned short)(d & 0xffffu);
+        if (i + 1 < Q) *(unsigned short*)(X + (i + 1) * N + n) = (unsigned short)(d >> 16);
+    }
+}
+
 template <typename S, int QH>
 __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __restrict__ fB, int n,
                                                 const DevParams& p, typename Acc<S>::R& ux,
@@ -167,17 +190,16 @@ __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __res
     using R = typename Acc<S>::R;
     R rho;
     collide_f<R>(fd, p, ux, uy, uz, rho);
-    if (sizeof(S) == 2 && p.stochastic) {
-        SrStream rs{sr_bits((uint32_t)n << 1, p.step)};
-#pragma unroll
-        for (int a = 0; a < 27; ++a) st_sr(fB + a * p.N + n, fd[a], rs.next());
+    if constexpr (sizeof(S) == 2) {
+        if (p.stochastic) store16<true, S, 27>(fB, fd, n, p.N, (uint32_t)n << 1, p.step);
+        else store16<false, S, 27>(fB, fd, n, p.N, 0u, 0u);
     } else {
 #pragma unroll
         for (int a = 0; a < 27; ++a) st(fB + a * p.N + n, fd[a]);
     }
 }
 
-template <typename S, int QH, bool CUM = false>
+template <typename S, int QH, bool CUM = false, bool TRT = false>
 __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __restrict__ hB, int n,
                                                 const DevParams& p, typename Acc<S>::R ux,
                                                 typename Acc<S>::R uy, typename Acc<S>::R uz,
@@ -191,18 +213,17 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
         R pre = R(0);
 #pragma unroll
         for (int i = 0; i < QH; ++i) pre += hd[i];
-        collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
+        collide_h<R, QH, CUM, TRT>(hd, ux, uy, uz, Q, p);
         R others = R(0);
 #pragma unroll
         for (int i = 1; i < QH; ++i) others += hd[i];
         hd[0] = (pre + Q) - others;
     } else {
-        collide_h<R, QH, CUM>(hd, ux, uy, uz, Q, p);
+        collide_h<R, QH, CUM, TRT>(hd, ux, uy, uz, Q, p);
     }
-    if (sizeof(S) == 2 && p.stochastic) {
-        SrStream rs{sr_bits(((uint32_t)n << 1) | 1u, p.step)};
-#pragma unroll
-        for (int i = 0; i < QH; ++i) st_sr(hB + i * p.N + n, hd[i], rs.next());
+    if constexpr (sizeof(S) == 2) {
+        if (p.stochastic) store16<true, S, QH>(hB, hd, n, p.N, ((uint32_t)n << 1) | 1u, p.step);
+        else store16<false, S, QH>(hB, hd, n, p.N, 0u, 0u);
     } else {
 #pragma unroll
         for (int i = 0; i < QH; ++i) st(hB + i * p.N + n, hd[i]);
@@ -238,8 +259,10 @@ template <typename S, int QH> constexpr int step_min_blocks() {
 }
 
 // EQ: the BB + EQ wall rule (compile time, so the default rules keep their
-// register allocation); CUM: the Cumulants-1st h kind
-template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false, bool PRE = false>
+// register allocation); CUM: the Cumulants-1st h kind; TRT: the CM-TRT kind
+// with its rates fixed at compile time
+template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false, bool PRE = false,
+          bool TRT = false>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const S* __restrict__ fA, S* __restrict__ fB,
                                                   const S* __restrict__ hA, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags,
@@ -356,248 +379,8 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
 #pragma unroll
         for (int i = 0; i < QH; ++i) ((R*)hrec)[i * N + n] = hd[i];
     }
-    collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
+    collide_store_h<S, QH, CUM, TRT>(hd, hB, n, p, ux, uy, uz, Q);
     }
-}
-
-// ---- staged step ------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// bounded wait for the phase of parity `parity` to complete; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// issue the bulk copies of tile `tile` into stage buffer `buf` (thread 0 only)
-template <typename S, int QH>
-__device__ __forceinline__ void stage_issue(const S* __restrict__ fA, const S* __restrict__ hA, int tile,
-                                            int tiles_per_row, S* buf, uint32_t bar, const DevParams& p) {
-    constexpr int PAD = stage_pad<S>();
-    constexpr int ROW = kTile + 2 * PAD;
-    const int row = tile / tiles_per_row;
-    const int x0 = (tile - row * tiles_per_row) * kTile;
-    const int y = row % p.ny, z = row / p.ny;
-    mbar_expect_tx(bar, (uint32_t)stage_bytes<S, QH>());
-    const int ym = (y == 0) ? p.ny - 1 : y - 1, yp = (y == p.ny - 1) ? 0 : y + 1;
-    const int zm = (z == 0) ? p.nz - 1 : z - 1, zp = (z == p.nz - 1) ? 0 : z + 1;
-    const int ys[3] = {yp, y, ym}, zs[3] = {zp, z, zm};  // source row of e = -1, 0, +1
-#pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        const S* src = fA + (size_t)a * p.N + ((size_t)zs[EZ(a) + 1] * p.ny + ys[EY(a) + 1]) * p.nx + x0 - PAD;
-        bulk_g2s(smem_addr(buf + a * ROW), src, ROW * sizeof(S), bar);
-    }
-#pragma unroll
-    for (int i = 0; i < QH; ++i) {
-        const int a = HDIR<QH>(i);
-        const S* src = hA + (size_t)i * p.N + ((size_t)zs[EZ(a) + 1] * p.ny + ys[EY(a) + 1]) * p.nx + x0 - PAD;
-        bulk_g2s(smem_addr(buf + (27 + i) * ROW), src, ROW * sizeof(S), bar);
-    }
-}
-
-template <typename S, int QH, bool CUM = false>
-__global__ void __launch_bounds__(kTile) k_step_staged(const S* __restrict__ fA, S* __restrict__ fB,
-                                                        const S* __restrict__ hA, S* __restrict__ hB,
-                                                        const uint8_t* __restrict__ flags,
-                                                        const float* __restrict__ theta,
-                                                        const typename Acc<S>::R* __restrict__ inlet,
-                                                        const int32_t* __restrict__ seg_base,
-                                                        const uint32_t* __restrict__ wmask,
-                                                        const int32_t* __restrict__ woff,
-                                                        const float* __restrict__ lq,
-                                                        const int32_t* __restrict__ lwall,
-                                                        const float* __restrict__ Twall, int* __restrict__ err,
-                                                        const DevParams p) {
-    using R = typename Acc<S>::R;
-    constexpr int PAD = stage_pad<S>();
-    constexpr int ROW = kTile + 2 * PAD;
-    constexpr int SELEMS = (27 + QH) * ROW;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    S* stage = reinterpret_cast<S*>(smem_raw);
-    __shared__ __align__(8) uint64_t bars[kStages];
-    const int N = p.N;
-    const int tiles_per_row = (p.nx + kTile - 1) / kTile;
-    const int ntiles = tiles_per_row * p.ny * p.nz;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // prologue: tiles of the first kStages-1 iterations
-    if (tid == 0) {
-        for (int s = 0; s < kStages - 1; ++s) {
-            const int t = blockIdx.x + s * gridDim.x;
-            if (t < ntiles) stage_issue<S, QH>(fA, hA, t, tiles_per_row, stage + s * SELEMS, smem_addr(&bars[s]), p);
-        }
-    }
-    for (int it = 0;; ++it) {
-        const int tile = blockIdx.x + it * gridDim.x;
-        if (tile >= ntiles) break;
-        const int sidx = it % kStages;
-        if (tid == 0) {
-            const int nxt = tile + (kStages - 1) * gridDim.x;
-            const int ns = (it + kStages - 1) % kStages;
-            if (nxt < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                stage_issue<S, QH>(fA, hA, nxt, tiles_per_row, stage + ns * SELEMS, smem_addr(&bars[ns]), p);
-            }
-        }
-        const bool ok = mbar_wait(smem_addr(&bars[sidx]), (uint32_t)((it / kStages) & 1));
-        if (__syncthreads_or(!ok)) {
-            // record the failure, give the copies of this stage one more
-            // bounded wait, and leave together
-            if (tid == 0) {
-                atomicExch(err, 1);
-                mbar_wait(smem_addr(&bars[sidx]), (uint32_t)((it / kStages) & 1));
-            }
-            return;
-        }
-        const S* buf = stage + sidx * SELEMS;
-        const int row = tile / tiles_per_row;
-        const int x0 = (tile - row * tiles_per_row) * kTile;
-        const int x = x0 + tid;
-        const bool in_row = x < p.nx;
-        const int y = row % p.ny, z = row / p.ny;
-        const int n = row * p.nx + x;
-        const uint8_t fl = in_row ? flags[n] : (uint8_t)T_SOLID;
-        const bool is_wall = (fl & F_WALL) != 0;
-        const uint32_t ballot = __ballot_sync(0xffffffffu, is_wall);
-        const int type = fl & 3;
-        if (type == T_INLET) {
-#pragma unroll
-            for (int a = 0; a < 27; ++a) st(fB + a * N + n, inlet[a]);
-#pragma unroll
-            for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
-        } else if (type != T_SOLID) {
-            uint32_t mask = 0;
-            int off = 0;
-            if (is_wall) {
-                const int lane = tid & 31;
-                const int idx = __ldg(seg_base + (n >> 5)) + __popc(ballot & ((1u << lane) - 1u));
-                mask = __ldg(wmask + idx);
-                off = __ldg(woff + idx);
-            }
-            const Nbr nb = make_nbr(x, y, z, p);
-            // the lanes at the ends of a row take the wrapped / clamped source
-            // from global memory; everyone else reads the staged row
-            const bool lfix = (x == 0), rfix = (x == p.nx - 1);
-            R fd[27];
-#pragma unroll
-            for (int a = 0; a < 27; ++a) {
-                if ((EX(a) == 1 && lfix) || (EX(a) == -1 && rfix)) fd[a] = ld<R>(fA + a * N + src_of(nb, a));
-                else fd[a] = (R)to_acc(buf[a * ROW + PAD + tid - EX(a)]);
-            }
-            if (mask) {
-#pragma unroll
-                for (int b = 0; b < 27; ++b) {
-                    const int a = OPP(b);
-                    if (!(mask & (1u << a))) continue;
-                    const float q = __ldg(lq + off + __popc(mask & ((1u << a) - 1u)));
-                    const bool thin = (mask >> b) & 1u;
-                    const R fa_b = ld<R>(fA + a * N + n);
-                    if (q <= 0.5f && !thin) {
-                        fd[b] = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];
-                    } else {
-                        const R qq = (R)fmaxf(q, 0.5f);
-                        const R fb_b = ld<R>(fA + b * N + n);
-                        fd[b] = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
-                    }
-                }
-            }
-            R ux, uy, uz;
-            collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
-            R hd[QH];
-#pragma unroll
-            for (int i = 0; i < QH; ++i) {
-                const int a = HDIR<QH>(i);
-                if ((EX(a) == 1 && lfix) || (EX(a) == -1 && rfix)) hd[i] = ld<R>(hA + i * N + src_of(nb, a));
-                else hd[i] = (R)to_acc(buf[(27 + i) * ROW + PAD + tid - EX(a)]);
-            }
-            if (mask) {
-                const R Tref = (R)p.Tref;
-#pragma unroll
-                for (int ib = 0; ib < QH; ++ib) {
-                    const int b = HDIR<QH>(ib);
-                    const int ia = HOPP<QH>(ib);
-                    const int a = HDIR<QH>(ia);
-                    if (!(mask & (1u << a))) continue;
-                    const int l = off + __popc(mask & ((1u << a) - 1u));
-                    const float q = __ldg(lq + l);
-                    const R heq2 = R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref);
-                    const bool thin = (mask >> b) & 1u;
-                    if (p.wall_bc == 1) {  // EQ
-                        hd[ib] = R(0.5) * heq2;
-                        continue;
-                    }
-                    const R ha_b = ld<R>(hA + ia * N + n);
-                    if (q <= 0.5f && !thin) {
-                        hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
-                    } else {
-                        const R qq = (R)fmaxf(q, 0.5f);
-                        const R hb_b = ld<R>(hA + ib * N + n);
-                        hd[ib] = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
-                    }
-                }
-            }
-            const R Q = theta ? (R)__ldg(theta + n) : R(0);
-            collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
-        }
-        __syncthreads();  // stage sidx is refilled at the next iteration
-    }
-}
-
-template <typename S, int QH, bool CUM>
-cudaError_t launch_step_staged_kind(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
-    using R = typename Acc<S>::R;
-    const size_t smem = (size_t)kStages * stage_bytes<S, QH>();
-    static unsigned long long configured = 0;  // per device: dynamic shared memory limit raised
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !(configured & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_staged<S, QH, CUM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured |= 1ull << dev;
-    }
-    int per_sm = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<S, QH, CUM>, kTile, smem);
-    if (e != cudaSuccess) return e;
-    const int tiles = ((p.nx + kTile - 1) / kTile) * p.ny * p.nz;
-    const int grid = std::max(1, std::min(tiles, num_sms * std::max(per_sm, 1)));
-    k_step_staged<S, QH, CUM><<<grid, kTile, smem, s>>>((const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB,
-                                                        b.flags, b.theta, (const R*)b.inlet_post, b.seg_base,
-                                                        b.wmask, b.woff, b.lq, b.lwall, b.Twall, err, p);
-    return cudaGetLastError();
-}
-
-template <typename S, int QH>
-cudaError_t launch_step_staged(const Buffers& b, const DevParams& p, int* err, int num_sms, cudaStream_t s) {
-    return p.hkind == 3 ? launch_step_staged_kind<S, QH, true>(b, p, err, num_sms, s)
-                        : launch_step_staged_kind<S, QH, false>(b, p, err, num_sms, s);
 }
 
 template <typename S, int QH>
@@ -626,7 +409,12 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
     if (advance_h) {
         const int v = (urec ? 4 : 0) | (cum ? 2 : 0) | (eq ? 1 : 0);
         switch (v) {
-            case 0: k_step<S, QH, true, false, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 0:
+                if (p.hkind == 0)
+                    k_step<S, QH, true, false, false, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+                else
+                    k_step<S, QH, true, false, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+                break;
             case 1: k_step<S, QH, true, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
             case 2: k_step<S, QH, true, false, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
             case 3: k_step<S, QH, true, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
@@ -1172,6 +960,32 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
     }
 }
 
+// Transpose of the Zou-He rule for h at an inlet node (k_inlet), the density
+// (from f) held fixed: an unknown arrival j (e_x = +1) is the equilibrium at
+// u_in with the amplitude that closes sum h = rho T_in, so it depends on the
+// known arrivals k (e_x <= 0) through -M_j(u_in) / M_+(u_in) per unit, M the
+// unit equilibrium and M_+ the sum of M over the unknowns; in product form
+// that ratio is w(e_y, u_y) w(e_z, u_z) (D3Q7: 1).  mu holds the adjoint of
+// the node's full arrival vector and becomes that of its known arrivals (the
+// unknown ones are pulled from nowhere and get 0).
+template <typename R>
+__device__ __forceinline__ R w1_unit(int e, R u) {
+    return e == 0 ? R(1) - u * u - cs2<R>() : R(0.5) * (u * u + R(e) * u + cs2<R>());
+}
+template <typename R, int QH>
+__device__ __forceinline__ void zou_he_h_transpose(R* mu, const DevParams& p) {
+    const R uy = (R)p.uin[1], uz = (R)p.uin[2];
+    R sum = R(0);
+#pragma unroll
+    for (int i = 0; i < QH; ++i) {
+        const int a = HDIR<QH>(i);
+        if (EX(a) != 1) continue;
+        sum += (QH == 27 ? w1_unit<R>(EY(a), uy) * w1_unit<R>(EZ(a), uz) : R(1)) * mu[i];
+    }
+#pragma unroll
+    for (int i = 0; i < QH; ++i) mu[i] = (EX(HDIR<QH>(i)) == 1) ? R(0) : mu[i] - sum;
+}
+
 template <typename R, int QH, bool CUM = false>
 __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_next, R* __restrict__ out,
                                                      const R* __restrict__ uk, const R* __restrict__ hk,
@@ -1195,7 +1009,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     if (!in_range) return;
     const int N = p.N;
     const int type = fl & 3;
-    if (type == T_SOLID || type == T_INLET) {
+    // a Zou-He inlet node streams and collides like a fluid node
+    if (type == T_SOLID || (type == T_INLET && !p.zou_he)) {
 #pragma unroll
         for (int i = 0; i < QH; ++i) out[i * N + n] = R(0);
         return;
@@ -1204,6 +1019,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     const uint32_t lt = (1u << lane) - 1u;
     int x, y, z;
     node_xyz(n, p, x, y, z);
+    // symmetry rows: the row beside a symmetry row reads its own populations,
+    // e_y reversed, through the row's copies (k_mirror), so a push into a
+    // symmetry row lands on this row with the mirrored velocity
+    const bool rlo = p.mirror_lo && y == 1, rhi = p.mirror_hi && y == p.ny - 2;
     // push neighbours: index 0 <-> e = -1, 2 <-> e = +1; -1 when outside a bounded x
     int xt[3] = {x - 1, x, x + 1};
     if (p.periodic_x) {
@@ -1224,7 +1043,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
     for (int i = 0; i < QH; ++i) {
         const int a = HDIR<QH>(i);
         const int xx = xt[EX(a) + 1];
-        lam[i] = (xx < 0) ? R(0) : __ldg(mu_next + i * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]);
+        const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+        const int row = refl ? y * p.nx : yt[EY(a) + 1];
+        const int ii = refl ? HFLIPY<QH>(i) : i;
+        lam[i] = (xx < 0) ? R(0) : __ldg(mu_next + ii * N + xx + row + zt[EZ(a) + 1]);
     }
     if (!p.periodic_x && x == p.nx - 1) {
         // outlet plane: its incoming e_x < 0 populations copy this node's value
@@ -1232,8 +1054,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
         for (int i = 0; i < QH; ++i) {
             const int a = HDIR<QH>(i);
             if (EX(a) != -1) continue;
-            const int t = x + yt[EY(a) + 1] + zt[EZ(a) + 1];
-            lam[i] += mu_next[i * N + t];
+            const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+            const int t = x + (refl ? y * p.nx : yt[EY(a) + 1]) + zt[EZ(a) + 1];
+            lam[i] += mu_next[(refl ? HFLIPY<QH>(i) : i) * N + t];
         }
     }
     if (is_rw) {
@@ -1292,6 +1115,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(const R* __restrict__ mu_nex
         }
         const R Q = theta ? (R)__ldg(theta + n) : R(0);
         h_collision_transpose<R, QH, CUM>(lam, hp, ux, uy, uz, Q, p, mu, dth);
+        if (type == T_INLET) zou_he_h_transpose<R, QH>(mu, p);
 #pragma unroll
         for (int i = 0; i < QH; ++i) out[i * N + n] = mu[i];
     }
@@ -1322,12 +1146,67 @@ cudaError_t launch_adjoint(const Buffers& b, const DevParams& p, const R* u_leve
 // equilibrium at u_in with the amplitude that makes sum h = rho T_in.  The
 // node then collides and stores like a fluid node.  Everything is in deviation
 // form (f - w rho0, h - w T_ref).
+// The rule on one node's arrivals (deviation form), with the known ones
+// (e_x <= 0) in place: fills the unknown f and returns the density deviation
+// (zou_he_fill_f), then the unknown h (zou_he_fill_h).  T is the arithmetic
+// type (a dual number differentiates the rule with respect to u_in).
+template <typename T>
+__device__ __forceinline__ T zou_he_fill_f(T* fd, T ux, T uy, T uz, const DevParams& p) {
+    T s0 = T(0), sm = T(0);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) == 0) s0 += fd[a];
+        if (EX(a) == -1) sm += fd[a];
+    }
+    // the e_x = 0 and e_x = -1 weights sum to 2/3 and 1/6
+    const T drho = (s0 + T(2) * sm + (T)p.rho0 * ux) / (T(1) - ux);
+    T fe[27];
+    feq_dev<T>(fe, drho, ux, uy, uz, p);
+    T Ny = T(0), Nz = T(0);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) != 0) continue;
+        if (EY(a) != 0) Ny += EY(a) * (fd[a] - fe[a]);
+        if (EZ(a) != 0) Nz += EZ(a) * (fd[a] - fe[a]);
+    }
+    Ny *= T(1) / T(6);
+    Nz *= T(1) / T(6);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) != 1) continue;
+        const int b = OPP(a);
+        fd[a] = fd[b] + fe[a] - fe[b] - EY(a) * Ny - EZ(a) * Nz;
+    }
+    return drho;
+}
+template <typename T, int QH>
+__device__ __forceinline__ void zou_he_fill_h(T* hd, T drho, T ux, T uy, T uz, const DevParams& p) {
+    T K = T(0);
+#pragma unroll
+    for (int k = 0; k < QH; ++k)
+        if (EX(HDIR<QH>(k)) != 1) K += hd[k];
+    // unknown deviations = h^eq(amp, u_in) - w T_ref; with damp = amp - T_ref:
+    // damp (c_s^2 + u_x^2 + u_x)/2 = rho T_in - T_ref - K - T_ref (u_x^2 + u_x)/2
+    const T Tref = (T)p.Tref;
+    const T mU = T(0.5) * (cs2<T>() + ux * ux + ux);
+    const T target = drho * (T)p.Tin + (T)(p.rho0 * p.Tin - p.Tref);
+    const T damp = (target - K - Tref * T(0.5) * (ux * ux + ux)) / mU;
+    T he[QH];
+    heq_dev<T, QH>(he, damp, ux, uy, uz, p);
+#pragma unroll
+    for (int k = 0; k < QH; ++k)
+        if (EX(HDIR<QH>(k)) == 1) hd[k] = he[k];
+}
+
+// frec, hrec: pre-collision records of the coupled adjoint (the full arrival
+// vectors after the rule), or nullptr
 template <typename S, int QH, bool CUM, bool DO_H>
 __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* __restrict__ fB,
                                                    const S* __restrict__ hA, S* __restrict__ hB,
                                                    const uint8_t* __restrict__ flags,
                                                    const float* __restrict__ theta,
-                                                   typename Acc<S>::R* __restrict__ urec, const DevParams p) {
+                                                   typename Acc<S>::R* __restrict__ urec, void* __restrict__ frec,
+                                                   void* __restrict__ hrec, const DevParams p) {
     using R = typename Acc<S>::R;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.ny * p.nz) return;
@@ -1337,32 +1216,13 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
     const int N = p.N;
     const Nbr nb = make_nbr(0, y, z, p);
     const R ux = (R)p.uin[0], uy = (R)p.uin[1], uz = (R)p.uin[2];
-    R fd[27], fe[27];
-    R s0 = R(0), sm = R(0);
+    R fd[27];
 #pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        if (EX(a) == 1) continue;
-        fd[a] = ld<R>(fA + a * N + src_of(nb, a));
-        if (EX(a) == 0) s0 += fd[a];
-        else sm += fd[a];
-    }
-    // the e_x = 0 and e_x = -1 weights sum to 2/3 and 1/6
-    const R drho = (s0 + R(2) * sm + (R)p.rho0 * ux) / (R(1) - ux);
-    feq_dev<R>(fe, drho, ux, uy, uz, p);
-    R Ny = R(0), Nz = R(0);
+    for (int a = 0; a < 27; ++a) fd[a] = (EX(a) == 1) ? R(0) : ld<R>(fA + a * N + src_of(nb, a));
+    const R drho = zou_he_fill_f<R>(fd, ux, uy, uz, p);
+    if (frec) {
 #pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        if (EX(a) != 0) continue;
-        if (EY(a) != 0) Ny += EY(a) * (fd[a] - fe[a]);
-        if (EZ(a) != 0) Nz += EZ(a) * (fd[a] - fe[a]);
-    }
-    Ny *= R(1) / R(6);
-    Nz *= R(1) / R(6);
-#pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        if (EX(a) != 1) continue;
-        const int b = OPP(a);
-        fd[a] = fd[b] + fe[a] - fe[b] - EY(a) * Ny - EZ(a) * Nz;
+        for (int a = 0; a < 27; ++a) ((R*)frec)[a * N + n] = fd[a];
     }
     R vx, vy, vz;
     collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz);
@@ -1372,25 +1232,17 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
         urec[2 * N + n] = vz;
     }
     if constexpr (DO_H) {
-        R hd[QH], he[QH];
-        R K = R(0);
+        R hd[QH];
 #pragma unroll
         for (int k = 0; k < QH; ++k) {
             const int a = HDIR<QH>(k);
-            if (EX(a) == 1) continue;
-            hd[k] = ld<R>(hA + k * N + src_of(nb, a));
-            K += hd[k];
+            hd[k] = (EX(a) == 1) ? R(0) : ld<R>(hA + k * N + src_of(nb, a));
         }
-        // unknown deviations = h^eq(amp, u_in) - w T_ref; with damp = amp - T_ref:
-        // damp (c_s^2 + u_x^2 + u_x)/2 = rho T_in - T_ref - K - T_ref (u_x^2 + u_x)/2
-        const R Tref = (R)p.Tref;
-        const R mU = R(0.5) * (cs2<R>() + ux * ux + ux);
-        const R target = drho * (R)p.Tin + (R)(p.rho0 * p.Tin - p.Tref);
-        const R damp = (target - K - Tref * R(0.5) * (ux * ux + ux)) / mU;
-        heq_dev<R, QH>(he, damp, ux, uy, uz, p);
+        zou_he_fill_h<R, QH>(hd, drho, ux, uy, uz, p);
+        if (hrec) {
 #pragma unroll
-        for (int k = 0; k < QH; ++k)
-            if (EX(HDIR<QH>(k)) == 1) hd[k] = he[k];
+            for (int k = 0; k < QH; ++k) ((R*)hrec)[k * N + n] = hd[k];
+        }
         const R Q = theta ? (R)__ldg(theta + n) : R(0);
         collide_store_h<S, QH, CUM>(hd, hB, n, p, vx, vy, vz, Q);
     }
@@ -1401,7 +1253,8 @@ cudaError_t launch_inlet(const Buffers& b, const DevParams& p, cudaStream_t s, b
     using R = typename Acc<S>::R;
     const int total = p.ny * p.nz;
     const int grid = (total + kBlock - 1) / kBlock;
-#define LBM_INLET_ARGS (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (R*)b.urec, p
+#define LBM_INLET_ARGS                                                                                   \
+    (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (R*)b.urec, b.frec, b.hrec, p
     if (!advance_h) k_inlet<S, QH, false, false><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
     else if (p.hkind == 3) k_inlet<S, QH, true, true><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
     else k_inlet<S, QH, false, true><<<grid, kBlock, 0, s>>>(LBM_INLET_ARGS);
@@ -1515,6 +1368,173 @@ __device__ __forceinline__ FFront<T> f_front(const T* m, const T Fx, const T Fy,
     return o;
 }
 
+// Reverse mode through f_front: from the adjoints of its outputs (bs = s
+// diagonal, bk = k off-diagonal, birho, bdrho_out, bv, bu) to those of the
+// ten moments m and of F, written out step by step backwards through f_front.
+template <typename R>
+__device__ __forceinline__ void f_front_adjoint(const R* m, const DevParams& p, R bsxx, R bsyy, R bszz, R bkxy,
+                                                R bkxz, R bkyz, R birho, R bdrho, const R* bv, const R* bu, R* G) {
+    const R c = cs2<R>();
+    const R drho = m[0], jx = m[1], jy = m[2], jz = m[3];
+    const R rho = (R)p.rho0 + drho;
+    const R irho = R(1) / rho;
+    const R mux = jx * irho, muy = jy * irho, muz = jz * irho;
+    const R om1 = R(1) - (R)p.omega1;
+    const R omb = R(1) - (R)p.omega_bulk;
+    const R F[3] = {(R)p.F[0], (R)p.F[1], (R)p.F[2]};
+    // sxx = (tr + dxy + dxz)/3, syy = sxx - dxy, szz = sxx - dxz
+    const R bst = bsxx + bsyy + bszz;
+    const R bdxy = bst * (R(1) / R(3)) - bsyy;
+    const R bdxz = bst * (R(1) / R(3)) - bszz;
+    const R btr = bst * (R(1) / R(3));
+    // dxy = (axx - ayy) om1, dxz = (axx - azz) om1, tr = (axx + ayy + azz) omb
+    const R baxx = om1 * (bdxy + bdxz) + omb * btr;
+    const R bayy = -om1 * bdxy + omb * btr;
+    const R bazz = -om1 * bdxz + omb * btr;
+    R bj[3] = {R(0), R(0), R(0)}, bmu[3] = {R(0), R(0), R(0)};
+    // kxy = (m7 - jx muy) om1, kxz = (m8 - jx muz) om1, kyz = (m9 - jy muz) om1
+    G[7] = om1 * bkxy;
+    G[8] = om1 * bkxz;
+    G[9] = om1 * bkyz;
+    bj[0] -= om1 * (bkxy * muy + bkxz * muz);
+    bmu[1] -= om1 * bkxy * jx;
+    bmu[2] -= om1 * (bkxz * jx + bkyz * jy);
+    bj[1] -= om1 * bkyz * muz;
+    // a_dd = m_(4+d) - drho c - j_d mu_d
+    const R ba[3] = {baxx, bayy, bazz};
+    const R mu[3] = {mux, muy, muz}, j[3] = {jx, jy, jz};
+    R bdr = bdrho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        G[4 + d] = ba[d];
+        bdr -= c * ba[d];
+        bj[d] -= mu[d] * ba[d];
+        bmu[d] -= j[d] * ba[d];
+    }
+    // v_d = mu_d + F_d irho, u_d = mu_d + F_d irho / 2
+    R bir = birho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bmu[d] += bv[d] + bu[d];
+        G[10 + d] = irho * (bv[d] + R(0.5) * bu[d]);
+        bir += F[d] * (bv[d] + R(0.5) * bu[d]);
+    }
+    // mu_d = j_d irho
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bj[d] += irho * bmu[d];
+        bir += j[d] * bmu[d];
+    }
+    // irho = 1 / (rho0 + drho)
+    bdr -= irho * irho * bir;
+    G[0] = bdr;
+    G[1] = bj[0];
+    G[2] = bj[1];
+    G[3] = bj[2];
+}
+
+// w_d = lambda_h . dC_h/du_d for the central-moment kinds (Eq.
+// H_cm_collision, App. D source), in reverse mode.  With Y = T(u) g the
+// central moments of the arrivals g (deviations), Y* their relaxed values and
+// z = T(u)^-T lambda: dT/du_d = -S_d T exactly on the three-point stencil,
+// (S_d Y)_mno = m_d Y_(m - e_d)no lowering the d-th order by one, and the
+// stored shift T_ref K(u) of the central moments gives S_d K, so
+//   dC_h/du_d = T^-1 (S_d Y* - (1 - S) S_d Y + S T_ref S_d K)
+// and w_d = z . (S_d Y* - (1 - S) S_d Y + S T_ref S_d K).
+template <typename R, int QH>
+__device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R ux, R uy, R uz, R Q,
+                                                   const DevParams& p, R* w) {
+    const R Tref = (R)p.Tref;
+    if constexpr (QH == 27) {
+        R Z[27], Y[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) {
+            Z[CUBE(a)] = lam[a];
+            Y[CUBE(a)] = g[a];
+        }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(Z[3 * j], Z[3 * j + 1], Z[3 * j + 2], ux);
+#pragma unroll
+        for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+            for (int xx = 0; xx < 3; ++xx) inv3T<R>(Z[9 * zz + xx], Z[9 * zz + 3 + xx], Z[9 * zz + 6 + xx], uy);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) inv3T<R>(Z[j], Z[9 + j], Z[18 + j], uz);
+        forward_cube<R>(Y, ux, uy, uz);
+        const R dH = Y[0] + R(0.5) * Q;
+        const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
+        R Ys[27];
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int n = 0; n < 3; ++n)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const R sr = (R)p.sh[m + n + o];
+                    const R E = Eq<R>(m, n, o);
+                    const R D = Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
+                    const int i = MIDX(m, n, o);
+                    Ys[i] = (R(1) - sr) * Y[i] + sr * (dH * E + Tref * D) + (R(1) - R(0.5) * sr) * Q * E;
+                }
+        R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int n = 0; n < 3; ++n)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const R sr = (R)p.sh[m + n + o];
+                    const R zz = Z[MIDX(m, n, o)];
+                    if (m >= 1) {
+                        const int lo = MIDX(m - 1, n, o);
+                        const R K = Kd<R>(m - 1, ux) * Kd<R>(n, uy) * Kd<R>(o, uz);
+                        acc[0] += zz * R(m) * (Ys[lo] - (R(1) - sr) * Y[lo] + sr * Tref * K);
+                    }
+                    if (n >= 1) {
+                        const int lo = MIDX(m, n - 1, o);
+                        const R K = Kd<R>(m, ux) * Kd<R>(n - 1, uy) * Kd<R>(o, uz);
+                        acc[1] += zz * R(n) * (Ys[lo] - (R(1) - sr) * Y[lo] + sr * Tref * K);
+                    }
+                    if (o >= 1) {
+                        const int lo = MIDX(m, n, o - 1);
+                        const R K = Kd<R>(m, ux) * Kd<R>(n, uy) * Kd<R>(o - 1, uz);
+                        acc[2] += zz * R(o) * (Ys[lo] - (R(1) - sr) * Y[lo] + sr * Tref * K);
+                    }
+                }
+        w[0] = acc[0];
+        w[1] = acc[1];
+        w[2] = acc[2];
+    } else {
+        // D3Q7: moments 0, 1d, 2d about u; S_d takes 0 -> 1d and 1d -> 2d (x2)
+        const R u[3] = {ux, uy, uz};
+        const R c = cs2<R>();
+        R z0 = lam[0];
+        R z1[3], z2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R mb2 = R(0.5) * (lam[1 + d] + lam[4 + d]) - lam[0];
+            const R mb1 = R(0.5) * (lam[1 + d] - lam[4 + d]);
+            z2[d] = mb2;
+            z1[d] = mb1 + R(2) * u[d] * mb2;
+            z0 += u[d] * mb1 + u[d] * u[d] * mb2;
+        }
+        (void)z0;
+        const R m0 = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+        const R dH = m0 + R(0.5) * Q;
+        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+        const R y0 = m0, ys0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R k1 = (g[1 + d] - g[4 + d]) - u[d] * m0;
+            const R ys1 = (R(1) - s1) * k1 + s1 * (Tref * u[d]);
+            // S_d K: 1 at the first order, 2 K_1 = -2 u_d at the second
+            w[d] = z1[d] * (ys0 - (R(1) - s1) * y0 + s1 * Tref) +
+                   z2[d] * R(2) * (ys1 - (R(1) - s2) * k1 - s2 * Tref * u[d]);
+        }
+        (void)c;
+    }
+}
+
 // Adjoint of the f collision of one node at its pre-collision arrivals g:
 // G[k] = lambda . (dC_f/dg) d_k + w . (dU/dg) d_k for the ten unit-moment
 // perturbations d_k (k < 10) and the same for the three components of F
@@ -1524,7 +1544,7 @@ __device__ __forceinline__ FFront<T> f_front(const T* m, const T Fx, const T Fy,
 // through both the equilibrium part of the moments and the transform, whose
 // derivative is d/dv_x T(v)^-1 kappa = T(v)^-1 (S_x kappa), (S_x kappa)_mno =
 // m kappa_(m-1)no (exact on the three-point lattice).  The front part (ten
-// moments and F -> s, k, 1/rho, v, u) runs in forward mode per direction.
+// moments and F -> s, k, 1/rho, v, u) is reversed by hand (f_front_adjoint).
 template <typename R>
 __device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p, const R* lam, const R* w, R* G) {
     R m[10] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -1651,20 +1671,8 @@ __device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p
                 if (n >= 1) bv[1] += zz * R(n) * K[MIDX(mm, n - 1, o)];
                 if (o >= 1) bv[2] += zz * R(o) * K[MIDX(mm, n, o - 1)];
             }
-    // forward mode through the front part, one direction at a time
-    using D = Dual<R>;
-#pragma unroll 1
-    for (int k = 0; k < 13; ++k) {
-        D md[10];
-#pragma unroll
-        for (int i = 0; i < 10; ++i) md[i] = D(m[i], (k == i) ? R(1) : R(0), 0);
-        const D Fx((R)p.F[0], k == 10 ? R(1) : R(0), 0), Fy((R)p.F[1], k == 11 ? R(1) : R(0), 0),
-            Fz((R)p.F[2], k == 12 ? R(1) : R(0), 0);
-        const FFront<D> T = f_front<D>(md, Fx, Fy, Fz, p);
-        G[k] = bsxx * T.sxx.d + bsyy * T.syy.d + bszz * T.szz.d + bkxy * T.kxy.d + bkxz * T.kxz.d +
-               bkyz * T.kyz.d + birho * T.irho.d + bdrho * T.drho.d + bv[0] * T.v[0].d + bv[1] * T.v[1].d +
-               bv[2] * T.v[2].d + w[0] * T.u[0].d + w[1] * T.u[1].d + w[2] * T.u[2].d;
-    }
+    // reverse mode through the front part
+    f_front_adjoint<R>(m, p, bsxx, bsyy, bszz, bkxy, bkxz, bkyz, birho, bdrho, bv, w, G);
 }
 
 template <typename R, int QH, bool CUM>
@@ -1711,30 +1719,40 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
     const R wsurf = (obj.kind == 0) ? (R)obj.weight : R(0);
     // force objective: d/ds_f of weight * e_a,comp (f*_a(x_b) + f_abar(x_b)) per link of obj.wall
     const R wforce = (obj.kind == 2) ? (R)obj.weight : R(0);
+    // symmetry rows: a push into a symmetry row lands on this row, e_y
+    // reversed (the row's copies, k_mirror; as in k_adjoint)
+    const bool rlo = p.mirror_lo && y == 1, rhi = p.mirror_hi && y == p.ny - 2;
     // lambda = P^T mu^{k+1} (+ the objective's terms)
     R lf[27], lh[QH];
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
         const int xx = xt[EX(a) + 1];
-        lf[a] = (xx < 0) ? R(0) : muf_next[a * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+        const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+        const int row = refl ? y * p.nx : yt[EY(a) + 1];
+        lf[a] = (xx < 0) ? R(0) : muf_next[(refl ? FLIPY(a) : a) * N + xx + row + zt[EZ(a) + 1]];
     }
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
         const int a = HDIR<QH>(i);
         const int xx = xt[EX(a) + 1];
-        lh[i] = (xx < 0) ? R(0) : muh_next[i * N + xx + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+        const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+        const int row = refl ? y * p.nx : yt[EY(a) + 1];
+        lh[i] = (xx < 0) ? R(0) : muh_next[(refl ? HFLIPY<QH>(i) : i) * N + xx + row + zt[EZ(a) + 1]];
     }
     if (!p.periodic_x && x == p.nx - 1) {
 #pragma unroll
         for (int a = 0; a < 27; ++a) {
             if (EX(a) != -1) continue;
-            lf[a] += muf_next[a * N + x + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+            const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+            lf[a] += muf_next[(refl ? FLIPY(a) : a) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) + zt[EZ(a) + 1]];
         }
 #pragma unroll
         for (int i = 0; i < QH; ++i) {
             const int a = HDIR<QH>(i);
             if (EX(a) != -1) continue;
-            lh[i] += muh_next[i * N + x + yt[EY(a) + 1] + zt[EZ(a) + 1]];
+            const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+            lh[i] += muh_next[(refl ? HFLIPY<QH>(i) : i) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) +
+                              zt[EZ(a) + 1]];
         }
     }
     if (is_rw) {
@@ -1838,19 +1856,25 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
         for (int a = 0; a < 27; ++a) fv[a] = g[a];
         collide_f<R>(fv, p, ux, uy, uz, rho);
     }
-    // w = (dC_h/du)^T lambda_h: three forward-mode passes in u
+    // w = (dC_h/du)^T lambda_h: reverse mode for the central-moment kinds,
+    // three forward-mode passes in u for the nonlinear Cumulants-1st
     R w[3];
+    if constexpr (CUM) {
 #pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-        D hd[QH];
+        for (int k = 0; k < 3; ++k) {
+            D hd[QH];
 #pragma unroll
-        for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i]);
-        const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0), vz(uz, k == 2 ? R(1) : R(0), 0);
-        collide_h<D, QH, CUM>(hd, vx, vy, vz, D(Q), p);
-        R acc = R(0);
+            for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i]);
+            const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0),
+                vz(uz, k == 2 ? R(1) : R(0), 0);
+            collide_h<D, QH, CUM>(hd, vx, vy, vz, D(Q), p);
+            R acc = R(0);
 #pragma unroll
-        for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
-        w[k] = acc;
+            for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
+            w[k] = acc;
+        }
+    } else {
+        h_velocity_adjoint<R, QH>(lh, hpre, ux, uy, uz, Q, p, w);
     }
     // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the h-only
     // adjoint's code; Cumulants-1st needs the post-collision state)

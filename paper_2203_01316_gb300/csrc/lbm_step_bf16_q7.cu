@@ -19,5 +19,4 @@ template cudaError_t launch_surface_flux<__nv_bfloat16, 7>(const Buffers&, const
                                                  cudaStream_t);
 template cudaError_t launch_wall_force<__nv_bfloat16, 7>(const Buffers&, const DevParams&, int, double*, double*,
                                                cudaStream_t);
-template cudaError_t launch_step_staged<__nv_bfloat16, 7>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 }  // namespace lbmd

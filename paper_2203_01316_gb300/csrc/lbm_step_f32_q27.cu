@@ -19,7 +19,6 @@ template cudaError_t launch_surface_flux<float, 27>(const Buffers&, const DevPar
                                                  cudaStream_t);
 template cudaError_t launch_wall_force<float, 27>(const Buffers&, const DevParams&, int, double*, double*,
                                                cudaStream_t);
-template cudaError_t launch_step_staged<float, 27>(const Buffers&, const DevParams&, int*, int, cudaStream_t);
 
 // streaming map of the step kernels (storage independent)
 __global__ void k_stream_map(const uint8_t* __restrict__ flags, const int32_t* __restrict__ wnode,

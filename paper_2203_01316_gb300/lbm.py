@@ -51,7 +51,7 @@ class Params(C.Structure):
                 ("cuda_stream", C.c_void_p), ("round_nearest", C.c_int), ("step_kernel", C.c_int),
                 ("wall_bc", C.c_int), ("inlet_bc", C.c_int)]
 WALL_BC = {"iabb": 0, "eq": 1, "abb": 2}
-STEP_KERNEL = {"auto": 0, "classic": 1, "staged": 2}
+STEP_KERNEL = {"auto": 0, "classic": 1}
 
 
 _lib = None
@@ -142,8 +142,8 @@ class Solver:
     'f32' | 'f64' | 'f16' | 'bf16'; periodic_x: True, or False for an
     inlet/outlet channel; stream: a torch.cuda.Stream or raw handle, or None
     for a library-owned stream; round_nearest: 16-bit storage rounds to
-    nearest instead of stochastically; step_kernel: 'auto' | 'classic' |
-    'staged' (implementation of the step, same results); wall_bc: 'iabb'
+    nearest instead of stochastically; step_kernel: 'auto' | 'classic'
+    (implementation of the step); wall_bc: 'iabb'
     (Eq. IBB/IABB with q) | 'eq' (BB + EQ) | 'abb' (BB + ABB); inlet_bc:
     'equilibrium' (fixed inlet equilibria) | 'zou_he'."""
 

@@ -7,13 +7,15 @@ from paper_2203_01316_gb300 import inputs as I
 
 
 def make_pair(w, nu, k, qh=27, hkind="trt", storage="f32", F=(0.0, 0.0, 0.0), wall_T=(1.0,),
-              rho0=1.0, T_ref=0.0, theta=None, omega_bulk=1.0, oracle=True, wall_bc="iabb"):
+              rho0=1.0, T_ref=0.0, theta=None, omega_bulk=1.0, oracle=True, wall_bc="iabb", step_kernel="auto",
+              round_nearest=False):
     from paper_2203_01316_gb300 import Solver
     nx, ny, nz = w["dims"]
     u_in = w.get("u_in", (0.0, 0.0, 0.0))
     T_in = w.get("T_in", 0.0)
     s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=qh, hkind=hkind, storage=storage, periodic_x=w["periodic_x"],
-               omega_bulk=omega_bulk, rho0=rho0, T_ref=T_ref, wall_bc=wall_bc)
+               omega_bulk=omega_bulk, rho0=rho0, T_ref=T_ref, wall_bc=wall_bc, step_kernel=step_kernel,
+               round_nearest=round_nearest)
     s.set_geometry(w["flags"], w["links"], n_walls=w["nwalls"])
     for i, T in enumerate(wall_T[: w["nwalls"]]):
         s.set_bc(i, T)
