@@ -578,7 +578,8 @@ def porous_study(args):
 def sphere_nusselt_study(args):
     """The heated sphere in a channel (192x64x64, D = 16 with a seeded
     sub-node centre offset, plug inlet u = 0.02, T_in = 0, T_w = 1, Re = 20:
-    nu = 0.016), D3Q27 cumulant f + D3Q27 CM-TRT h with Eq. IBB / Eq. IABB,
+    nu = 0.016; --scale s multiplies the grid and D), D3Q27 cumulant f + D3Q27
+    CM-TRT h (--kinds) with Eq. IBB / Eq. IABB,
     for Pr = 10, 100, 1000 over `steps` steps (default 20k): the sphere's
     Nusselt number Nu = q D / (k pi D^2 (T_w - T_in)) (the Sec. 4.4
     definition with the sphere's area, reading R10), averaged over the last
@@ -588,19 +589,23 @@ def sphere_nusselt_study(args):
     from paper_2203_01316_gb300 import Solver, build, inputs as I
     build.build()
     stream = torch.cuda.Stream()
-    D, U, Re = 16.0, 0.02, 20.0
+    sc = args.scale  # 2: the same channel at twice the resolution (384x128x128, D = 32)
+    D, U, Re = 16.0 * sc, 0.02, 20.0
     nu = U * D / Re
-    w = I.heated_sphere(192, 64, 64, D=D, cx=48.0, seed=WORKLOAD["seed"], u_in=U, T_in=0.0)
+    w = I.heated_sphere(int(round(192 * sc)), int(round(64 * sc)), int(round(64 * sc)), D=D, cx=48.0 * sc,
+                        seed=WORKLOAD["seed"], u_in=U, T_in=0.0)
     nx, ny, nz = w["dims"]
     steps = args.steps
     win = max(1, steps // 10)
     out = {"nusselt_study": f"heated sphere {nx}x{ny}x{nz}, D={D:g}, Re={Re:g}, nu={nu:g}, {steps} steps, "
                             f"Nu averaged over the last {win} steps", "results": {}}
-    for Pr in [float(v) for v in (args.prs or "10,100,1000").split(",")]:
+    kinds = (args.kinds or "trt").split(",")
+    storages = (args.storages or "f32,f64").split(",")
+    for Pr, kind in itertools.product([float(v) for v in (args.prs or "10,100,1000").split(",")], kinds):
         k = nu / Pr
-        r = {"k": k}
-        for storage in ("f32", "f64"):
-            s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind="trt", storage=storage, periodic_x=False,
+        r = {"k": k, "h_kind": kind}
+        for storage in storages:
+            s = Solver(nx, ny, nz, nu=nu, k=k, lat_h=27, hkind=kind, storage=storage, periodic_x=False,
                        T_ref=w["T_in"], stream=stream.cuda_stream)
             s.set_geometry(w["flags"], w["links"], n_walls=1)
             s.set_bc(0, 1.0)
@@ -618,7 +623,12 @@ def sphere_nusselt_study(args):
                     with torch.cuda.stream(stream):  # ordered after the accumulation
                         half.copy_(J)
                 s.step(1)
-            mass, energy = s.balances()
+            try:
+                mass, energy = s.balances()
+            except Exception as e:  # a kind that is unstable on this mesh: say so and go on
+                r[storage] = {"diverged": str(e)}
+                s.close()
+                continue
             dt = time.perf_counter() - t0
             Nu = float(J.item())
             # drift check: the mean over the window's second half against its first half
@@ -626,9 +636,10 @@ def sphere_nusselt_study(args):
             r[storage] = {"Nu": Nu, "Nu_first_half_of_window": first, "Nu_second_half_of_window": second,
                           "wall_s": dt, "MLUPS": nx * ny * nz * steps / dt / 1e6, "mass": mass}
             s.close()
-        r["Nu_f32_vs_f64"] = abs(r["f32"]["Nu"] - r["f64"]["Nu"]) / abs(r["f64"]["Nu"])
-        out["results"][f"Pr={Pr:g}"] = r
-        print(json.dumps({f"Pr={Pr:g}": r}), flush=True)
+        if "Nu" in r.get("f32", {}) and "Nu" in r.get("f64", {}):
+            r["Nu_f32_vs_f64"] = abs(r["f32"]["Nu"] - r["f64"]["Nu"]) / abs(r["f64"]["Nu"])
+        out["results"][f"Pr={Pr:g} {kind}"] = r
+        print(json.dumps({f"Pr={Pr:g} {kind}": r}), flush=True)
     print(json.dumps(out), flush=True)
 
 
@@ -922,8 +933,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--flow-adjoint", action="store_true",
                     help="time the coupled f + h adjoint (gradients for F and u_in) on the workload")
-    ap.add_argument("--storages", default="", help="validation hill: comma-separated storages (f64, f32)")
-    ap.add_argument("--kinds", default="", help="validation confined: comma-separated h kinds")
+    ap.add_argument("--storages", default="", help="validation hill, nusselt study: comma-separated storages")
+    ap.add_argument("--kinds", default="", help="validation confined, nusselt study: comma-separated h kinds")
     ap.add_argument("--prs", default="", help="validation confined: comma-separated Prandtl numbers")
     ap.add_argument("--orders", default="", help="validation confined: wall-rule orders, '1st', '2nd' or both")
     ap.add_argument("--inlet", default="zou_he", choices=["zou_he", "equilibrium"],

@@ -8,5 +8,5 @@ template cudaError_t launch_adjoint<float, 27>(const Buffers&, const DevParams&,
                                            const float*, float*, AdjObjective, double*, cudaStream_t);
 template cudaError_t launch_adjoint_flow<float, 27>(const Buffers&, const DevParams&, const float*, const float*,
                                                 const float*, const float*, float*, float*, AdjObjective, double*,
-                                                double*, const float*, cudaStream_t);
+                                                double*, const float*, float*, cudaStream_t);
 }  // namespace lbmd

@@ -8,5 +8,5 @@ template cudaError_t launch_adjoint<double, 7>(const Buffers&, const DevParams&,
                                            const double*, double*, AdjObjective, double*, cudaStream_t);
 template cudaError_t launch_adjoint_flow<double, 7>(const Buffers&, const DevParams&, const double*, const double*,
                                                 const double*, const double*, double*, double*, AdjObjective, double*,
-                                                double*, const double*, cudaStream_t);
+                                                double*, const double*, double*, cudaStream_t);
 }  // namespace lbmd

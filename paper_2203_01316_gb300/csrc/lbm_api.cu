@@ -44,6 +44,7 @@ struct lbm_ctx {
     double* d_dlink = nullptr;      // adjoint: per link dJ/dT_w accumulators
     double* d_flowacc = nullptr;    // coupled adjoint: per node (dJ/dF, dJ/du_in) accumulators, [N][6]
     void* d_din = nullptr;          // coupled adjoint: d(inlet state)/du_in, R[3][27 + qh]
+    void* d_wflow = nullptr;        // coupled adjoint: velocity derivative of the h step, R[3][N]
     std::vector<double> h_din;      // the uploaded copy of d_din
     int n_walls = 1;
     float* d_Twall = nullptr;
@@ -356,6 +357,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;
+    lbmd::sync_float_params(d);
     lbm_status s = upload_inlet(c);
     if (s != LBM_OK) return bail(s);
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -381,6 +383,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_theta);
     cudaFree(c->d_flowacc);
     cudaFree(c->d_din);
+    cudaFree(c->d_wflow);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
@@ -666,6 +669,7 @@ lbm_status lbm_set_inlet(lbm_ctx* c, double ux, double uy, double uz, double T_i
     c->dp.uin[1] = uy;
     c->dp.uin[2] = uz;
     c->dp.Tin = T_in;
+    lbmd::sync_float_params(c->dp);
     return upload_inlet(c);
 }
 
@@ -675,6 +679,7 @@ lbm_status lbm_set_force(lbm_ctx* c, double Fx, double Fy, double Fz) {
     c->dp.F[0] = Fx;
     c->dp.F[1] = Fy;
     c->dp.F[2] = Fz;
+    lbmd::sync_float_params(c->dp);
     return LBM_OK;
 }
 
@@ -1162,7 +1167,6 @@ lbm_status lbm_adjoint_flow_step(lbm_ctx* c, const void* f_level, const void* h_
     if (!c->geometry) return fail(c, LBM_ERR_STATE, "set the geometry first");
     if (c->p.storage != LBM_F32 && c->p.storage != LBM_F64)
         return fail(c, LBM_ERR_INVALID, "the coupled adjoint needs FP32 or FP64 storage");
-    if (c->dp.zou_he) return fail(c, LBM_ERR_INVALID, "the coupled adjoint does not cover the Zou-He inlet");
     if ((f_level == nullptr) != (h_level == nullptr))
         return fail(c, LBM_ERR_INVALID, "give both level records or neither (initial level)");
     lbm_status st = check_objective(c, obj);
@@ -1171,11 +1175,13 @@ lbm_status lbm_adjoint_flow_step(lbm_ctx* c, const void* f_level, const void* h_
     const size_t rsize = c->ssize;
     if (!c->d_flowacc) {
         if (dev_alloc(c, &c->d_flowacc, (size_t)c->N * 6 * sizeof(double)) != cudaSuccess)
-            return fail(c, LBM_ERR_NOMEM, "coupled adjoint accumulators");
+            return fail(c, LBM_ERR_NOMEM, "coupled adjoint accumulators: out of device memory");
         CK(cudaMemsetAsync(c->d_flowacc, 0, (size_t)c->N * 6 * sizeof(double), c->stream), "accumulators");
     }
     if (!c->d_din && dev_alloc(c, &c->d_din, (size_t)3 * (27 + c->qh) * rsize) != cudaSuccess)
-        return fail(c, LBM_ERR_NOMEM, "inlet derivative table");
+        return fail(c, LBM_ERR_NOMEM, "inlet derivative table: out of device memory");
+    if (!c->d_wflow && dev_alloc(c, &c->d_wflow, (size_t)3 * c->N * rsize) != cudaSuccess)
+        return fail(c, LBM_ERR_NOMEM, "coupled adjoint velocity derivative: out of device memory");
     std::vector<double> din = inlet_derivative(c);
     if (din != c->h_din) {
         CK(cudaStreamSynchronize(c->stream), "inlet derivative table");
@@ -1198,21 +1204,21 @@ lbm_status lbm_adjoint_flow_step(lbm_ctx* c, const void* f_level, const void* h_
         e = c->qh == 27 ? lbmd::launch_adjoint_flow<R, 27>(b, p, (const R*)f_level, (const R*)h_level,
                                                           (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
                                                           (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
-                                                          (const R*)c->d_din, c->stream)
+                                                          (const R*)c->d_din, (R*)c->d_wflow, c->stream)
                         : lbmd::launch_adjoint_flow<R, 7>(b, p, (const R*)f_level, (const R*)h_level,
                                                          (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
                                                          (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
-                                                         (const R*)c->d_din, c->stream);
+                                                         (const R*)c->d_din, (R*)c->d_wflow, c->stream);
     } else {
         using R = float;
         e = c->qh == 27 ? lbmd::launch_adjoint_flow<R, 27>(b, p, (const R*)f_level, (const R*)h_level,
                                                           (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
                                                           (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
-                                                          (const R*)c->d_din, c->stream)
+                                                          (const R*)c->d_din, (R*)c->d_wflow, c->stream)
                         : lbmd::launch_adjoint_flow<R, 7>(b, p, (const R*)f_level, (const R*)h_level,
                                                          (const R*)muf_next, (const R*)muh_next, (R*)muf_out,
                                                          (R*)muh_out, a, dJ_dtheta, c->d_flowacc,
-                                                         (const R*)c->d_din, c->stream);
+                                                         (const R*)c->d_din, (R*)c->d_wflow, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "coupled adjoint launch");
     return LBM_OK;

@@ -145,6 +145,12 @@ template <typename T> struct Dual {
 template <typename T> struct ScalarOf { using type = T; };
 template <typename T> struct ScalarOf<Dual<T>> { using type = T; };
 
+// a parameter in arithmetic type R: the float copy for FP32-based types
+template <typename R> __device__ __forceinline__ R par(double d, float f) {
+    if constexpr (sizeof(typename ScalarOf<R>::type) == 4) return R(f);
+    else return R(d);
+}
+
 // slot of moment mno in the cube after the forward passes
 __host__ __device__ __forceinline__ constexpr int MIDX(int m, int n, int o) { return o * 9 + n * 3 + m; }
 
@@ -243,7 +249,26 @@ struct DevParams {
     double rho0, Tref;
     double F[3];
     double uin[3], Tin;
+    // the same parameters rounded to float once on the host (sync_float_params):
+    // FP32 arithmetic reads these, so no kernel converts a double per use
+    struct {
+        float omega1, omega_bulk, sh[7], rho0, Tref, F[3], uin[3], Tin;
+    } pf;
 };
+
+// refresh DevParams::pf after changing a double parameter (host)
+inline void sync_float_params(DevParams& d) {
+    d.pf.omega1 = (float)d.omega1;
+    d.pf.omega_bulk = (float)d.omega_bulk;
+    for (int i = 0; i < 7; ++i) d.pf.sh[i] = (float)d.sh[i];
+    d.pf.rho0 = (float)d.rho0;
+    d.pf.Tref = (float)d.Tref;
+    for (int i = 0; i < 3; ++i) {
+        d.pf.F[i] = (float)d.F[i];
+        d.pf.uin[i] = (float)d.uin[i];
+    }
+    d.pf.Tin = (float)d.Tin;
+}
 
 // ---- f: cumulant collision (Eq. hydro_cu_collision) ----------------------
 // fd: pulled deviations in, post-collision deviations out.  Second-order
@@ -270,7 +295,7 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
         if (EY(a) * EZ(a) != 0) myz += (EY(a) * EZ(a)) * v;
     }
     const R c = cs2<R>();
-    const R rho0 = (R)p.rho0;
+    const R rho0 = par<R>(p.rho0, p.pf.rho0);
     const R rho = rho0 + drho;
     const R irho = R(1) / rho;
     const R mux = jx * irho, muy = jy * irho, muz = jz * irho;
@@ -281,8 +306,8 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
     R kxy = mxy - jx * muy;
     R kxz = mxz - jx * muz;
     R kyz = myz - jy * muz;
-    const R om1 = R(1) - (R)p.omega1;
-    const R omb = R(1) - (R)p.omega_bulk;
+    const R om1 = R(1) - par<R>(p.omega1, p.pf.omega1);
+    const R omb = R(1) - par<R>(p.omega_bulk, p.pf.omega_bulk);
     R dxy = (axx - ayy) * om1;
     R dxz = (axx - azz) * om1;
     R tr = (axx + ayy + azz) * omb;
@@ -343,7 +368,7 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
 
 template <typename R>
 __device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& uy, R& uz, R& rho_out) {
-    collide_f_force<R>(fd, p, (R)p.F[0], (R)p.F[1], (R)p.F[2], ux, uy, uz, rho_out);
+    collide_f_force<R>(fd, p, par<R>(p.F[0], p.pf.F[0]), par<R>(p.F[1], p.pf.F[1]), par<R>(p.F[2], p.pf.F[2]), ux, uy, uz, rho_out);
 }
 
 // ---- h: central-moment collision (Eq. H_cm_collision + App. D source) ----
@@ -360,7 +385,7 @@ __device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const 
 #pragma unroll
     for (int a = 0; a < 27; ++a) cb[CUBE(a)] = hd[a];
     forward_cube<R>(cb, ux, uy, uz);
-    const R Tref = (R)p.Tref;
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
     const R dH = cb[0] + R(0.5) * Q;
     const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
 #pragma unroll
@@ -376,11 +401,11 @@ __device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const 
                     if ((m + n + o) % 2 == 0) {
                         y = dH * E + Tref * D + R(0.5) * Q * E;
                     } else {
-                        const R s = (R)p.sh[1];
+                        const R s = par<R>(p.sh[1], p.pf.sh[1]);
                         y = (R(1) - s) * y + s * (Tref * D);
                     }
                 } else {
-                    const R s = (R)p.sh[m + n + o];
+                    const R s = par<R>(p.sh[m + n + o], p.pf.sh[m + n + o]);
                     y = (R(1) - s) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
                 }
             }
@@ -394,15 +419,15 @@ template <typename R, bool TRT = false>
 __device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
     const R u[3] = {ux, uy, uz};
     const R m0 = hd[0] + hd[1] + hd[2] + hd[3] + hd[4] + hd[5] + hd[6];
-    const R Tref = (R)p.Tref;
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
     const R dH = m0 + R(0.5) * Q;
     const R c = cs2<R>();
-    const R s1 = (R)p.sh[1];
+    const R s1 = par<R>(p.sh[1], p.pf.sh[1]);
     R y0, y1[3], y2[3];
     if constexpr (TRT) {  // orders 0 and 2 relax with rate 1
         y0 = dH + R(0.5) * Q;
     } else {
-        const R s0 = (R)p.sh[0];
+        const R s0 = par<R>(p.sh[0], p.pf.sh[0]);
         y0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
     }
 #pragma unroll
@@ -414,7 +439,7 @@ __device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const D
         if constexpr (TRT) {
             y2[d] = dH * c - Tref * u[d] * u[d] + R(0.5) * Q * c;
         } else {
-            const R s2 = (R)p.sh[2];
+            const R s2 = par<R>(p.sh[2], p.pf.sh[2]);
             const R m2 = hd[1 + d] + hd[4 + d];
             const R k2 = m2 - u[d] * (m1 + k1);
             y2[d] = (R(1) - s2) * k2 + s2 * (dH * c - Tref * u[d] * u[d]) + (R(1) - R(0.5) * s2) * Q * c;
@@ -453,9 +478,9 @@ __device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, cons
         if (EY(a) != 0) jy += EY(a) * v;
         if (EZ(a) != 0) jz += EZ(a) * v;
     }
-    const R Ht = (R)p.Tref + dH;  // zeroth moment of the stored (App. D shifted) h
+    const R Ht = par<R>(p.Tref, p.pf.Tref) + dH;  // zeroth moment of the stored (App. D shifted) h
     const R iH = R(1) / Ht;
-    const R s = (R)p.sh[1];
+    const R s = par<R>(p.sh[1], p.pf.sh[1]);
     // v = u + (1 - s)(m - u): exactly u at s = 1
     const R vx = ux + (R(1) - s) * (jx * iH - ux);
     const R vy = uy + (R(1) - s) * (jy * iH - uy);
@@ -481,7 +506,7 @@ __device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const De
 // (the density enters as its deviation, like heq_dev's zeroth moment)
 template <typename R>
 __device__ __forceinline__ void feq_dev(R* fd, R drho, R ux, R uy, R uz, const DevParams& p) {
-    const R rho0 = (R)p.rho0;
+    const R rho0 = par<R>(p.rho0, p.pf.rho0);
     const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
     R cb[27];
 #pragma unroll
@@ -500,7 +525,7 @@ __device__ __forceinline__ void feq_dev(R* fd, R drho, R ux, R uy, R uz, const D
 // its deviation dpsi, so no Tref is added and subtracted again in FP32
 template <typename R, int QH>
 __device__ __forceinline__ void heq_dev(R* hd, R dpsi, R ux, R uy, R uz, const DevParams& p) {
-    const R Tref = (R)p.Tref;
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
     if constexpr (QH == 27) {
         const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
         R cb[27];

@@ -69,11 +69,12 @@ cudaError_t launch_mirror(const Buffers& b, const DevParams& p, cudaStream_t s);
 // per-node dJ/dF, dJ/du_in accumulators)
 cudaError_t launch_reduce6(const double* acc, int n, double* out, cudaStream_t s);
 // adjoint of one level of the coupled f + h evolution (records of the level's
-// pre-collision arrivals; f_level NULL at the initial level)
+// pre-collision arrivals; f_level NULL at the initial level); wbuf: R[3][N]
+// scratch for the velocity derivative passed from the h to the f kernel
 template <typename R, int QH>
 cudaError_t launch_adjoint_flow(const Buffers& b, const DevParams& p, const R* f_level, const R* h_level,
                                 const R* muf_next, const R* muh_next, R* muf_out, R* muh_out, AdjObjective obj,
-                                double* dtheta, double* acc6, const R* din, cudaStream_t s);
+                                double* dtheta, double* acc6, const R* din, R* wbuf, cudaStream_t s);
 // rec[i * N + n] = post-collision h deviation of population i at node n (type R)
 template <typename S, int QH>
 cudaError_t launch_record_h(const Buffers& b, const DevParams& p, void* rec, cudaStream_t s);
@@ -295,9 +296,9 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
             for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
         }
         if (REC) {
-            urec[n] = (R)p.uin[0];
-            urec[N + n] = (R)p.uin[1];
-            urec[2 * N + n] = (R)p.uin[2];
+            urec[n] = par<R>(p.uin[0], p.pf.uin[0]);
+            urec[N + n] = par<R>(p.uin[1], p.pf.uin[1]);
+            urec[2 * N + n] = par<R>(p.uin[2], p.pf.uin[2]);
         }
         return;
     }
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
 #pragma unroll
     for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + i * N + src_of(nb, HDIR<QH>(i)));
     if (mask) {
-        const R Tref = (R)p.Tref;
+        const R Tref = par<R>(p.Tref, p.pf.Tref);
 #pragma unroll
         for (int ib = 0; ib < QH; ++ib) {
             const int b = HDIR<QH>(ib);
@@ -512,13 +513,13 @@ __global__ void k_macros(const S* __restrict__ fA, const S* __restrict__ hA, con
     }
 #pragma unroll
     for (int i = 0; i < QH; ++i) dh += ld<R>(hA + i * N + n);
-    const R r = (R)p.rho0 + dr;
+    const R r = par<R>(p.rho0, p.pf.rho0) + dr;
     const R Q = theta ? (R)theta[n] : R(0);
     rho[n] = (double)r;
-    u[n] = (double)((jx - R(0.5) * (R)p.F[0]) / r);
-    u[N + n] = (double)((jy - R(0.5) * (R)p.F[1]) / r);
-    u[2 * N + n] = (double)((jz - R(0.5) * (R)p.F[2]) / r);
-    T[n] = (double)(((R)p.Tref + dh - R(0.5) * Q) / r);
+    u[n] = (double)((jx - R(0.5) * par<R>(p.F[0], p.pf.F[0])) / r);
+    u[N + n] = (double)((jy - R(0.5) * par<R>(p.F[1], p.pf.F[1])) / r);
+    u[2 * N + n] = (double)((jz - R(0.5) * par<R>(p.F[2], p.pf.F[2])) / r);
+    T[n] = (double)((par<R>(p.Tref, p.pf.Tref) + dh - R(0.5) * Q) / r);
 }
 
 template <typename S, int QH>
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(kRedThreads) k_surface_flux(const S* __restric
     __shared__ double sh[32];
     double v[1] = {0.0};
     const size_t N = (size_t)p.N;
-    const R Tref = (R)p.Tref;
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
         const int n = wnode[w];
         const uint32_t mask = wmask[w];
@@ -821,7 +822,7 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
         //   mu_b = L0 + A/H sum_d ((1 - s) e_bd - (v_d - s u_d)) G_d,
         //   L0 = sum_a lambda_a M_a(v),  G_d = sum_a lambda_a dM_a/dv_d,
         // and dJ/dQ += L0.
-        R A = (R)p.Tref, jx = R(0), jy = R(0), jz = R(0);
+        R A = par<R>(p.Tref, p.pf.Tref), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
         for (int i = 0; i < QH; ++i) {
             const int a = HDIR<QH>(i);
@@ -870,7 +871,7 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
                 G[d] = lam[0] * D[d][1] + lam[1 + d] * D[d][2] + lam[4 + d] * D[d][0];
             }
         }
-        const R s = (R)p.sh[1];
+        const R s = par<R>(p.sh[1], p.pf.sh[1]);
         const R kap = A / (A - Q);
         R base = L0;
 #pragma unroll
@@ -903,7 +904,7 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
                     const R E = Eq<R>(m, nn, o);
-                    const R sr = (R)p.sh[m + nn + o];
+                    const R sr = par<R>(p.sh[m + nn + o], p.pf.sh[m + nn + o]);
                     R& v = cb[MIDX(m, nn, o)];
                     if (E != R(0)) {
                         dth += (double)(E * v);
@@ -935,7 +936,7 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
             z1[d] = mb1 + R(2) * u[d] * mb2;
             z0 += u[d] * mb1 + u[d] * u[d] * mb2;
         }
-        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+        const R s0 = par<R>(p.sh[0], p.pf.sh[0]), s1 = par<R>(p.sh[1], p.pf.sh[1]), s2 = par<R>(p.sh[2], p.pf.sh[2]);
         dth = (double)z0 + (double)(c * (z2[0] + z2[1] + z2[2]));
         const R rank = s0 * z0 + s2 * c * (z2[0] + z2[1] + z2[2]);
         z0 *= (R(1) - s0);
@@ -974,7 +975,7 @@ __device__ __forceinline__ R w1_unit(int e, R u) {
 }
 template <typename R, int QH>
 __device__ __forceinline__ void zou_he_h_transpose(R* mu, const DevParams& p) {
-    const R uy = (R)p.uin[1], uz = (R)p.uin[2];
+    const R uy = par<R>(p.uin[1], p.pf.uin[1]), uz = par<R>(p.uin[2], p.pf.uin[2]);
     R sum = R(0);
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
@@ -1159,7 +1160,7 @@ __device__ __forceinline__ T zou_he_fill_f(T* fd, T ux, T uy, T uz, const DevPar
         if (EX(a) == -1) sm += fd[a];
     }
     // the e_x = 0 and e_x = -1 weights sum to 2/3 and 1/6
-    const T drho = (s0 + T(2) * sm + (T)p.rho0 * ux) / (T(1) - ux);
+    const T drho = (s0 + T(2) * sm + par<T>(p.rho0, p.pf.rho0) * ux) / (T(1) - ux);
     T fe[27];
     feq_dev<T>(fe, drho, ux, uy, uz, p);
     T Ny = T(0), Nz = T(0);
@@ -1187,9 +1188,9 @@ __device__ __forceinline__ void zou_he_fill_h(T* hd, T drho, T ux, T uy, T uz, c
         if (EX(HDIR<QH>(k)) != 1) K += hd[k];
     // unknown deviations = h^eq(amp, u_in) - w T_ref; with damp = amp - T_ref:
     // damp (c_s^2 + u_x^2 + u_x)/2 = rho T_in - T_ref - K - T_ref (u_x^2 + u_x)/2
-    const T Tref = (T)p.Tref;
+    const T Tref = par<T>(p.Tref, p.pf.Tref);
     const T mU = T(0.5) * (cs2<T>() + ux * ux + ux);
-    const T target = drho * (T)p.Tin + (T)(p.rho0 * p.Tin - p.Tref);
+    const T target = drho * par<T>(p.Tin, p.pf.Tin) + (T)(p.rho0 * p.Tin - p.Tref);
     const T damp = (target - K - Tref * T(0.5) * (ux * ux + ux)) / mU;
     T he[QH];
     heq_dev<T, QH>(he, damp, ux, uy, uz, p);
@@ -1215,7 +1216,7 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
     if ((flags[n] & 3) != T_INLET) return;  // symmetry rows are solid on the device
     const int N = p.N;
     const Nbr nb = make_nbr(0, y, z, p);
-    const R ux = (R)p.uin[0], uy = (R)p.uin[1], uz = (R)p.uin[2];
+    const R ux = par<R>(p.uin[0], p.pf.uin[0]), uy = par<R>(p.uin[1], p.pf.uin[1]), uz = par<R>(p.uin[2], p.pf.uin[2]);
     R fd[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = (EX(a) == 1) ? R(0) : ld<R>(fA + a * N + src_of(nb, a));
@@ -1342,14 +1343,14 @@ __device__ __forceinline__ FFront<T> f_front(const T* m, const T Fx, const T Fy,
     FFront<T> o;
     const T c = cs2<T>();
     const T drho = m[0], jx = m[1], jy = m[2], jz = m[3];
-    const T rho = (T)p.rho0 + drho;
+    const T rho = par<T>(p.rho0, p.pf.rho0) + drho;
     const T irho = T(1) / rho;
     const T mux = jx * irho, muy = jy * irho, muz = jz * irho;
     const T axx = m[4] - drho * c - jx * mux;
     const T ayy = m[5] - drho * c - jy * muy;
     const T azz = m[6] - drho * c - jz * muz;
-    const T om1 = T(1) - (T)p.omega1;
-    const T omb = T(1) - (T)p.omega_bulk;
+    const T om1 = T(1) - par<T>(p.omega1, p.pf.omega1);
+    const T omb = T(1) - par<T>(p.omega_bulk, p.pf.omega_bulk);
     const T dxy = (axx - ayy) * om1, dxz = (axx - azz) * om1, tr = (axx + ayy + azz) * omb;
     o.kxy = (m[7] - jx * muy) * om1;
     o.kxz = (m[8] - jx * muz) * om1;
@@ -1376,12 +1377,12 @@ __device__ __forceinline__ void f_front_adjoint(const R* m, const DevParams& p, 
                                                 R bkxz, R bkyz, R birho, R bdrho, const R* bv, const R* bu, R* G) {
     const R c = cs2<R>();
     const R drho = m[0], jx = m[1], jy = m[2], jz = m[3];
-    const R rho = (R)p.rho0 + drho;
+    const R rho = par<R>(p.rho0, p.pf.rho0) + drho;
     const R irho = R(1) / rho;
     const R mux = jx * irho, muy = jy * irho, muz = jz * irho;
-    const R om1 = R(1) - (R)p.omega1;
-    const R omb = R(1) - (R)p.omega_bulk;
-    const R F[3] = {(R)p.F[0], (R)p.F[1], (R)p.F[2]};
+    const R om1 = R(1) - par<R>(p.omega1, p.pf.omega1);
+    const R omb = R(1) - par<R>(p.omega_bulk, p.pf.omega_bulk);
+    const R F[3] = {par<R>(p.F[0], p.pf.F[0]), par<R>(p.F[1], p.pf.F[1]), par<R>(p.F[2], p.pf.F[2])};
     // sxx = (tr + dxy + dxz)/3, syy = sxx - dxy, szz = sxx - dxz
     const R bst = bsxx + bsyy + bszz;
     const R bdxy = bst * (R(1) / R(3)) - bsyy;
@@ -1444,7 +1445,7 @@ __device__ __forceinline__ void f_front_adjoint(const R* m, const DevParams& p, 
 template <typename R, int QH>
 __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R ux, R uy, R uz, R Q,
                                                    const DevParams& p, R* w) {
-    const R Tref = (R)p.Tref;
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
     if constexpr (QH == 27) {
         R Z[27], Y[27];
 #pragma unroll
@@ -1470,7 +1471,7 @@ __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R u
             for (int n = 0; n < 3; ++n)
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    const R sr = (R)p.sh[m + n + o];
+                    const R sr = par<R>(p.sh[m + n + o], p.pf.sh[m + n + o]);
                     const R E = Eq<R>(m, n, o);
                     const R D = Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
                     const int i = MIDX(m, n, o);
@@ -1483,7 +1484,7 @@ __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R u
             for (int n = 0; n < 3; ++n)
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    const R sr = (R)p.sh[m + n + o];
+                    const R sr = par<R>(p.sh[m + n + o], p.pf.sh[m + n + o]);
                     const R zz = Z[MIDX(m, n, o)];
                     if (m >= 1) {
                         const int lo = MIDX(m - 1, n, o);
@@ -1521,7 +1522,7 @@ __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R u
         (void)z0;
         const R m0 = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
         const R dH = m0 + R(0.5) * Q;
-        const R s0 = (R)p.sh[0], s1 = (R)p.sh[1], s2 = (R)p.sh[2];
+        const R s0 = par<R>(p.sh[0], p.pf.sh[0]), s1 = par<R>(p.sh[1], p.pf.sh[1]), s2 = par<R>(p.sh[2], p.pf.sh[2]);
         const R y0 = m0, ys0 = (R(1) - s0) * m0 + s0 * dH + (R(1) - R(0.5) * s0) * Q;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1559,11 +1560,11 @@ __device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p
         if (EX(a) * EZ(a) != 0) m[8] += (EX(a) * EZ(a)) * val;
         if (EY(a) * EZ(a) != 0) m[9] += (EY(a) * EZ(a)) * val;
     }
-    const FFront<R> S = f_front<R>(m, (R)p.F[0], (R)p.F[1], (R)p.F[2], p);
+    const FFront<R> S = f_front<R>(m, par<R>(p.F[0], p.pf.F[0]), par<R>(p.F[1], p.pf.F[1]), par<R>(p.F[2], p.pf.F[2]), p);
     const R c = cs2<R>();
     const R sxx = S.sxx, syy = S.syy, szz = S.szz, kxy = S.kxy, kxz = S.kxz, kyz = S.kyz, irho = S.irho;
     const R vx = S.v[0], vy = S.v[1], vz = S.v[2];
-    const R rho0 = (R)p.rho0;
+    const R rho0 = par<R>(p.rho0, p.pf.rho0);
     // post-collision central moments kappa (as in collide_f_force)
     R K[27];
     {
@@ -1675,16 +1676,134 @@ __device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p
     f_front_adjoint<R>(m, p, bsxx, bsyy, bszz, bkxy, bkxz, bkyz, birho, bdrho, bv, w, G);
 }
 
-template <typename R, int QH, bool CUM>
+// Adjoint of the Zou-He rule at an inlet node for the coupled sweep (the
+// rule: zou_he_fill_f, zou_he_fill_h).  g, gh: the node's recorded full
+// arrival vectors (the known ones, e_x <= 0, as pulled); muf, muh: the
+// adjoints of the full arrival vectors, replaced by those of the known ones
+// (the unknown ones are pulled from nowhere: 0).  For fixed u_in the rule is
+// affine in the known arrivals, and its transpose follows the rule backwards:
+// the h amplitude damp = (rho T_in - T_ref - K - T_ref (u_x^2 + u_x)/2) / M+
+// (M+ = (c_s^2 + u_x^2 + u_x)/2, K the sum of the known h), the unknown f
+// f_a = f_abar + fe_a - fe_abar - e_ya N_y - e_za N_z with fe the equilibrium
+// at (drho, u_in) and N_d = sum_{e_x = 0} e_d (f - fe) / 6, and drho =
+// (s_0 + 2 s_- + rho0 u_x) / (1 - u_x) from the known f.  dJ/du_in
+// (accumulated into duin[3]) comes from three forward-mode passes through the
+// rule itself.
+template <typename R, int QH>
+__device__ __forceinline__ void zou_he_transpose_coupled(const R* g, const R* gh, R* muf, R* muh,
+                                                         const DevParams& p, double* duin) {
+    const R ux = par<R>(p.uin[0], p.pf.uin[0]), uy = par<R>(p.uin[1], p.pf.uin[1]), uz = par<R>(p.uin[2], p.pf.uin[2]);
+    using D = Dual<R>;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        D fd[27], hd[QH];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) fd[a] = D(EX(a) == 1 ? R(0) : g[a], R(0), 0);
+#pragma unroll
+        for (int k = 0; k < QH; ++k) hd[k] = D(EX(HDIR<QH>(k)) == 1 ? R(0) : gh[k], R(0), 0);
+        const D vx(ux, d == 0 ? R(1) : R(0), 0), vy(uy, d == 1 ? R(1) : R(0), 0), vz(uz, d == 2 ? R(1) : R(0), 0);
+        const D drho = zou_he_fill_f<D>(fd, vx, vy, vz, p);
+        zou_he_fill_h<D, QH>(hd, drho, vx, vy, vz, p);
+        R acc = R(0);
+#pragma unroll
+        for (int a = 0; a < 27; ++a)
+            if (EX(a) == 1) acc += muf[a] * fd[a].d;
+#pragma unroll
+        for (int k = 0; k < QH; ++k)
+            if (EX(HDIR<QH>(k)) == 1) acc += muh[k] * hd[k].d;
+        duin[d] += (double)acc;
+    }
+    // per-axis unit equilibrium weights at u_in (index e + 1)
+    R M[3][3];
+#pragma unroll
+    for (int e = -1; e <= 1; ++e) {
+        M[0][e + 1] = w1_unit<R>(e, ux);
+        M[1][e + 1] = w1_unit<R>(e, uy);
+        M[2][e + 1] = w1_unit<R>(e, uz);
+    }
+    const R mU = M[0][2];
+    // h: the unknown arrivals are damp M_j (+ a constant)
+    R bdamp = R(0);
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+        const int a = HDIR<QH>(k);
+        if (EX(a) != 1) continue;
+        bdamp += muh[k] * (QH == 27 ? M[0][2] * M[1][EY(a) + 1] * M[2][EZ(a) + 1] : mU);
+    }
+    const R bK = -bdamp / mU;
+    R bdrho = par<R>(p.Tin, p.pf.Tin) * bdamp / mU;
+#pragma unroll
+    for (int k = 0; k < QH; ++k) muh[k] = (EX(HDIR<QH>(k)) == 1) ? R(0) : muh[k] + bK;
+    // f: the unknown arrivals through fe (drho) and N_y, N_z
+    R bfe[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) bfe[a] = R(0);
+    R bNy = R(0), bNz = R(0);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        if (EX(a) != 1) continue;
+        const int b = OPP(a);
+        const R m = muf[a];
+        muf[b] += m;
+        bfe[a] += m;
+        bfe[b] -= m;
+        bNy -= R(EY(a)) * m;
+        bNz -= R(EZ(a)) * m;
+    }
+#pragma unroll
+    for (int c = 0; c < 27; ++c) {
+        if (EX(c) != 0) continue;
+        const R t = (R(EY(c)) * bNy + R(EZ(c)) * bNz) * (R(1) / R(6));
+        muf[c] += t;
+        bfe[c] -= t;
+    }
+#pragma unroll
+    for (int a = 0; a < 27; ++a) bdrho += bfe[a] * M[0][EX(a) + 1] * M[1][EY(a) + 1] * M[2][EZ(a) + 1];
+    const R q = bdrho / (R(1) - ux);
+#pragma unroll
+    for (int c = 0; c < 27; ++c) {
+        if (EX(c) == 0) muf[c] += q;
+        else if (EX(c) == -1) muf[c] += R(2) * q;
+        else muf[c] = R(0);
+    }
+}
+
+// velocity u of the h collision from a node's pre-collision f arrivals, as
+// collide_f_force computes it: u = (sum e f + F/2) / rho
+template <typename R>
+__device__ __forceinline__ void flow_velocity(const R* g, const DevParams& p, R& ux, R& uy, R& uz) {
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+        const R v = g[a];
+        drho += v;
+        if (EX(a) != 0) jx += EX(a) * v;
+        if (EY(a) != 0) jy += EY(a) * v;
+        if (EZ(a) != 0) jz += EZ(a) * v;
+    }
+    const R irho = R(1) / (par<R>(p.rho0, p.pf.rho0) + drho);
+    ux = jx * irho + R(0.5) * par<R>(p.F[0], p.pf.F[0]) * irho;
+    uy = jy * irho + R(0.5) * par<R>(p.F[1], p.pf.F[1]) * irho;
+    uz = jz * irho + R(0.5) * par<R>(p.F[2], p.pf.F[2]) * irho;
+}
+
+// One level of the coupled sweep in two kernels, each about half the code
+// (one kernel held both and was bound by instruction fetch): PART 1, the h
+// adjoint (gather of mu_h, transposed h collision, the velocity derivative w
+// written to wbuf[3][N], dJ/dQ, the wall-temperature terms); PART 2, the f
+// adjoint (gather of mu_f, the reversed f collision with w, dJ/dF).  PART 1
+// runs first.
+template <typename R, int QH, bool CUM, int PART>
 __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
     const R* __restrict__ muf_next, const R* __restrict__ muh_next, R* __restrict__ muf_out, R* __restrict__ muh_out,
     const R* __restrict__ gf, const R* __restrict__ gh, const float* __restrict__ theta,
-    double* __restrict__ dtheta, double* __restrict__ acc6, const R* __restrict__ din,
+    double* __restrict__ dtheta, double* __restrict__ acc6, const R* __restrict__ din, R* __restrict__ wbuf,
     const uint8_t* __restrict__ flags, const int32_t* __restrict__ seg_base, const uint32_t* __restrict__ wmask,
     const int32_t* __restrict__ woff, const float* __restrict__ lq, const int32_t* __restrict__ lwall,
     const int32_t* __restrict__ rseg_base, const uint32_t* __restrict__ rmask, const int32_t* __restrict__ roff,
     const int32_t* __restrict__ rlink, double* __restrict__ dlink, const AdjObjective obj, const DevParams p) {
     using D = Dual<R>;
+    constexpr bool HP = PART == 1, FP = PART == 2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in_range = n < p.N;
     const uint8_t fl = in_range ? flags[n] : (uint8_t)T_SOLID;
@@ -1695,10 +1814,13 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
     const int N = p.N;
     const int type = fl & 3;
     if (type == T_SOLID) {
+        if constexpr (FP) {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+            for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+        } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+            for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+        }
         return;
     }
     const int lane = threadIdx.x & 31;
@@ -1723,36 +1845,41 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
     // reversed (the row's copies, k_mirror; as in k_adjoint)
     const bool rlo = p.mirror_lo && y == 1, rhi = p.mirror_hi && y == p.ny - 2;
     // lambda = P^T mu^{k+1} (+ the objective's terms)
-    R lf[27], lh[QH];
-#pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        const int xx = xt[EX(a) + 1];
-        const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
-        const int row = refl ? y * p.nx : yt[EY(a) + 1];
-        lf[a] = (xx < 0) ? R(0) : muf_next[(refl ? FLIPY(a) : a) * N + xx + row + zt[EZ(a) + 1]];
-    }
-#pragma unroll
-    for (int i = 0; i < QH; ++i) {
-        const int a = HDIR<QH>(i);
-        const int xx = xt[EX(a) + 1];
-        const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
-        const int row = refl ? y * p.nx : yt[EY(a) + 1];
-        lh[i] = (xx < 0) ? R(0) : muh_next[(refl ? HFLIPY<QH>(i) : i) * N + xx + row + zt[EZ(a) + 1]];
-    }
-    if (!p.periodic_x && x == p.nx - 1) {
+    R lf[FP ? 27 : 1], lh[HP ? QH : 1];
+    if constexpr (FP) {
 #pragma unroll
         for (int a = 0; a < 27; ++a) {
-            if (EX(a) != -1) continue;
+            const int xx = xt[EX(a) + 1];
             const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
-            lf[a] += muf_next[(refl ? FLIPY(a) : a) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) + zt[EZ(a) + 1]];
+            const int row = refl ? y * p.nx : yt[EY(a) + 1];
+            lf[a] = (xx < 0) ? R(0) : muf_next[(refl ? FLIPY(a) : a) * N + xx + row + zt[EZ(a) + 1]];
         }
+        if (!p.periodic_x && x == p.nx - 1) {
+#pragma unroll
+            for (int a = 0; a < 27; ++a) {
+                if (EX(a) != -1) continue;
+                const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+                lf[a] += muf_next[(refl ? FLIPY(a) : a) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) + zt[EZ(a) + 1]];
+            }
+        }
+    } else {
 #pragma unroll
         for (int i = 0; i < QH; ++i) {
             const int a = HDIR<QH>(i);
-            if (EX(a) != -1) continue;
+            const int xx = xt[EX(a) + 1];
             const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
-            lh[i] += muh_next[(refl ? HFLIPY<QH>(i) : i) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) +
-                              zt[EZ(a) + 1]];
+            const int row = refl ? y * p.nx : yt[EY(a) + 1];
+            lh[i] = (xx < 0) ? R(0) : muh_next[(refl ? HFLIPY<QH>(i) : i) * N + xx + row + zt[EZ(a) + 1]];
+        }
+        if (!p.periodic_x && x == p.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < QH; ++i) {
+                const int a = HDIR<QH>(i);
+                if (EX(a) != -1) continue;
+                const bool refl = (EY(a) == -1 && rlo) || (EY(a) == 1 && rhi);
+                lh[i] += muh_next[(refl ? HFLIPY<QH>(i) : i) * N + x + (refl ? y * p.nx : yt[EY(a) + 1]) +
+                                  zt[EZ(a) + 1]];
+            }
         }
     }
     if (is_rw) {
@@ -1760,161 +1887,222 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
         const int idx = __ldg(rseg_base + (n >> 5)) + __popc(bal_r & lt);
         const uint32_t rm = __ldg(rmask + idx);
         const int ro = __ldg(roff + idx);
+        if constexpr (FP) {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) {
-            if (!(rm & (1u << a))) continue;
-            const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
-            const float q = __ldg(lq + l);
-            const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
-            const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(a, obj.comp) : R(0);
-            lf[a] += (R(1) - R(2) * (R)q) * (muf_next[OPP(a) * N + t] + cf);
-        }
+            for (int a = 0; a < 27; ++a) {
+                if (!(rm & (1u << a))) continue;
+                const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
+                const float q = __ldg(lq + l);
+                const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
+                const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(a, obj.comp) : R(0);
+                lf[a] += (R(1) - R(2) * (R)q) * (muf_next[OPP(a) * N + t] + cf);
+            }
+        } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) {
-            const int a = HDIR<QH>(i);
-            if (!(rm & (1u << a))) continue;
-            const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
-            const float q = __ldg(lq + l);
-            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
-            const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
-            lh[i] -= (R(1) - R(2) * (R)q) * (muh_next[HOPP<QH>(i) * N + t] + cw);
+            for (int i = 0; i < QH; ++i) {
+                const int a = HDIR<QH>(i);
+                if (!(rm & (1u << a))) continue;
+                const int l = __ldg(rlink + ro + __popc(rm & ((1u << a) - 1u)));
+                const float q = __ldg(lq + l);
+                const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+                const int t = xt[EX(a) + 1] + yt[EY(a) + 1] + zt[EZ(a) + 1];
+                lh[i] -= (R(1) - R(2) * (R)q) * (muh_next[HOPP<QH>(i) * N + t] + cw);
+            }
         }
     }
     if (is_wall) {
         const int idx = __ldg(seg_base + (n >> 5)) + __popc(bal_w & lt);
         const uint32_t mask = __ldg(wmask + idx);
         const int off = __ldg(woff + idx);
+        if constexpr (FP) {
 #pragma unroll
-        for (int b = 0; b < 27; ++b) {
-            if (!(mask & (1u << b))) continue;
-            const int ib = OPP(b);
-            const int l = off + __popc(mask & ((1u << b) - 1u));
-            const float q = __ldg(lq + l);
-            const bool thin = (mask >> ib) & 1u;
-            R d_ab, d_abb;
-            ibb_partials<R>(q, thin, d_ab, d_abb);
-            const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(b, obj.comp) : R(0);
-            const R m = muf_next[ib * N + n] + cf;
-            lf[b] += d_ab * m + cf;
-            lf[ib] += d_abb * m;
-        }
+            for (int b = 0; b < 27; ++b) {
+                if (!(mask & (1u << b))) continue;
+                const int ib = OPP(b);
+                const int l = off + __popc(mask & ((1u << b) - 1u));
+                const float q = __ldg(lq + l);
+                const bool thin = (mask >> ib) & 1u;
+                R d_ab, d_abb;
+                ibb_partials<R>(q, thin, d_ab, d_abb);
+                const R cf = (__ldg(lwall + l) == obj.wall) ? wforce * (R)ecomp(b, obj.comp) : R(0);
+                const R m = muf_next[ib * N + n] + cf;
+                lf[b] += d_ab * m + cf;
+                lf[ib] += d_abb * m;
+            }
+        } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) {
-            const int b = HDIR<QH>(i);
-            if (!(mask & (1u << b))) continue;
-            const int ib = HOPP<QH>(i);
-            const int l = off + __popc(mask & ((1u << b) - 1u));
-            const float q = __ldg(lq + l);
-            const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
-            const bool thin = (mask >> HDIR<QH>(ib)) & 1u;
-            R d_ab, d_abb, d_T;
-            iabb_partials<R>(q, thin, p.wall_bc, d_ab, d_abb, d_T);
-            const R m = muh_next[ib * N + n] + cw;
-            lh[i] += d_ab * m - cw;
-            lh[ib] += d_abb * m;
-            dlink[l] += (double)d_T * HW<QH>(i) * (double)m;
+            for (int i = 0; i < QH; ++i) {
+                const int b = HDIR<QH>(i);
+                if (!(mask & (1u << b))) continue;
+                const int ib = HOPP<QH>(i);
+                const int l = off + __popc(mask & ((1u << b) - 1u));
+                const float q = __ldg(lq + l);
+                const R cw = (__ldg(lwall + l) == obj.wall) ? wsurf : R(0);
+                const bool thin = (mask >> HDIR<QH>(ib)) & 1u;
+                R d_ab, d_abb, d_T;
+                iabb_partials<R>(q, thin, p.wall_bc, d_ab, d_abb, d_T);
+                const R m = muh_next[ib * N + n] + cw;
+                lh[i] += d_ab * m - cw;
+                lh[ib] += d_abb * m;
+                dlink[l] += (double)d_T * HW<QH>(i) * (double)m;
+            }
         }
     }
-    if (obj.kind == 1 && x == obj.plane) {
+    if constexpr (HP) {
+        if (obj.kind == 1 && x == obj.plane) {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) lh[i] += (R)obj.weight * (R)EX(HDIR<QH>(i));
+            for (int i = 0; i < QH; ++i) lh[i] += (R)obj.weight * (R)EX(HDIR<QH>(i));
+        }
     }
     if (!gf) {  // the initial level: its state is given; write lambda
+        if constexpr (FP) {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = lf[a];
+            for (int a = 0; a < 27; ++a) muf_out[a * N + n] = lf[a];
+        } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = lh[i];
+            for (int i = 0; i < QH; ++i) muh_out[i * N + n] = lh[i];
+        }
         return;
     }
-    if (type == T_INLET) {
+    if (type == T_INLET && !p.zou_he) {
         // the inlet holds the equilibria at u_in: din[d * (27 + QH) + .] = d s_in / d u_in,d
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
             double acc = 0.0;
+            if constexpr (FP) {
 #pragma unroll
-            for (int a = 0; a < 27; ++a) acc += (double)(din[d * (27 + QH) + a] * lf[a]);
+                for (int a = 0; a < 27; ++a) acc += (double)(din[d * (27 + QH) + a] * lf[a]);
+            } else {
 #pragma unroll
-            for (int i = 0; i < QH; ++i) acc += (double)(din[d * (27 + QH) + 27 + i] * lh[i]);
+                for (int i = 0; i < QH; ++i) acc += (double)(din[d * (27 + QH) + 27 + i] * lh[i]);
+            }
             acc6[(size_t)n * 6 + 3 + d] += acc;
         }
+        if constexpr (FP) {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+            for (int a = 0; a < 27; ++a) muf_out[a * N + n] = R(0);
+        } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+            for (int i = 0; i < QH; ++i) muh_out[i * N + n] = R(0);
+        }
         return;
     }
-    R g[27], hpre[QH];
+    R g[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) g[a] = gf[a * N + n];
+    if constexpr (HP) {
+        R hpre[QH];
 #pragma unroll
-    for (int i = 0; i < QH; ++i) hpre[i] = gh[i * N + n];
-    const R Q = theta ? (R)__ldg(theta + n) : R(0);
-    R ux, uy, uz, rho;
-    {
-        R fv[27];
-#pragma unroll
-        for (int a = 0; a < 27; ++a) fv[a] = g[a];
-        collide_f<R>(fv, p, ux, uy, uz, rho);
-    }
-    // w = (dC_h/du)^T lambda_h: reverse mode for the central-moment kinds,
-    // three forward-mode passes in u for the nonlinear Cumulants-1st
-    R w[3];
-    if constexpr (CUM) {
+        for (int i = 0; i < QH; ++i) hpre[i] = gh[i * N + n];
+        const R Q = theta ? (R)__ldg(theta + n) : R(0);
+        R ux, uy, uz;
+        flow_velocity<R>(g, p, ux, uy, uz);
+        // w = (dC_h/du)^T lambda_h: reverse mode for the central-moment kinds,
+        // three forward-mode passes in u for the nonlinear Cumulants-1st
+        R w[3];
+        if constexpr (CUM) {
 #pragma unroll 1
-        for (int k = 0; k < 3; ++k) {
-            D hd[QH];
+            for (int k = 0; k < 3; ++k) {
+                D hd[QH];
 #pragma unroll
-            for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i]);
-            const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0),
-                vz(uz, k == 2 ? R(1) : R(0), 0);
-            collide_h<D, QH, CUM>(hd, vx, vy, vz, D(Q), p);
-            R acc = R(0);
+                for (int i = 0; i < QH; ++i) hd[i] = D(hpre[i]);
+                const D vx(ux, k == 0 ? R(1) : R(0), 0), vy(uy, k == 1 ? R(1) : R(0), 0),
+                    vz(uz, k == 2 ? R(1) : R(0), 0);
+                collide_h<D, QH, CUM>(hd, vx, vy, vz, D(Q), p);
+                R acc = R(0);
 #pragma unroll
-            for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
-            w[k] = acc;
+                for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
+                w[k] = acc;
+            }
+        } else {
+            h_velocity_adjoint<R, QH>(lh, hpre, ux, uy, uz, Q, p, w);
         }
-    } else {
-        h_velocity_adjoint<R, QH>(lh, hpre, ux, uy, uz, Q, p, w);
-    }
-    // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the h-only
-    // adjoint's code; Cumulants-1st needs the post-collision state)
-    double dth = 0.0;
-    {
-        R hp[QH], mu[QH];
+        wbuf[n] = w[0];
+        wbuf[N + n] = w[1];
+        wbuf[2 * N + n] = w[2];
+        // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the
+        // h-only adjoint's code; Cumulants-1st needs the post-collision state)
+        double dth = 0.0;
+        R muh[QH], hp[QH];
         if constexpr (CUM) {
 #pragma unroll
             for (int i = 0; i < QH; ++i) hp[i] = hpre[i];
             collide_h<R, QH, true>(hp, ux, uy, uz, Q, p);
         }
-        h_collision_transpose<R, QH, CUM>(lh, hp, ux, uy, uz, Q, p, mu, dth);
+        h_collision_transpose<R, QH, CUM>(lh, hp, ux, uy, uz, Q, p, muh, dth);
+        // (a Zou-He inlet node writes the adjoint of its full arrival vector
+        // here; k_zou_he_adjoint then transposes the rule that built it)
 #pragma unroll
-        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = mu[i];
+        for (int i = 0; i < QH; ++i) muh_out[i * N + n] = muh[i];
+        if (dtheta) dtheta[n] += dth;
+    } else {
+        const R w[3] = {wbuf[n], wbuf[N + n], wbuf[2 * N + n]};
+        // G_k for the ten unit-moment perturbations (k < 10) and the force (10..12)
+        R G[13];
+        collide_f_adjoint<R>(g, p, lf, w, G);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc6[(size_t)n * 6 + d] += (double)G[10 + d];
+#pragma unroll
+        for (int b = 0; b < 27; ++b) {
+            const R ex = (R)EX(b), ey = (R)EY(b), ez = (R)EZ(b);
+            muf_out[b * N + n] = G[0] + ex * G[1] + ey * G[2] + ez * G[3] + ex * ex * G[4] + ey * ey * G[5] +
+                                 ez * ez * G[6] + ex * ey * G[7] + ex * ez * G[8] + ey * ez * G[9];
+        }
     }
-    // G_k for the ten unit-moment perturbations (k < 10) and the force (10..12)
-    R G[13];
-    collide_f_adjoint<R>(g, p, lf, w, G);
+}
+
+// The Zou-He transpose of every inlet node of a level of the coupled sweep,
+// after k_adjoint_flow (one thread per inlet node, in place; it would raise
+// the register count of the whole sweep kernel if done there)
+template <typename R, int QH>
+__global__ void __launch_bounds__(kBlock) k_zou_he_adjoint(R* __restrict__ muf, R* __restrict__ muh,
+                                                            const R* __restrict__ gf, const R* __restrict__ gh,
+                                                            const uint8_t* __restrict__ flags,
+                                                            double* __restrict__ acc6, const DevParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.ny * p.nz) return;
+    const int n = p.nx * i;  // x = 0, row i = y + ny z
+    if ((flags[n] & 3) != T_INLET) return;
+    const int N = p.N;
+    R g[27], h[QH], mf[27], mh[QH];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) acc6[(size_t)n * 6 + d] += (double)G[10 + d];
-#pragma unroll
-    for (int b = 0; b < 27; ++b) {
-        const R ex = (R)EX(b), ey = (R)EY(b), ez = (R)EZ(b);
-        muf_out[b * N + n] = G[0] + ex * G[1] + ey * G[2] + ez * G[3] + ex * ex * G[4] + ey * ey * G[5] +
-                             ez * ez * G[6] + ex * ey * G[7] + ex * ez * G[8] + ey * ez * G[9];
+    for (int a = 0; a < 27; ++a) {
+        g[a] = gf[a * N + n];
+        mf[a] = muf[a * N + n];
     }
-    if (dtheta) dtheta[n] += dth;
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+        h[k] = gh[k * N + n];
+        mh[k] = muh[k * N + n];
+    }
+    zou_he_transpose_coupled<R, QH>(g, h, mf, mh, p, acc6 + (size_t)n * 6 + 3);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) muf[a * N + n] = mf[a];
+#pragma unroll
+    for (int k = 0; k < QH; ++k) muh[k * N + n] = mh[k];
 }
 
 template <typename R, int QH>
 cudaError_t launch_adjoint_flow(const Buffers& b, const DevParams& p, const R* f_level, const R* h_level,
                                 const R* muf_next, const R* muh_next, R* muf_out, R* muh_out, AdjObjective obj,
-                                double* dtheta, double* acc6, const R* din, cudaStream_t s) {
+                                double* dtheta, double* acc6, const R* din, R* wbuf, cudaStream_t s) {
     const int grid = (p.N + kBlock - 1) / kBlock;
 #define LBM_ADJF_ARGS                                                                                            \
-    muf_next, muh_next, muf_out, muh_out, f_level, h_level, b.theta, dtheta, acc6, din, b.flags, b.seg_base,    \
-        b.wmask, b.woff, b.lq, b.lwall, b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p
-    if (p.hkind == 3) k_adjoint_flow<R, QH, true><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
-    else k_adjoint_flow<R, QH, false><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+    muf_next, muh_next, muf_out, muh_out, f_level, h_level, b.theta, dtheta, acc6, din, wbuf, b.flags,          \
+        b.seg_base, b.wmask, b.woff, b.lq, b.lwall, b.rseg_base, b.rmask, b.roff, b.rlink, b.dlink, obj, p
+    if (p.hkind == 3) {
+        k_adjoint_flow<R, QH, true, 1><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+        k_adjoint_flow<R, QH, true, 2><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+    } else {
+        k_adjoint_flow<R, QH, false, 1><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+        k_adjoint_flow<R, QH, false, 2><<<grid, kBlock, 0, s>>>(LBM_ADJF_ARGS);
+    }
 #undef LBM_ADJF_ARGS
+    if (p.zou_he && f_level) {
+        const int rows = p.ny * p.nz;
+        k_zou_he_adjoint<R, QH><<<(rows + kBlock - 1) / kBlock, kBlock, 0, s>>>(muf_out, muh_out, f_level, h_level,
+                                                                              b.flags, acc6, p);
+    }
     return cudaGetLastError();
 }
 

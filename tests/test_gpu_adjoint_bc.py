@@ -6,9 +6,9 @@ differences of J in test_oracle_adjoint_bc):
 * the h adjoint (lbm_adjoint_step / lbm_adjoint_step_h) with symmetry rows,
   with the Zou-He inlet and with both, for the central-moment kinds on both
   lattices and for Cumulants-1st;
-* the coupled f + h adjoint (lbm_adjoint_flow_step) with symmetry rows
-  (gradients with respect to theta, T_w and F), and its refusal of the
-  Zou-He inlet.
+* the coupled f + h adjoint (lbm_adjoint_flow_step) with the same three
+  boundary sets: gradients with respect to theta, T_w, F and (with the
+  Zou-He inlet) u_in.
 
 Tolerances as in test_gpu_adjoint and test_gpu_flow_adjoint: FP64 storage
 to 1e-9 (h adjoint) or 1e-8 (coupled) of the largest entry, FP32 to 1e-4;
@@ -79,10 +79,11 @@ def test_h_adjoint_with_boundary_rules_matches_oracle(storage, bc, qh, kind, obj
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["mirror", "zou_he", "both"])
 @pytest.mark.parametrize("qh,kind,obj", [(27, "trt", ("surface", 0, 1.0)), (27, "trt", ("force", 0, 1.0, 0)),
                                          (7, "cum1st", ("force", 0, 1.0, 1))])
-def test_coupled_adjoint_with_symmetry_rows_matches_oracle(storage, qh, kind, obj):
-    w, p = _case("mirror", qh, kind, ny=10)
+def test_coupled_adjoint_with_boundary_rules_matches_oracle(storage, bc, qh, kind, obj):
+    w, p = _case(bc, qh, kind, ny=10)
     Tw = 0.9
     s = _solver(w, p, storage, Tw)
     f0, h0 = s.populations()
@@ -94,22 +95,14 @@ def test_coupled_adjoint_with_symmetry_rows_matches_oracle(storage, qh, kind, ob
         assert abs(Jg - Jo) <= (1e-10 if storage == "f64" else 1e-6) * abs(obj[2]) * (WINDOW[1] - WINDOW[0])
     else:
         assert abs(Jg - Jo) <= (1e-10 if storage == "f64" else 1e-6) * max(abs(Jo), 1e-3)
-    assert np.abs(dF_g - dF_o).max() <= tol * max(np.abs(dF_o).max(), 1e-12)
-    assert np.all(du_g == 0.0) and np.all(du_o == 0.0)
+    scale = max(np.abs(dF_o).max(), np.abs(du_o).max())
+    assert np.abs(dF_g - dF_o).max() <= tol * scale
+    if bc == "mirror":
+        assert np.all(du_g == 0.0) and np.all(du_o == 0.0)
+    else:
+        assert np.abs(du_g - du_o).max() <= tol * scale, (du_g, du_o)
+        assert np.abs(du_o).max() > 1e-3 * scale  # the inlet velocity matters
     if obj[0] == "surface":
         assert np.abs(dth_g - dth_o).max() <= tol * np.abs(dth_o).max()
         assert np.abs(dTw_g - dTw_o).max() <= tol * max(np.abs(dTw_o).max(), 1e-12)
-    s.close()
-
-
-def test_coupled_adjoint_refuses_the_zou_he_inlet():
-    import torch
-    from paper_2203_01316_gb300 import LBMError
-    w, p = _case("zou_he", 27, "trt", ny=10)
-    s = _solver(w, p, "f32", 0.9)
-    N = s.N
-    z = torch.zeros(27 * N, dtype=torch.float32, device="cuda")
-    out_f, out_h = torch.empty_like(z), torch.empty_like(z)
-    with pytest.raises(LBMError):
-        s.adjoint_flow_step(None, None, z, z, out_f, out_h)
     s.close()

@@ -25,7 +25,7 @@ def _calls(s, w, torch):
     mu = torch.zeros(27 * N, dtype=torch.float32, device="cuda")
     out = torch.empty_like(mu)
     return [
-        ("geometry", lambda: s.set_geometry(w["flags"], w["links"], n_walls=1)),
+        ("geometry", lambda: s.set_geometry(w["flags"], w["links"], n_walls=w["nwalls"])),
         ("source", lambda: s.set_source(w["theta"].astype(np.float32))),
         ("init", lambda: s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])),
         ("step", lambda: s.step(2)),
