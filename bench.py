@@ -817,7 +817,7 @@ def validation_confined(args):
                 for order, bc in (("1st", "eq"), ("2nd", "iabb")):
                     if args.orders and order not in args.orders.split(","):
                         continue
-                    r = confined_nu(S, kind, bc, Pr, inlet_bc=args.inlet)
+                    r = confined_nu(S, kind, bc, Pr, inlet_bc=args.inlet, max_flow_throughs=args.flow_throughs)
                     r.update({"S": S, "Pr": Pr, "kernel": kind, "bc_order": order})
                     out.append(r)
                     print("# " + json.dumps(r), file=sys.stderr, flush=True)
@@ -942,6 +942,8 @@ def main():
     ap.add_argument("--validation", choices=["cylinders", "hill", "confined"],
                     help="run one of the paper's validation workloads on the GPU path")
     ap.add_argument("--sizes", default="", help="validation: comma-separated D (cylinders) or k (hill)")
+    ap.add_argument("--flow-throughs", type=float, default=4.0,
+                    help="validation confined: stop after this many flow-through times L/U at most")
     ap.add_argument("--nusselt-study", action="store_true",
                     help="heated sphere 192x64x64 at Pr 10, 100, 1000 (--prs): mean Nu after --steps steps")
     ap.add_argument("--workload", choices=["sphere", "porous"], default="sphere",

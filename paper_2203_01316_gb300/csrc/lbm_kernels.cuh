@@ -804,6 +804,51 @@ __device__ __forceinline__ void iabb_partials(float q, bool thin, int wall_bc, R
     }
 }
 
+// Pieces of the D3Q27 central-moment transposes, shared by the h-only and
+// the coupled adjoint: cube slots of z = T(u)^-T lambda (from the cube of
+// lambda) and mu = L(u)^T lambda from z (Eq. H_cm_collision transposed: the
+// per-order relaxation, the rank-one equilibrium term, then T(u)^T).
+template <typename R> __device__ __forceinline__ void z_from_lambda27(R* cb, R ux, R uy, R uz) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+    for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx) inv3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+}
+template <typename R>
+__device__ __forceinline__ void transpose_from_z27(R* cb, R ux, R uy, R uz, const DevParams& p, R* mu,
+                                                   double& dth) {
+    R rank = R(0);
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int nn = 0; nn < 3; ++nn)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const R E = Eq<R>(m, nn, o);
+                const R sr = par<R>(p.sh[m + nn + o], p.pf.sh[m + nn + o]);
+                R& v = cb[MIDX(m, nn, o)];
+                if (E != R(0)) {
+                    dth += (double)(E * v);
+                    rank += E * sr * v;
+                }
+                v *= (R(1) - sr);
+            }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) fwd3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
+#pragma unroll
+    for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx) fwd3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) fwd3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) mu[a] = cb[CUBE(a)] + rank;
+}
+
 // The transposed Jacobian of one node's h collision at velocity u (fixed):
 // mu = (dC_h/dg)^T lambda and dth = (dC_h/dQ)^T lambda.  Central-moment kinds:
 // C_h = L(u) g + e(u) Q (Eq. H_cm_collision, App. D source), transposed
@@ -887,41 +932,8 @@ __device__ __forceinline__ void h_collision_transpose(const R* lam, const R* hpo
         R cb[27];
 #pragma unroll
         for (int a = 0; a < 27; ++a) cb[CUBE(a)] = lam[a];
-        // z = T^-T lambda
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
-#pragma unroll
-        for (int zz = 0; zz < 3; ++zz)
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) inv3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
-        R rank = R(0);
-#pragma unroll
-        for (int o = 0; o < 3; ++o)
-#pragma unroll
-            for (int nn = 0; nn < 3; ++nn)
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const R E = Eq<R>(m, nn, o);
-                    const R sr = par<R>(p.sh[m + nn + o], p.pf.sh[m + nn + o]);
-                    R& v = cb[MIDX(m, nn, o)];
-                    if (E != R(0)) {
-                        dth += (double)(E * v);
-                        rank += E * sr * v;
-                    }
-                    v *= (R(1) - sr);
-                }
-#pragma unroll
-        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[3 * j], cb[3 * j + 1], cb[3 * j + 2], ux);
-#pragma unroll
-        for (int zz = 0; zz < 3; ++zz)
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) fwd3T<R>(cb[9 * zz + xx], cb[9 * zz + 3 + xx], cb[9 * zz + 6 + xx], uy);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) fwd3T<R>(cb[j], cb[9 + j], cb[18 + j], uz);
-#pragma unroll
-        for (int a = 0; a < 27; ++a) mu[a] = cb[CUBE(a)] + rank;
+        z_from_lambda27<R>(cb, ux, uy, uz);
+        transpose_from_z27<R>(cb, ux, uy, uz, p, mu, dth);
     } else {
         // D3Q7: moments 000, 100/010/001, 200/020/002
         const R u[3] = {ux, uy, uz};
@@ -1442,25 +1454,15 @@ __device__ __forceinline__ void f_front_adjoint(const R* m, const DevParams& p, 
 // stored shift T_ref K(u) of the central moments gives S_d K, so
 //   dC_h/du_d = T^-1 (S_d Y* - (1 - S) S_d Y + S T_ref S_d K)
 // and w_d = z . (S_d Y* - (1 - S) S_d Y + S T_ref S_d K).
-template <typename R, int QH>
-__device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R ux, R uy, R uz, R Q,
-                                                   const DevParams& p, R* w) {
+// w from z = T(u)^-T lambda in cube slots (D3Q27)
+template <typename R>
+__device__ __forceinline__ void velocity_from_z27(const R* Z, const R* g, R ux, R uy, R uz, R Q, const DevParams& p,
+                                                  R* w) {
     const R Tref = par<R>(p.Tref, p.pf.Tref);
-    if constexpr (QH == 27) {
-        R Z[27], Y[27];
+    {
+        R Y[27];
 #pragma unroll
-        for (int a = 0; a < 27; ++a) {
-            Z[CUBE(a)] = lam[a];
-            Y[CUBE(a)] = g[a];
-        }
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(Z[3 * j], Z[3 * j + 1], Z[3 * j + 2], ux);
-#pragma unroll
-        for (int zz = 0; zz < 3; ++zz)
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) inv3T<R>(Z[9 * zz + xx], Z[9 * zz + 3 + xx], Z[9 * zz + 6 + xx], uy);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) inv3T<R>(Z[j], Z[9 + j], Z[18 + j], uz);
+        for (int a = 0; a < 27; ++a) Y[CUBE(a)] = g[a];
         forward_cube<R>(Y, ux, uy, uz);
         const R dH = Y[0] + R(0.5) * Q;
         const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
@@ -1505,6 +1507,19 @@ __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R u
         w[0] = acc[0];
         w[1] = acc[1];
         w[2] = acc[2];
+    }
+}
+
+template <typename R, int QH>
+__device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R ux, R uy, R uz, R Q,
+                                                   const DevParams& p, R* w) {
+    const R Tref = par<R>(p.Tref, p.pf.Tref);
+    if constexpr (QH == 27) {
+        R Z[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) Z[CUBE(a)] = lam[a];
+        z_from_lambda27<R>(Z, ux, uy, uz);
+        velocity_from_z27<R>(Z, g, ux, uy, uz, Q, p, w);
     } else {
         // D3Q7: moments 0, 1d, 2d about u; S_d takes 0 -> 1d and 1d -> 2d (x2)
         const R u[3] = {ux, uy, uz};
@@ -1533,6 +1548,26 @@ __device__ __forceinline__ void h_velocity_adjoint(const R* lam, const R* g, R u
                    z2[d] * R(2) * (ys1 - (R(1) - s2) * k1 - s2 * Tref * u[d]);
         }
         (void)c;
+    }
+}
+
+// mu_h, dJ/dQ and w of a central-moment kind, z = T(u)^-T lambda computed
+// once for both (D3Q27; D3Q7 forms z in a few operations and calls the two
+// functions)
+template <typename R, int QH>
+__device__ __forceinline__ void h_transpose_and_velocity(const R* lam, const R* g, R ux, R uy, R uz, R Q,
+                                                         const DevParams& p, R* mu, double& dth, R* w) {
+    if constexpr (QH == 27) {
+        R Z[27];
+#pragma unroll
+        for (int a = 0; a < 27; ++a) Z[CUBE(a)] = lam[a];
+        z_from_lambda27<R>(Z, ux, uy, uz);
+        velocity_from_z27<R>(Z, g, ux, uy, uz, Q, p, w);
+        dth = 0.0;
+        transpose_from_z27<R>(Z, ux, uy, uz, p, mu, dth);
+    } else {
+        h_velocity_adjoint<R, QH>(lam, g, ux, uy, uz, Q, p, w);
+        h_collision_transpose<R, QH, false>(lam, nullptr, ux, uy, uz, Q, p, mu, dth);
     }
 }
 
@@ -2014,22 +2049,24 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
                 for (int i = 0; i < QH; ++i) acc += lh[i] * hd[i].d;
                 w[k] = acc;
             }
+        }
+        // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the
+        // h-only adjoint's code; Cumulants-1st needs the post-collision
+        // state); the central-moment kinds get w from the same z
+        double dth = 0.0;
+        R muh[QH];
+        if constexpr (CUM) {
+            R hp[QH];
+#pragma unroll
+            for (int i = 0; i < QH; ++i) hp[i] = hpre[i];
+            collide_h<R, QH, true>(hp, ux, uy, uz, Q, p);
+            h_collision_transpose<R, QH, CUM>(lh, hp, ux, uy, uz, Q, p, muh, dth);
         } else {
-            h_velocity_adjoint<R, QH>(lh, hpre, ux, uy, uz, Q, p, w);
+            h_transpose_and_velocity<R, QH>(lh, hpre, ux, uy, uz, Q, p, muh, dth, w);
         }
         wbuf[n] = w[0];
         wbuf[N + n] = w[1];
         wbuf[2 * N + n] = w[2];
-        // mu_h = (dC_h/dg_h)^T lambda_h and dJ/dQ, transposed exactly (the
-        // h-only adjoint's code; Cumulants-1st needs the post-collision state)
-        double dth = 0.0;
-        R muh[QH], hp[QH];
-        if constexpr (CUM) {
-#pragma unroll
-            for (int i = 0; i < QH; ++i) hp[i] = hpre[i];
-            collide_h<R, QH, true>(hp, ux, uy, uz, Q, p);
-        }
-        h_collision_transpose<R, QH, CUM>(lh, hp, ux, uy, uz, Q, p, muh, dth);
         // (a Zou-He inlet node writes the adjoint of its full arrival vector
         // here; k_zou_he_adjoint then transposes the rule that built it)
 #pragma unroll
