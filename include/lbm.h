@@ -101,10 +101,16 @@ typedef enum { LBM_INLET_EQUILIBRIUM = 0, LBM_INLET_ZOU_HE = 1 } lbm_inlet_bc;
  * at q = 1/2). */
 typedef enum { LBM_WALL_IBB_IABB = 0, LBM_WALL_BB_EQ = 1, LBM_WALL_BB_ABB = 2 } lbm_wall_bc;
 
-/* Implementation of lbm_step.  Both values run the one-node-per-thread
- * kernel (the fastest measured on GB300: the step sits near the SM issue
- * limit and gains from the warps its 96-register cap keeps resident); the
- * field is kept for choosing among implementations. */
+/* Implementation of lbm_step.  Both run the one-node-per-thread kernel (the
+ * fastest measured on GB300: the step sits near the SM issue limit and gains
+ * from the warps its 96-register cap keeps resident).  LBM_STEP_AUTO replays
+ * a CUDA graph of two steps for calls of 4 or more steps (captured on the
+ * context's stream at first use and again whenever the buffers or
+ * parameters it captured change; not for stochastically rounded 16-bit
+ * storage, whose rounding follows the step count), which removes the launch
+ * gaps that dominate small grids; results are bit-identical to
+ * LBM_STEP_CLASSIC, which launches every step.  While the caller is
+ * capturing the context's stream, lbm_step launches every step. */
 typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1 } lbm_step_kernel;
 
 /* Create a context and allocate its device state.  The populations are zero

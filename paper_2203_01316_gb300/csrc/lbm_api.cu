@@ -64,6 +64,16 @@ struct lbm_ctx {
     // memory without allocating
     long fault_alloc = 0;
     long n_alloc = 0;
+    // CUDA graphs of two plain steps (lbm_step, LBM_STEP_AUTO): replayed
+    // while the launches they captured stay the same, i.e. while buffers()
+    // and dp (but for its step counter) match what was captured
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        lbmd::Buffers b{};
+        lbmd::DevParams p{};
+    } graphs[2];
+    int graph_next = 0;
+    bool graph_broken = false;  // capture failed once: plain launches from then on
 };
 
 static std::string g_create_err;
@@ -384,6 +394,8 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_flowacc);
     cudaFree(c->d_din);
     cudaFree(c->d_wflow);
+    for (auto& gr : c->graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
@@ -758,25 +770,96 @@ static cudaError_t fill_mirror(lbm_ctx* c, const Buffers& b, const DevParams& p)
     });
 }
 
+// the launches of one plain step (symmetry rows, the step, the Zou-He inlet)
+static lbm_status step_once(lbm_ctx* c) {
+    const Buffers b = buffers(c);
+    c->dp.step += 1;
+    const DevParams p = c->dp;
+    cudaError_t e;
+    if ((e = fill_mirror(c, b, p)) != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
+    e = dispatch(c, [&](auto tag) {
+        using Tg = decltype(tag);
+        return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    if ((e = zou_he_inlet(c, b, p, true)) != cudaSuccess) return cuda_fail(c, e, "inlet launch");
+    c->cur_f = 1 - c->cur_f;
+    c->cur_h = 1 - c->cur_h;
+    return LBM_OK;
+}
+
+// A graph of two plain steps for the current buffers and parameters
+// (captured on first use, cached in two slots), or nullptr when none can be
+// had (the stream is being captured by the caller, or capture failed).  Two
+// steps bring the A/B buffers back to the same roles, so the graph replays
+// as long as the signature matches; the step counter is not part of it, so
+// graphs serve only storage whose kernels ignore that counter (everything
+// but stochastically rounded 16-bit storage).
+static lbm_ctx::StepGraph* step_graph(lbm_ctx* c) {
+    lbm_ctx::StepGraph key;
+    key.b = buffers(c);
+    key.p = c->dp;
+    key.p.step = 0;
+    for (auto& gr : c->graphs)
+        if (gr.exec && std::memcmp(&gr.b, &key.b, sizeof key.b) == 0 && std::memcmp(&gr.p, &key.p, sizeof key.p) == 0)
+            return &gr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const int cf = c->cur_f, ch = c->cur_h;
+    const uint32_t step = c->dp.step;
+    const std::string err = c->err;
+    cudaGraph_t graph = nullptr;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = step_once(c);
+        if (st == LBM_OK) st = step_once(c);
+        e = cudaStreamEndCapture(c->stream, &graph);
+    }
+    // the captured launches did not run: undo their bookkeeping
+    c->cur_f = cf;
+    c->cur_h = ch;
+    c->dp.step = step;
+    c->err = err;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && st == LBM_OK && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || st != LBM_OK || !exec) {
+        cudaGetLastError();
+        c->graph_broken = true;
+        return nullptr;
+    }
+    lbm_ctx::StepGraph& slot = c->graphs[c->graph_next];
+    c->graph_next ^= 1;
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    slot = key;
+    slot.exec = exec;
+    return &slot;
+}
+
 lbm_status lbm_step(lbm_ctx* c, int n) {
     if (!c) return LBM_ERR_INVALID;
     if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
     DeviceGuard g(c->device);
+    // launch-bound stretches replay graphs of two steps (LBM_STEP_AUTO)
+    const bool graphs = c->p.step_kernel == LBM_STEP_AUTO && !c->graph_broken && n >= 4 &&
+                        !(c->ssize == 2 && c->dp.stochastic);
+    if (graphs) {
+        while (n >= 2) {
+            lbm_ctx::StepGraph* gr = step_graph(c);
+            if (!gr) break;
+            CK(cudaGraphLaunch(gr->exec, c->stream), "step graph launch");
+            c->dp.step += 2;
+            n -= 2;
+        }
+    }
     for (int i = 0; i < n; ++i) {
-        const Buffers b = buffers(c);
-        c->dp.step += 1;
-        const DevParams p = c->dp;
-        cudaError_t e;
-        if ((e = fill_mirror(c, b, p)) != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
-        e = dispatch(c, [&](auto tag) {
-            using Tg = decltype(tag);
-            return lbmd::launch_step<typename Tg::S, Tg::Q>(b, p, c->stream);
-        });
-        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
-        if ((e = zou_he_inlet(c, b, p, true)) != cudaSuccess) return cuda_fail(c, e, "inlet launch");
-        c->cur_f = 1 - c->cur_f;
-        c->cur_h = 1 - c->cur_h;
+        const lbm_status st = step_once(c);
+        if (st != LBM_OK) return st;
     }
     return LBM_OK;
 }
