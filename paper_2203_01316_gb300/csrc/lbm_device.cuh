@@ -85,19 +85,20 @@ __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v)
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
 // Random bits of the stochastic rounding of one node's 16-bit stores: a
-// strong hash of (node, array, time level) seeds a linear congruential
-// sequence (Numerical Recipes constants) that advances once per pair of
-// stores.  Reproducible, and one multiply-add per draw.
+// strong hash of (node, array, time level) starts a Weyl sequence (the
+// golden-ratio increment 0x9E3779B9) that advances once per pair of stores.
+// Each draw is uniform because its start is; reproducible, one add per draw.
 struct SrStream {
     uint32_t s;
     __device__ __forceinline__ uint32_t next() {
-        s = s * 1664525u + 1013904223u;
-        return s;
+        const uint32_t r = s;
+        s += 0x9E3779B9u;
+        return r;
     }
 };
 
 // counter-based 32-bit hash (the "lowbias32" integer mixer of C. Wellons) of
-// (node and array, time level): the seed of a node's SrStream
+// (node and array, time level): the start of a node's SrStream
 __device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t step) {
     uint32_t x = key ^ (step * 0x9E3779B9u);
     x ^= x >> 16;
@@ -235,6 +236,78 @@ template <typename R> __device__ __forceinline__ void inverse_cube(R* c, R vx, R
     for (int j = 0; j < 9; ++j) inv3<R>(c[3 * j], c[3 * j + 1], c[3 * j + 2], vx);
 }
 
+// The same inverse in six operations per three-point group instead of
+// eight.  With k2 entering halved, g+ = k2/2 + (v + 1/2) k1 + v(v + 1)/2 k0,
+// g- = k2/2 + (v - 1/2) k1 + v(v - 1)/2 k0 and g0 = k0 - g+ - g- (the raw
+// moments g+ + g- = k2 + 2 v k1 + v^2 k0 and g+ - g- = k1 + v k0 of the
+// shifted transform).  The caller fills the cube with every moment scaled by
+// 2^-(number of its indices equal to 2): each pass is linear and leaves the
+// other indices alone, so every later pass also receives its index-2 slots
+// halved.
+template <typename R> struct InvAxis {
+    R p1, p0, m1, m0;
+};
+template <typename R> __device__ __forceinline__ InvAxis<R> inv_axis(R v) {
+    const R hv = R(0.5) * v;
+    return {v + R(0.5), hv * v + hv, v - R(0.5), hv * v - hv};
+}
+template <typename R> __device__ __forceinline__ void inv3h(R& a, R& b, R& c, const InvAxis<R>& k) {
+    const R gp = c + k.p1 * b + k.p0 * a;
+    const R gm = c + k.m1 * b + k.m0 * a;
+    b = a - gp - gm;
+    a = gm;
+    c = gp;
+}
+template <typename R> __device__ __forceinline__ void inverse_cube_h(R* c, R vx, R vy, R vz) {
+    const InvAxis<R> kx = inv_axis(vx), ky = inv_axis(vy), kz = inv_axis(vz);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3h<R>(c[j], c[9 + j], c[18 + j], kz);
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) inv3h<R>(c[9 * z + x], c[9 * z + 3 + x], c[9 * z + 6 + x], ky);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) inv3h<R>(c[3 * j], c[3 * j + 1], c[3 * j + 2], kx);
+}
+
+// E and D scaled by 2^-(indices equal to 2), for inverse_cube_h.  Every
+// index-2 factor of E and of K is c_s^2 + v^2 (E: v = 0), so the scaled forms
+// are E and D with c_s^2 and v^2 both halved: hx = vx^2 / 2 etc.
+template <typename R> __device__ __forceinline__ constexpr R cs2h() { return R(1.0 / 6.0); }
+template <typename R> __device__ __forceinline__ R Eqh(int m, int n, int o) {
+    using T = typename ScalarOf<R>::type;
+    if (m == 1 || n == 1 || o == 1) return R(0);
+    T v = T(1);
+    if (m == 2) v *= cs2h<T>();
+    if (n == 2) v *= cs2h<T>();
+    if (o == 2) v *= cs2h<T>();
+    return R(v);
+}
+template <typename R> __device__ __forceinline__ R Kdh(int m, R v, R h) {
+    return m == 0 ? R(1) : (m == 1 ? -v : cs2h<R>() + h);
+}
+template <typename R>
+__device__ __forceinline__ R Dmh(int m, int n, int o, R vx, R vy, R vz, R hx, R hy, R hz) {
+    if (m == 1 || n == 1 || o == 1) return -(Kdh<R>(m, vx, hx) * Kdh<R>(n, vy, hy) * Kdh<R>(o, vz, hz));
+    const R c = cs2h<R>();
+    const R a = (m == 2) ? hx : R(0);
+    const R b = (n == 2) ? hy : R(0);
+    const R d = (o == 2) ? hz : R(0);
+    const int cnt = (m == 2) + (n == 2) + (o == 2);
+    if (cnt == 0) return R(0);
+    if (cnt == 1) return -(a + b + d);
+    if (cnt == 2) {
+        const R p = (m == 2) ? a : b;
+        const R q = (o == 2) ? d : b;
+        return -(c * (p + q) + p * q);
+    }
+    return -(c * c * (a + b + d) + c * (a * b + a * d + b * d) + a * b * d);
+}
+// 2^-(indices equal to 2) for slot mno
+__host__ __device__ __forceinline__ constexpr double HALVES(int m, int n, int o) {
+    return (m == 2 ? 0.5 : 1.0) * (n == 2 ? 0.5 : 1.0) * (o == 2 ? 0.5 : 1.0);
+}
+
 // ---- parameters -------------------------------------------------------------
 struct DevParams {
     int nx, ny, nz, N, periodic_x;
@@ -270,6 +343,45 @@ inline void sync_float_params(DevParams& d) {
     d.pf.Tin = (float)d.Tin;
 }
 
+// ---- raw moments of order <= 2 of 27 populations -------------------------
+// Sums along x, then y, then z over the 3x3x3 cube, keeping only what the
+// ten moments need (66 additions instead of the 171 of summing each
+// population into each moment)
+template <typename R>
+__device__ __forceinline__ void raw_moments_f(const R* fd, R& m000, R& m100, R& m010, R& m001, R& m200, R& m020,
+                                              R& m002, R& m110, R& m101, R& m011) {
+    R X0[9], X1[9], X2[9];  // x moments 0, 1, 2 of the line (y, z) = (j % 3 - 1, j / 3 - 1)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const int ey = j % 3 - 1, ez = j / 3 - 1;
+        const R a = fd[DIR(-1, ey, ez)], b = fd[DIR(0, ey, ez)], c = fd[DIR(1, ey, ez)];
+        X2[j] = a + c;
+        X1[j] = c - a;
+        X0[j] = X2[j] + b;
+    }
+    R Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];  // [z]: x moment, y moment
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int j = 3 * k;
+        Y02[k] = X0[j] + X0[j + 2];
+        Y01[k] = X0[j + 2] - X0[j];
+        Y00[k] = Y02[k] + X0[j + 1];
+        Y11[k] = X1[j + 2] - X1[j];
+        Y10[k] = X1[j] + X1[j + 1] + X1[j + 2];
+        Y20[k] = X2[j] + X2[j + 1] + X2[j + 2];
+    }
+    m002 = Y00[0] + Y00[2];
+    m001 = Y00[2] - Y00[0];
+    m000 = m002 + Y00[1];
+    m010 = Y01[0] + Y01[1] + Y01[2];
+    m011 = Y01[2] - Y01[0];
+    m020 = Y02[0] + Y02[1] + Y02[2];
+    m100 = Y10[0] + Y10[1] + Y10[2];
+    m101 = Y10[2] - Y10[0];
+    m110 = Y11[0] + Y11[1] + Y11[2];
+    m200 = Y20[0] + Y20[1] + Y20[2];
+}
+
 // ---- f: cumulant collision (Eq. hydro_cu_collision) ----------------------
 // fd: pulled deviations in, post-collision deviations out.  Second-order
 // cumulants relax with omega1 (off-diagonal, deviators) and omega_bulk
@@ -282,18 +394,8 @@ inline void sync_float_params(DevParams& d) {
 template <typename R>
 __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const R Fx, const R Fy, const R Fz, R& ux,
                                                 R& uy, R& uz, R& rho_out) {
-    R drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
-#pragma unroll
-    for (int a = 0; a < 27; ++a) {
-        const R v = fd[a];
-        drho += v;
-        if (EX(a) != 0) { jx += EX(a) * v; mxx += v; }
-        if (EY(a) != 0) { jy += EY(a) * v; myy += v; }
-        if (EZ(a) != 0) { jz += EZ(a) * v; mzz += v; }
-        if (EX(a) * EY(a) != 0) mxy += (EX(a) * EY(a)) * v;
-        if (EX(a) * EZ(a) != 0) mxz += (EX(a) * EZ(a)) * v;
-        if (EY(a) * EZ(a) != 0) myz += (EY(a) * EZ(a)) * v;
-    }
+    R drho, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz;
+    raw_moments_f<R>(fd, drho, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz);
     const R c = cs2<R>();
     const R rho0 = par<R>(p.rho0, p.pf.rho0);
     const R rho = rho0 + drho;
@@ -323,20 +425,26 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
     uy = muy + R(0.5) * Fy * irho;
     uz = muz + R(0.5) * Fz * irho;
     rho_out = rho;
-    const R tx = vx * vx, ty = vy * vy, tz = vz * vz;
+    // halved squares and halved second-order moments: the cube is filled
+    // scaled by 2^-(indices equal to 2) for inverse_cube_h
+    const R hx = R(0.5) * vx * vx, hy = R(0.5) * vy * vy, hz = R(0.5) * vz * vz;
+    const R ch = cs2h<R>();
+    const R sxh = R(0.5) * sxx, syh = R(0.5) * syy, szh = R(0.5) * szz;
 
     // non-equilibrium part of the post-collision central moments
-    // (kappa* - rho E); zero for odd orders
-    const R n220 = c * (sxx + syy) + (sxx * syy + R(2) * kxy * kxy) * irho;
-    const R n202 = c * (sxx + szz) + (sxx * szz + R(2) * kxz * kxz) * irho;
-    const R n022 = c * (syy + szz) + (syy * szz + R(2) * kyz * kyz) * irho;
-    const R n211 = c * kyz + (sxx * kyz + R(2) * kxy * kxz) * irho;
-    const R n121 = c * kxz + (syy * kxz + R(2) * kxy * kyz) * irho;
-    const R n112 = c * kxy + (szz * kxy + R(2) * kxz * kyz) * irho;
-    const R n222 = c * c * (sxx + syy + szz) +
-                   (c * (sxx * syy + sxx * szz + syy * szz) + R(2) * c * (kxy * kxy + kxz * kxz + kyz * kyz)) * irho +
-                   (sxx * syy * szz + R(2) * (sxx * kyz * kyz + syy * kxz * kxz + szz * kxy * kxy) +
-                    R(8) * kxy * kxz * kyz) * irho * irho;
+    // (kappa* - rho E), zero for odd orders, each scaled like its slot:
+    // kappa_220 = c(sxx + syy) + (sxx syy + 2 kxy^2)/rho etc., the Isserlis
+    // products of the relaxed second-order cumulants
+    const R n220 = ch * (sxh + syh) + (sxh * syh + R(0.5) * kxy * kxy) * irho;
+    const R n202 = ch * (sxh + szh) + (sxh * szh + R(0.5) * kxz * kxz) * irho;
+    const R n022 = ch * (syh + szh) + (syh * szh + R(0.5) * kyz * kyz) * irho;
+    const R n211 = ch * kyz + (sxh * kyz + kxy * kxz) * irho;
+    const R n121 = ch * kxz + (syh * kxz + kxy * kyz) * irho;
+    const R n112 = ch * kxy + (szh * kxy + kxz * kyz) * irho;
+    const R n222 = ch * ch * (sxh + syh + szh) +
+                   (ch * (sxh * syh + sxh * szh + syh * szh) + R(0.5) * ch * (kxy * kxy + kxz * kxz + kyz * kyz)) * irho +
+                   (sxh * syh * szh + R(0.5) * (sxh * kyz * kyz + syh * kxz * kxz + szh * kxy * kxy) +
+                    kxy * kxz * kyz) * irho * irho;
 
     R cb[27];
 #pragma unroll
@@ -349,9 +457,9 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
                 if (m == 1 && n == 1 && o == 0) neq = kxy;
                 if (m == 1 && n == 0 && o == 1) neq = kxz;
                 if (m == 0 && n == 1 && o == 1) neq = kyz;
-                if (m == 2 && n == 0 && o == 0) neq = sxx;
-                if (m == 0 && n == 2 && o == 0) neq = syy;
-                if (m == 0 && n == 0 && o == 2) neq = szz;
+                if (m == 2 && n == 0 && o == 0) neq = sxh;
+                if (m == 0 && n == 2 && o == 0) neq = syh;
+                if (m == 0 && n == 0 && o == 2) neq = szh;
                 if (m == 2 && n == 2 && o == 0) neq = n220;
                 if (m == 2 && n == 0 && o == 2) neq = n202;
                 if (m == 0 && n == 2 && o == 2) neq = n022;
@@ -359,9 +467,9 @@ __device__ __forceinline__ void collide_f_force(R* fd, const DevParams& p, const
                 if (m == 1 && n == 2 && o == 1) neq = n121;
                 if (m == 1 && n == 1 && o == 2) neq = n112;
                 if (m == 2 && n == 2 && o == 2) neq = n222;
-                cb[MIDX(m, n, o)] = neq + drho * Eq<R>(m, n, o) + rho0 * Dm<R>(m, n, o, vx, vy, vz, tx, ty, tz);
+                cb[MIDX(m, n, o)] = neq + drho * Eqh<R>(m, n, o) + rho0 * Dmh<R>(m, n, o, vx, vy, vz, hx, hy, hz);
             }
-    inverse_cube<R>(cb, vx, vy, vz);
+    inverse_cube_h<R>(cb, vx, vy, vz);
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = cb[CUBE(a)];
 }
@@ -379,46 +487,53 @@ __device__ __forceinline__ void collide_f(R* fd, const DevParams& p, R& ux, R& u
 // so they go straight to equilibrium plus half the source and their
 // pre-collision values are never needed (the odd orders, whose equilibrium
 // part E vanishes, keep s^H)
+// m0 (if given) receives the pre-collision zeroth moment sum(h)
 template <typename R, bool TRT = false>
-__device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+__device__ __forceinline__ void collide_h27(R* hd, R ux, R uy, R uz, R Q, const DevParams& p, R* m0 = nullptr) {
     R cb[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) cb[CUBE(a)] = hd[a];
     forward_cube<R>(cb, ux, uy, uz);
+    if (m0) *m0 = cb[0];
     const R Tref = par<R>(p.Tref, p.pf.Tref);
     const R dH = cb[0] + R(0.5) * Q;
-    const R tx = ux * ux, ty = uy * uy, tz = uz * uz;
+    // relaxed moments scaled by 2^-(indices equal to 2) for inverse_cube_h:
+    // E and D come scaled (Eqh, Dmh), the pre-collision moment y is scaled
+    // through its coefficient
+    const R hx = R(0.5) * ux * ux, hy = R(0.5) * uy * uy, hz = R(0.5) * uz * uz;
 #pragma unroll
     for (int o = 0; o < 3; ++o)
 #pragma unroll
         for (int n = 0; n < 3; ++n)
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const R E = Eq<R>(m, n, o);
-                const R D = Dm<R>(m, n, o, ux, uy, uz, tx, ty, tz);
+                const R E = Eqh<R>(m, n, o);
+                const R D = Dmh<R>(m, n, o, ux, uy, uz, hx, hy, hz);
+                const R sc = R(HALVES(m, n, o));
                 R& y = cb[MIDX(m, n, o)];
                 if constexpr (TRT) {
                     if ((m + n + o) % 2 == 0) {
                         y = dH * E + Tref * D + R(0.5) * Q * E;
                     } else {
                         const R s = par<R>(p.sh[1], p.pf.sh[1]);
-                        y = (R(1) - s) * y + s * (Tref * D);
+                        y = ((R(1) - s) * sc) * y + s * (Tref * D);
                     }
                 } else {
                     const R s = par<R>(p.sh[m + n + o], p.pf.sh[m + n + o]);
-                    y = (R(1) - s) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
+                    y = ((R(1) - s) * sc) * y + s * (dH * E + Tref * D) + (R(1) - R(0.5) * s) * Q * E;
                 }
             }
-    inverse_cube<R>(cb, ux, uy, uz);
+    inverse_cube_h<R>(cb, ux, uy, uz);
 #pragma unroll
     for (int a = 0; a < 27; ++a) hd[a] = cb[CUBE(a)];
 }
 
 // D3Q7 (pops 0, +x, +y, +z, -x, -y, -z; moments 000, 100, 010, 001, 200, 020, 002)
 template <typename R, bool TRT = false>
-__device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+__device__ __forceinline__ void collide_h7(R* hd, R ux, R uy, R uz, R Q, const DevParams& p, R* m0_out = nullptr) {
     const R u[3] = {ux, uy, uz};
     const R m0 = hd[0] + hd[1] + hd[2] + hd[3] + hd[4] + hd[5] + hd[6];
+    if (m0_out) *m0_out = m0;
     const R Tref = par<R>(p.Tref, p.pf.Tref);
     const R dH = m0 + R(0.5) * Q;
     const R c = cs2<R>();
@@ -467,7 +582,7 @@ __device__ __forceinline__ void heq_dev(R* hd, R dpsi, R ux, R uy, R uz, const D
 // relaxed mean velocity v = (1 - s) m + s u, m = sum(e h)/sum(h): the result
 // is that equilibrium.  The zeroth moment sum(h) must be positive.
 template <typename R, int QH>
-__device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+__device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, const DevParams& p, R* m0 = nullptr) {
     R dH = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
@@ -478,6 +593,7 @@ __device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, cons
         if (EY(a) != 0) jy += EY(a) * v;
         if (EZ(a) != 0) jz += EZ(a) * v;
     }
+    if (m0) *m0 = dH;
     const R Ht = par<R>(p.Tref, p.pf.Tref) + dH;  // zeroth moment of the stored (App. D shifted) h
     const R iH = R(1) / Ht;
     const R s = par<R>(p.sh[1], p.pf.sh[1]);
@@ -491,13 +607,13 @@ __device__ __forceinline__ void collide_h_cum(R* hd, R ux, R uy, R uz, R Q, cons
 // CUM: the Cumulants-1st kind (compile time, so the central-moment kinds
 // keep their register allocation)
 template <typename R, int QH, bool CUM = false, bool TRT = false>
-__device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const DevParams& p) {
+__device__ __forceinline__ void collide_h(R* hd, R ux, R uy, R uz, R Q, const DevParams& p, R* m0 = nullptr) {
     if constexpr (CUM) {
-        collide_h_cum<R, QH>(hd, ux, uy, uz, Q, p);
+        collide_h_cum<R, QH>(hd, ux, uy, uz, Q, p, m0);
     } else if constexpr (QH == 27) {
-        collide_h27<R, TRT>(hd, ux, uy, uz, Q, p);
+        collide_h27<R, TRT>(hd, ux, uy, uz, Q, p, m0);
     } else {
-        collide_h7<R, TRT>(hd, ux, uy, uz, Q, p);
+        collide_h7<R, TRT>(hd, ux, uy, uz, Q, p, m0);
     }
 }
 

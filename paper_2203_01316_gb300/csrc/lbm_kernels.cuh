@@ -145,19 +145,21 @@ __device__ __forceinline__ int src_of(const Nbr& b, int a) {
 }
 
 // ---- collision + store shared by the bulk and the wall kernels ----------------
+// element (i, node) of an SoA array [Q][N] as a 32-bit unsigned index
+// (lbm_create keeps 27 N below 2^31), so that each address is one widening
+// multiply-add instead of sign extensions and 64-bit adds
+__device__ __forceinline__ uint32_t soa(int i, int N, int node) {
+    return (uint32_t)i * (uint32_t)N + (uint32_t)node;
+}
+
 // ---- 16-bit stores ------------------------------------------------------------
 // Two values of one node (populations a and a + 1) are converted with one
 // packed conversion and stored as two 16-bit halves.  Stochastic rounding
 // uses the conversion's own random-bits operand (FP16: bits 0-12 round the
 // low value, bits 16-28 the high one; BF16: bits 0-15 and 16-31): the value
 // rounds up in magnitude with probability equal to the discarded fraction,
-// so rounding errors have zero mean.  The 32 bits come from the node's
-// stream, its high half folded onto the low half (the low bits of a linear
-// congruential sequence are weak).
-__device__ __forceinline__ uint32_t sr_pair_bits(SrStream& rs) {
-    const uint32_t r = rs.next();
-    return r ^ (r >> 16);
-}
+// so rounding errors have zero mean.  The 32 bits are one draw of the node's
+// stream.
 template <bool SR> __device__ __forceinline__ uint32_t cvt_pair(__half*, float hi, float lo, uint32_t r) {
     uint32_t d;
     if constexpr (SR) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
@@ -178,9 +180,9 @@ __device__ __forceinline__ void store16(S* __restrict__ X, const float* v, int n
 #pragma unroll
     for (int i = 0; i < Q; i += 2) {
         const float hi = (i + 1 < Q) ? v[i + 1] : 0.0f;
-        const uint32_t d = cvt_pair<SR>(X, hi, v[i], SR ? sr_pair_bits(rs) : 0u);
-        *(unsigned short*)(X + i * N + n) = (unsigned short)(d & 0xffffu);
-        if (i + 1 < Q) *(unsigned short*)(X + (i + 1) * N + n) = (unsigned short)(d >> 16);
+        const uint32_t d = cvt_pair<SR>(X, hi, v[i], SR ? rs.next() : 0u);
+        *(unsigned short*)(X + soa(i, N, n)) = (unsigned short)(d & 0xffffu);
+        if (i + 1 < Q) *(unsigned short*)(X + soa(i + 1, N, n)) = (unsigned short)(d >> 16);
     }
 }
 
@@ -196,7 +198,7 @@ __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __res
         else store16<false, S, 27>(fB, fd, n, p.N, 0u, 0u);
     } else {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) st(fB + a * p.N + n, fd[a]);
+        for (int a = 0; a < 27; ++a) st(fB + soa(a, p.N, n), fd[a]);
     }
 }
 
@@ -211,10 +213,8 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
         // the result (a steady energy drift over long runs at small k), so
         // the rest population takes exactly what the others leave of the
         // pre-collision zeroth moment plus the source
-        R pre = R(0);
-#pragma unroll
-        for (int i = 0; i < QH; ++i) pre += hd[i];
-        collide_h<R, QH, CUM, TRT>(hd, ux, uy, uz, Q, p);
+        R pre;
+        collide_h<R, QH, CUM, TRT>(hd, ux, uy, uz, Q, p, &pre);
         R others = R(0);
 #pragma unroll
         for (int i = 1; i < QH; ++i) others += hd[i];
@@ -227,7 +227,7 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
         else store16<false, S, QH>(hB, hd, n, p.N, 0u, 0u);
     } else {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) st(hB + i * p.N + n, hd[i]);
+        for (int i = 0; i < QH; ++i) st(hB + soa(i, p.N, n), hd[i]);
     }
 }
 
@@ -290,10 +290,10 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     const int N = p.N;
     if (type == T_INLET) {
 #pragma unroll
-        for (int a = 0; a < 27; ++a) st(fB + a * N + n, inlet[a]);
+        for (int a = 0; a < 27; ++a) st(fB + soa(a, N, n), inlet[a]);
         if (DO_H) {
 #pragma unroll
-            for (int i = 0; i < QH; ++i) st(hB + i * N + n, inlet[27 + i]);
+            for (int i = 0; i < QH; ++i) st(hB + soa(i, N, n), inlet[27 + i]);
         }
         if (REC) {
             urec[n] = par<R>(p.uin[0], p.pf.uin[0]);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     const Nbr nb = make_nbr(x, y, z, p);
     R fd[27];
 #pragma unroll
-    for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + a * N + src_of(nb, a));
+    for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + soa(a, N, src_of(nb, a)));
     if (mask) {
         // the arrival b whose source x_b - e_b = x_b + e_a (a = opp b) is solid
 #pragma unroll
@@ -324,12 +324,12 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
             if (!(mask & (1u << a))) continue;
             const float q = __ldg(lq + off + __popc(mask & ((1u << a) - 1u)));
             const bool thin = (mask >> b) & 1u;  // x_f = x_b - e_a is solid too
-            const R fa_b = ld<R>(fA + a * N + n);
+            const R fa_b = ld<R>(fA + soa(a, N, n));
             if (q <= 0.5f && !thin) {
                 fd[b] = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];  // fd[a] = f*_a(x_f)
             } else {
                 const R qq = (R)fmaxf(q, 0.5f);
-                const R fb_b = ld<R>(fA + b * N + n);
+                const R fb_b = ld<R>(fA + soa(b, N, n));
                 fd[b] = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
             }
         }
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     R ux, uy, uz;
     if constexpr (PRE) {  // pre-collision arrivals for the coupled adjoint
 #pragma unroll
-        for (int a = 0; a < 27; ++a) ((R*)frec)[a * N + n] = fd[a];
+        for (int a = 0; a < 27; ++a) ((R*)frec)[soa(a, N, n)] = fd[a];
     }
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
     if (REC) {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     if constexpr (DO_H) {
     R hd[QH];
 #pragma unroll
-    for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + i * N + src_of(nb, HDIR<QH>(i)));
+    for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + soa(i, N, src_of(nb, HDIR<QH>(i))));
     if (mask) {
         const R Tref = par<R>(p.Tref, p.pf.Tref);
 #pragma unroll
@@ -365,12 +365,12 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
                 hd[ib] = R(0.5) * heq2;
                 continue;
             }
-            const R ha_b = ld<R>(hA + ia * N + n);
+            const R ha_b = ld<R>(hA + soa(ia, N, n));
             if (q <= 0.5f && !thin) {
                 hd[ib] = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
             } else {
                 const R qq = (R)fmaxf(q, 0.5f);
-                const R hb_b = ld<R>(hA + ib * N + n);
+                const R hb_b = ld<R>(hA + soa(ib, N, n));
                 hd[ib] = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
             }
         }
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     const R Q = theta ? (R)__ldg(theta + n) : R(0);
     if constexpr (PRE) {
 #pragma unroll
-        for (int i = 0; i < QH; ++i) ((R*)hrec)[i * N + n] = hd[i];
+        for (int i = 0; i < QH; ++i) ((R*)hrec)[soa(i, N, n)] = hd[i];
     }
     collide_store_h<S, QH, CUM, TRT>(hd, hB, n, p, ux, uy, uz, Q);
     }
