@@ -137,8 +137,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx);
  * fluid->solid link is listed exactly once; symmetry rows are whole, their
  * neighbour rows hold no solid node and no wall link.  Links may come in any
  * order.  Replaces any earlier geometry; the populations must be
- * (re)initialised afterwards.  The coupled adjoint (lbm_adjoint_flow_step)
- * refuses contexts with the Zou-He inlet. */
+ * (re)initialised afterwards. */
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, int64_t n_links,
                             const int32_t* link_node, const int32_t* link_dir,
                             const float* link_q, const int32_t* link_wall, int n_walls,
@@ -301,15 +300,18 @@ lbm_status lbm_adjoint_step_h(lbm_ctx* ctx, const void* u_level, const void* h_l
  * through u, so this sweep carries the adjoint of f as well (Eq.
  * hydro_cu_collision, Eq. IBB) next to that of h (Eq. H_cm_collision or
  * H_cu_collision, Eq. IABB).  FP32 or FP64 storage only (LBM_ERR_INVALID
- * otherwise); symmetry rows are covered as in lbm_adjoint_step, the Zou-He
- * inlet is not (LBM_ERR_INVALID).  Adjoint arrays:
+ * otherwise); symmetry rows and the Zou-He inlet are covered as in
+ * lbm_adjoint_step (with the Zou-He inlet, dJ/du_in differentiates the rule
+ * that builds the inlet's unknown arrivals).  Adjoint arrays:
  * element type float (FP32) or double (FP64), SoA [27][N] for f and [Q_h][N]
  * for h. */
 
 /* lbm_step_record with advance_h = 1 that records, for each step k = 1..n,
- * the pre-collision arrivals of every non-solid, non-inlet node (after
- * streaming, the walls and the planes) as deviations: f at f_rec + (k-1)*27*N
- * and h at h_rec + (k-1)*Q_h*N (device). */
+ * the pre-collision arrivals of every node that collides (fluid and outlet
+ * nodes, and inlet nodes with the Zou-He inlet, whose unknown arrivals the
+ * rule has filled) as deviations, after streaming, the walls and the
+ * planes: f at f_rec + (k-1)*27*N and h at h_rec + (k-1)*Q_h*N (device).
+ * Other nodes' entries are left as they are. */
 lbm_status lbm_step_record_pre(lbm_ctx* ctx, int n, void* f_rec, void* h_rec);
 
 /* One level k of the coupled adjoint sweep: from the adjoints of the next
