@@ -101,16 +101,15 @@ typedef enum { LBM_INLET_EQUILIBRIUM = 0, LBM_INLET_ZOU_HE = 1 } lbm_inlet_bc;
  * at q = 1/2). */
 typedef enum { LBM_WALL_IBB_IABB = 0, LBM_WALL_BB_EQ = 1, LBM_WALL_BB_ABB = 2 } lbm_wall_bc;
 
-/* Implementation of lbm_step.  Both run the one-node-per-thread kernel (the
- * fastest measured on GB300: the step sits near the SM issue limit and gains
- * from the warps its 96-register cap keeps resident).  LBM_STEP_AUTO replays
- * a CUDA graph of two steps for calls of 4 or more steps (captured on the
- * context's stream at first use and again whenever the buffers or
- * parameters it captured change; not for stochastically rounded 16-bit
- * storage, whose rounding follows the step count), which removes the launch
- * gaps that dominate small grids; results are bit-identical to
- * LBM_STEP_CLASSIC, which launches every step.  While the caller is
- * capturing the context's stream, lbm_step launches every step. */
+/* Implementation of lbm_step.  Both run the fused one-node-per-thread
+ * kernel (f and h of a node in one thread; the fastest measured on GB300).
+ * LBM_STEP_AUTO replays a CUDA graph of two steps for calls of 4 or more
+ * steps (captured on the context's stream at first use and again whenever
+ * the buffers or parameters it captured change; not for stochastically
+ * rounded 16-bit storage, whose rounding follows the step count), which
+ * removes the launch gaps that dominate small grids; results are
+ * bit-identical to LBM_STEP_CLASSIC, which launches every step.  While the
+ * caller is capturing the context's stream, lbm_step launches every step. */
 typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1 } lbm_step_kernel;
 
 /* Create a context and allocate its device state.  The populations are zero
@@ -307,12 +306,24 @@ lbm_status lbm_adjoint_step_h(lbm_ctx* ctx, const void* u_level, const void* h_l
  * for h. */
 
 /* lbm_step_record with advance_h = 1 that records, for each step k = 1..n,
- * the pre-collision arrivals of every node that collides (fluid and outlet
- * nodes, and inlet nodes with the Zou-He inlet, whose unknown arrivals the
- * rule has filled) as deviations, after streaming, the walls and the
- * planes: f at f_rec + (k-1)*27*N and h at h_rec + (k-1)*Q_h*N (device).
- * Other nodes' entries are left as they are. */
+ * what the coupled adjoint needs of the pre-collision arrivals (deviations,
+ * after streaming, the walls and the planes) of every node that collides
+ * (fluid and outlet nodes, and inlet nodes with the Zou-He inlet, whose
+ * unknown arrivals the rule has filled).  Level k's f record starts at
+ * f_rec + (k-1)*F and holds the ten raw moments of the f arrivals as
+ * [10][N] (sum f, sum e_x f, sum e_y f, sum e_z f, sum e_x^2 f, sum e_y^2 f,
+ * sum e_z^2 f, sum e_x e_y f, sum e_x e_z f, sum e_y e_z f: the f collision
+ * reads f only through them), followed, with the Zou-He inlet, by the inlet
+ * nodes' 27 arrivals as [27][ny*nz] (row y + ny*z); F = 10*N, plus 27*ny*nz
+ * with the Zou-He inlet (inlet_bc = LBM_INLET_ZOU_HE and periodic_x = 0).  Level k's h record holds the h arrivals [Q_h][N]
+ * at h_rec + (k-1)*Q_h*N.  Element type as the storage (float or double),
+ * device memory; lbm_flow_record_size gives F and Q_h*N.  Other nodes'
+ * entries are left as they are. */
 lbm_status lbm_step_record_pre(lbm_ctx* ctx, int n, void* f_rec, void* h_rec);
+
+/* Elements of one level's f and h records of lbm_step_record_pre (see there).
+ * Errors: LBM_ERR_INVALID for null arguments. */
+lbm_status lbm_flow_record_size(lbm_ctx* ctx, int64_t* f_elems, int64_t* h_elems);
 
 /* One level k of the coupled adjoint sweep: from the adjoints of the next
  * level's arrivals (muf_next, muh_next; zeros at the last level) and the

@@ -148,17 +148,18 @@ class FlowObjective(torch.autograd.Function):
         s.adjoint_flow_gradient(reset=True)
         lo, hi = ctx.window
         cur = 0
+        FR, HR = s.flow_record_size()
         for seg_start in sorted(ctx.ckpts, reverse=True):
             seg_end = min(seg_start + ctx.every, ctx.nsteps)
             L = seg_end - seg_start
             s.load_state(ctx.ckpts[seg_start])
-            frec = torch.empty(L * 27 * N, dtype=rdt, device=dev)
-            hrec = torch.empty(L * qh * N, dtype=rdt, device=dev)
+            frec = torch.empty(L * FR, dtype=rdt, device=dev)
+            hrec = torch.empty(L * HR, dtype=rdt, device=dev)
             s.step_record_pre(L, frec, hrec)
             for k in range(seg_end, seg_start, -1):
                 obj = ctx.objective if lo <= k <= hi else None
                 j = k - seg_start - 1
-                s.adjoint_flow_step(frec[j * 27 * N:(j + 1) * 27 * N], hrec[j * qh * N:(j + 1) * qh * N],
+                s.adjoint_flow_step(frec[j * FR:(j + 1) * FR], hrec[j * HR:(j + 1) * HR],
                                     muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj, dtheta)
                 cur = 1 - cur
         obj0 = ctx.objective if lo <= 0 <= hi else None

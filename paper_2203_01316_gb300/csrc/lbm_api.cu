@@ -339,6 +339,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
         dev_alloc(c, &c->d_scratch, (3 * lbmd::kRedBlocks + 4) * sizeof(double)) != cudaSuccess ||
         dev_alloc(c, &c->d_Twall, sizeof(float)) != cudaSuccess)
         return bail(fail(c, LBM_ERR_NOMEM, "context buffers: out of device memory"));
+
     cudaMemsetAsync(c->d_flags, 0, N, c->stream);
     cudaMemsetAsync(c->d_Twall, 0, sizeof(float), c->stream);
 
@@ -1214,6 +1215,19 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* u_level, const void* mu_next
     return adjoint_step_impl(c, u_level, nullptr, mu_next, out, obj, dJ_dtheta);
 }
 
+// elements of one level's f record of the coupled adjoint: ten moments per
+// node, then the Zou-He inlet nodes' full arrivals
+static int64_t flow_frec_elems(const lbm_ctx* c) {
+    return (int64_t)10 * c->N + (c->dp.zou_he ? (int64_t)27 * c->p.ny * c->p.nz : 0);
+}
+
+lbm_status lbm_flow_record_size(lbm_ctx* c, int64_t* f_elems, int64_t* h_elems) {
+    if (!c || !f_elems || !h_elems) return LBM_ERR_INVALID;
+    *f_elems = flow_frec_elems(c);
+    *h_elems = (int64_t)c->qh * c->N;
+    return LBM_OK;
+}
+
 lbm_status lbm_step_record_pre(lbm_ctx* c, int n, void* f_rec, void* h_rec) {
     if (!c) return LBM_ERR_INVALID;
     if (n < 0) return fail(c, LBM_ERR_INVALID, "n must be >= 0");
@@ -1227,7 +1241,7 @@ lbm_status lbm_step_record_pre(lbm_ctx* c, int n, void* f_rec, void* h_rec) {
         Buffers b = buffers(c);
         c->dp.step += 1;
         const DevParams p = c->dp;
-        b.frec = (char*)f_rec + (size_t)i * 27 * c->N * rsize;
+        b.frec = (char*)f_rec + (size_t)i * flow_frec_elems(c) * rsize;
         b.hrec = (char*)h_rec + (size_t)i * c->qh * c->N * rsize;
         cudaError_t e = fill_mirror(c, b, p);
         if (e != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");

@@ -34,7 +34,9 @@ struct Buffers {
     const int32_t* rlink;     // link index (into lq / lwall) of each entry
     double* dlink;            // per link accumulator of dJ/dT_w terms
     void* urec;               // recorded velocities of a step (3N, R) or nullptr
-    void* frec;               // recorded pre-collision f arrivals (27N, R; coupled adjoint) or nullptr
+    void* frec;               // coupled adjoint record of a level (R): the ten raw moments of the
+                              // pre-collision f arrivals [10][N], then, with the Zou-He inlet, the
+                              // inlet nodes' full arrivals [27][ny nz]; or nullptr
     void* hrec;               // recorded pre-collision h arrivals (Q_h N, R) or nullptr
 };
 
@@ -336,9 +338,11 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
         }
     }
     R ux, uy, uz;
-    if constexpr (PRE) {  // pre-collision arrivals for the coupled adjoint
+    if constexpr (PRE) {  // the coupled adjoint needs f only through these ten moments
+        R m[10];
+        raw_moments_f<R>(fd, m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9]);
 #pragma unroll
-        for (int a = 0; a < 27; ++a) ((R*)frec)[soa(a, N, n)] = fd[a];
+        for (int k = 0; k < 10; ++k) ((R*)frec)[soa(k, N, n)] = m[k];
     }
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
     if (REC) {
@@ -1212,8 +1216,9 @@ __device__ __forceinline__ void zou_he_fill_h(T* hd, T drho, T ux, T uy, T uz, c
         if (EX(HDIR<QH>(k)) == 1) hd[k] = he[k];
 }
 
-// frec, hrec: pre-collision records of the coupled adjoint (the full arrival
-// vectors after the rule), or nullptr
+// frec, hrec: pre-collision records of the coupled adjoint (the f moments and,
+// after them, the inlet node's full arrival vector after the rule; the h
+// arrivals), or nullptr
 template <typename S, int QH, bool CUM, bool DO_H>
 __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* __restrict__ fB,
                                                    const S* __restrict__ hA, S* __restrict__ hB,
@@ -1235,8 +1240,13 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
     for (int a = 0; a < 27; ++a) fd[a] = (EX(a) == 1) ? R(0) : ld<R>(fA + a * N + src_of(nb, a));
     const R drho = zou_he_fill_f<R>(fd, ux, uy, uz, p);
     if (frec) {
+        R m[10];
+        raw_moments_f<R>(fd, m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9]);
 #pragma unroll
-        for (int a = 0; a < 27; ++a) ((R*)frec)[a * N + n] = fd[a];
+        for (int k = 0; k < 10; ++k) ((R*)frec)[k * N + n] = m[k];
+        R* inl = (R*)frec + (size_t)10 * N;  // [27][ny nz], row i = y + ny z
+#pragma unroll
+        for (int a = 0; a < 27; ++a) inl[(size_t)a * p.ny * p.nz + i] = fd[a];
     }
     R vx, vy, vz;
     collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz);
@@ -1572,8 +1582,9 @@ __device__ __forceinline__ void h_transpose_and_velocity(const R* lam, const R* 
     }
 }
 
-// Adjoint of the f collision of one node at its pre-collision arrivals g:
-// G[k] = lambda . (dC_f/dg) d_k + w . (dU/dg) d_k for the ten unit-moment
+// Adjoint of the f collision of one node, given the ten raw moments m of its
+// pre-collision arrivals (raw_moments_f order; the collision reads f only
+// through them): G[k] = lambda . (dC_f/dg) d_k + w . (dU/dg) d_k for the ten unit-moment
 // perturbations d_k (k < 10) and the same for the three components of F
 // (k = 10..12).  The synthesis (central moments -> populations through the
 // inverse transform at the mean v) is differentiated in reverse mode once:
@@ -1583,9 +1594,7 @@ __device__ __forceinline__ void h_transpose_and_velocity(const R* lam, const R* 
 // m kappa_(m-1)no (exact on the three-point lattice).  The front part (ten
 // moments and F -> s, k, 1/rho, v, u) is reversed by hand (f_front_adjoint).
 template <typename R>
-__device__ __forceinline__ void collide_f_adjoint(const R* g, const DevParams& p, const R* lam, const R* w, R* G) {
-    R m[10];
-    raw_moments_f<R>(g, m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9]);
+__device__ __forceinline__ void collide_f_adjoint(const R* m, const DevParams& p, const R* lam, const R* w, R* G) {
     const FFront<R> S = f_front<R>(m, par<R>(p.F[0], p.pf.F[0]), par<R>(p.F[1], p.pf.F[1]), par<R>(p.F[2], p.pf.F[2]), p);
     const R c = cs2<R>();
     const R sxx = S.sxx, syy = S.syy, szz = S.szz, kxy = S.kxy, kxz = S.kxz, kyz = S.kyz, irho = S.irho;
@@ -1818,13 +1827,12 @@ template <typename R> __device__ __forceinline__ void moments_transpose_f(const 
     }
 }
 
-// velocity u of the h collision from a node's pre-collision f arrivals, as
+// velocity u of the h collision from the raw moments of a node's pre-collision
+// f arrivals (m[0] = density deviation, m[1..3] = momentum), as
 // collide_f_force computes it: u = (sum e f + F/2) / rho
 template <typename R>
-__device__ __forceinline__ void flow_velocity(const R* g, const DevParams& p, R& ux, R& uy, R& uz) {
-    // the moment sums of collide_f_force (unused second moments drop out)
-    R drho, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz;
-    raw_moments_f<R>(g, drho, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz);
+__device__ __forceinline__ void flow_velocity(const R* m, const DevParams& p, R& ux, R& uy, R& uz) {
+    const R drho = m[0], jx = m[1], jy = m[2], jz = m[3];
     const R irho = R(1) / (par<R>(p.rho0, p.pf.rho0) + drho);
     ux = jx * irho + R(0.5) * par<R>(p.F[0], p.pf.F[0]) * irho;
     uy = jy * irho + R(0.5) * par<R>(p.F[1], p.pf.F[1]) * irho;
@@ -2031,9 +2039,11 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_flow(
         }
         return;
     }
-    R g[27];
+    // the level's f moments (raw_moments_f order): the h part needs only
+    // the density and momentum, the f part all ten
+    R g[10];
 #pragma unroll
-    for (int a = 0; a < 27; ++a) g[a] = gf[a * N + n];
+    for (int k = 0; k < (HP ? 4 : 10); ++k) g[k] = gf[k * N + n];
     if constexpr (HP) {
         R hpre[QH];
 #pragma unroll
@@ -2109,9 +2119,10 @@ __global__ void __launch_bounds__(kBlock) k_zou_he_adjoint(R* __restrict__ muf, 
     if ((flags[n] & 3) != T_INLET) return;
     const int N = p.N;
     R g[27], h[QH], mf[27], mh[QH];
+    const R* inl = gf + (size_t)10 * N;  // the inlet nodes' arrivals [27][ny nz]
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
-        g[a] = gf[a * N + n];
+        g[a] = inl[(size_t)a * p.ny * p.nz + i];
         mf[a] = muf[a * N + n];
     }
 #pragma unroll

@@ -27,7 +27,7 @@ SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_s
            "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
            "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
            "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h", "lbm_step_record_pre",
-           "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient", "lbm_wall_force"]
+           "lbm_flow_record_size", "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient", "lbm_wall_force"]
 OBJ_SURFACE, OBJ_SECTION, OBJ_FORCE = 0, 1, 2
 
 
@@ -95,6 +95,7 @@ def lib():
         "lbm_adjoint_step": [vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_step_record_h": [vp, i32, vp, vp],
         "lbm_step_record_pre": [vp, i32, vp, vp],
+        "lbm_flow_record_size": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
         "lbm_adjoint_flow_step": [vp, vp, vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_adjoint_flow_gradient": [vp, C.POINTER(dbl), C.POINTER(dbl), i32],
         "lbm_adjoint_step_h": [vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
@@ -341,9 +342,18 @@ class Solver:
         else:
             self._check(self.L.lbm_adjoint_step(self._h, *args))
 
+    def flow_record_size(self):
+        """Elements (F, H) of one level's f and h records of step_record_pre."""
+        f = C.c_int64()
+        h = C.c_int64()
+        self._check(self.L.lbm_flow_record_size(self._h, C.byref(f), C.byref(h)))
+        return int(f.value), int(h.value)
+
     def step_record_pre(self, n, f_rec, h_rec):
-        """n steps recording each level's pre-collision arrivals into f_rec
-        ([n, 27, N]) and h_rec ([n, Q_h, N]) device tensors (FP32/FP64)."""
+        """n steps recording what the coupled adjoint needs of each level's
+        pre-collision arrivals into device tensors f_rec (n x F elements: the
+        ten f moments, plus the Zou-He inlet nodes' arrivals) and h_rec
+        (n x Q_h N: the h arrivals), FP32/FP64; (F, Q_h N) = flow_record_size()."""
         self._check(self.L.lbm_step_record_pre(self._h, int(n), f_rec.data_ptr() if n > 0 else None,
                                                h_rec.data_ptr() if n > 0 else None))
 

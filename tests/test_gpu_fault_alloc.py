@@ -21,7 +21,8 @@ LBM_ERR_NOMEM, LBM_ERR_STATE = 2, 5
 def _calls(s, w, torch):
     """The library's allocating calls, in an order a user makes them."""
     N = s.N
-    rec = torch.empty(2 * 27 * N, dtype=torch.float32, device="cuda")
+    F, H = s.flow_record_size()
+    rec = torch.empty(F + H, dtype=torch.float32, device="cuda")
     mu = torch.zeros(27 * N, dtype=torch.float32, device="cuda")
     out = torch.empty_like(mu)
     return [
@@ -32,8 +33,8 @@ def _calls(s, w, torch):
         ("macros", lambda: s.macros()),
         ("populations", lambda: s.populations()),
         ("stream_map", lambda: s.stream_map()),
-        ("record_pre", lambda: s.step_record_pre(1, rec[:27 * N], rec[27 * N:])),
-        ("flow_adjoint", lambda: s.adjoint_flow_step(rec[:27 * N], rec[27 * N:], mu, mu, out, out.clone())),
+        ("record_pre", lambda: s.step_record_pre(1, rec[:F], rec[F:])),
+        ("flow_adjoint", lambda: s.adjoint_flow_step(rec[:F], rec[F:], mu, mu, out, out.clone())),
     ]
 
 
