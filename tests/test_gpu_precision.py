@@ -81,6 +81,46 @@ def test_one_step_16bit(storage, round_nearest, qh):
 CROP_UT_BOUND = {"f32": (1e-5, 1e-5), "f16": (1e-3, 1e-3), "bf16": (1e-2, 1e-2)}
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_stochastic_rounding_is_unbiased(storage):
+    """One step of a 48^3 periodic Taylor-Green box: the stored 16-bit values
+    minus the oracle's exact post-collision values, in units of the format's
+    spacing, average to zero (stochastic rounding rounds up with probability
+    equal to the discarded fraction, so its error has zero mean; truncation
+    would average -1/2, a bias in the random bits a clear fraction of it).
+    Bound: 5 standard deviations of the mean of M errors of variance <= 1/4."""
+    from paper_2203_01316_gb300 import Solver
+    w = I.periodic_tgv(48)
+    n = w["dims"][0]
+    s = Solver(n, n, n, nu=0.03, k=2e-3, storage=storage, periodic_x=True, T_ref=1.0)
+    s.set_geometry(w["flags"], w["links"], n_walls=1)
+    s.init_fields(w["rho"], w["u"].reshape(-1), w["T"])
+    s.step(2)
+    o = O.Oracle(O.make_params(nx=n, ny=n, nz=n, periodic_x=True, nu=0.03, k=2e-3))
+    o.set_geometry(w["flags"], w["links"], nwalls=1)
+    f0, h0 = s.populations()
+    o.set_post(f0, h0)
+    assert o.stream() == 0
+    fo, ho = o.post()
+    s.step(1)
+    f1, h1 = s.populations()
+    _, w27, _, _ = O.lattice(27)
+    err = []
+    for got, ref, shift in ((f1, fo, w27[:, None] * 1.0), (h1, ho, w27[:, None] * 1.0)):
+        dev = ref - shift
+        # stored values of at least 2^-8: their spacing (>= 2^-18 in FP16)
+        # dwarfs the FP32 arithmetic's error (about 1e-9 here), which would
+        # otherwise blur the rounding error of the smallest values
+        big = np.abs(dev) >= 2.0 ** -8
+        err.append(((got - ref) / _ulp(dev, storage))[big])
+    e = np.concatenate(err)
+    assert e.size > 5 * 10 ** 5
+    assert np.all(np.abs(e) <= 1.0 + 1e-3)
+    M = e.size
+    assert abs(e.mean()) <= 5.0 * 0.5 / math.sqrt(M), (e.mean(), M)
+    assert np.mean(np.abs(e) > 1e-3) > 0.5  # most values were rounded, not exact
+
+
 def test_crop_nusselt_and_field_errors_16bit():
     from paper_2203_01316_gb300 import Solver
     w = I.heated_sphere(96, 32, 32, D=8.0, cx=24.0, seed=1234, u_in=0.02, T_in=0.0)
