@@ -254,6 +254,7 @@ void free_geometry(lbm_ctx* c) {
     c->d_lq = nullptr;
     c->d_lwall = nullptr;
     c->nw = 0;
+    c->dp.nwall = 0;
     c->nl = 0;
 }
 
@@ -365,6 +366,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     d.hkind = p.hkind;
     d.wall_bc = p.wall_bc;
     d.zou_he = (p.inlet_bc == LBM_INLET_ZOU_HE && !p.periodic_x) ? 1 : 0;
+    d.nwall = 0;
     d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;
@@ -595,6 +597,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
     c->geometry = false;
     c->initialised = false;
     c->nw = (int)wnode.size();
+    c->dp.nwall = c->nw;
     c->nl = n_links;
     CK(cudaMemcpyAsync(c->d_flags, iflags.data(), N, cudaMemcpyHostToDevice, c->stream), "flags upload");
     if (c->nw > 0) {

@@ -316,6 +316,7 @@ struct DevParams {
     int wall_bc;         // 0 Eq. IBB + Eq. IABB, 1 BB + EQ, 2 BB + ABB (BB/ABB: q = 1/2 on the device)
     int mirror_lo, mirror_hi;  // rows y = 0 / y = ny-1 are symmetry rows
     int zou_he;                // inlet plane: 0 fixed equilibria, 1 Zou-He (k_inlet after the step)
+    int nwall;                 // wall nodes (entries of the wall table)
     uint32_t step;       // time level being written (seeds the stochastic rounding)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6

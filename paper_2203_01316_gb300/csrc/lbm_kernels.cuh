@@ -264,9 +264,11 @@ template <typename S, int QH> constexpr int step_min_blocks() {
 
 // EQ: the BB + EQ wall rule (compile time, so the default rules keep their
 // register allocation); CUM: the Cumulants-1st h kind; TRT: the CM-TRT kind
-// with its rates fixed at compile time
+// with its rates fixed at compile time.  WM (wall mode): 0 every node; 1
+// every node but the wall nodes; 2 the wall nodes only, one thread per entry
+// of the wall table (modes 1 and 2 together make one step; see launch_step)
 template <typename S, int QH, bool DO_H, bool REC, bool CUM = false, bool EQ = false, bool PRE = false,
-          bool TRT = false>
+          bool TRT = false, int WM = 0>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const S* __restrict__ fA, S* __restrict__ fB,
                                                   const S* __restrict__ hA, S* __restrict__ hB,
                                                   const uint8_t* __restrict__ flags,
@@ -280,14 +282,16 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
                                                   const float* __restrict__ Twall,
                                                   typename Acc<S>::R* __restrict__ urec,
                                                   void* __restrict__ frec, void* __restrict__ hrec,
-                                                  const DevParams p) {
+                                                  const int32_t* __restrict__ wnode, const DevParams p) {
     using R = typename Acc<S>::R;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = n < p.N;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = (WM == 2) ? t < p.nwall : t < p.N;
+    const int n = (WM == 2) ? (in_range ? __ldg(wnode + t) : 0) : t;
     const uint8_t fl = in_range ? flags[n] : (uint8_t)T_SOLID;
     const bool is_wall = (fl & F_WALL) != 0;
-    const uint32_t ballot = __ballot_sync(0xffffffffu, is_wall);
+    const uint32_t ballot = (WM == 0) ? __ballot_sync(0xffffffffu, is_wall) : 0u;
     if (!in_range) return;
+    if (WM == 1 && is_wall) return;
     const int type = fl & 3;
     if (type == T_SOLID) return;
     const int N = p.N;
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     int off = 0;
     if (is_wall) {
         const int lane = threadIdx.x & 31;
-        const int idx = __ldg(seg_base + (n >> 5)) + __popc(ballot & ((1u << lane) - 1u));
+        const int idx = (WM == 2) ? t : __ldg(seg_base + (n >> 5)) + __popc(ballot & ((1u << lane) - 1u));
         mask = __ldg(wmask + idx);
         off = __ldg(woff + idx);
     }
@@ -319,7 +323,25 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     R fd[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + soa(a, N, src_of(nb, a)));
-    if (mask) {
+    if (WM == 2) {
+        // wall nodes alone, so every lane has links: the link bodies without
+        // branches (loads predicated on the mask bit, the result selected),
+        // so that their loads are in flight together
+#pragma unroll
+        for (int b = 0; b < 27; ++b) {
+            const int a = OPP(b);
+            const bool has = (mask >> a) & 1u;
+            const float q = has ? __ldg(lq + off + __popc(mask & ((1u << a) - 1u))) : 0.5f;
+            const bool thin = (mask >> b) & 1u;
+            const R fa_b = has ? ld<R>(fA + soa(a, N, n)) : R(0);
+            const R fb_b = has ? ld<R>(fA + soa(b, N, n)) : R(0);
+            const R qq = (R)fmaxf(q, 0.5f);
+            const R v_lin = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];
+            const R v_far = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
+            const R v = (q <= 0.5f && !thin) ? v_lin : v_far;
+            fd[b] = has ? v : fd[b];
+        }
+    } else if (mask) {
         // the arrival b whose source x_b - e_b = x_b + e_a (a = opp b) is solid
 #pragma unroll
         for (int b = 0; b < 27; ++b) {
@@ -354,7 +376,32 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     R hd[QH];
 #pragma unroll
     for (int i = 0; i < QH; ++i) hd[i] = ld<R>(hA + soa(i, N, src_of(nb, HDIR<QH>(i))));
-    if (mask) {
+    if (WM == 2) {  // as for f: no branches in the link bodies
+        const R Tref = par<R>(p.Tref, p.pf.Tref);
+#pragma unroll
+        for (int ib = 0; ib < QH; ++ib) {
+            const int b = HDIR<QH>(ib);
+            const int ia = HOPP<QH>(ib);
+            const int a = HDIR<QH>(ia);
+            const bool has = (mask >> a) & 1u;
+            const int l = off + __popc(mask & ((1u << a) - 1u));
+            const float q = has ? __ldg(lq + l) : 0.5f;
+            const R heq2 = has ? R(2) * (R)HW<QH>(ia) * ((R)__ldg(Twall + __ldg(lwall + l)) - Tref) : R(0);
+            const bool thin = (mask >> b) & 1u;
+            R v;
+            if constexpr (EQ) {
+                v = R(0.5) * heq2;
+            } else {
+                const R ha_b = has ? ld<R>(hA + soa(ia, N, n)) : R(0);
+                const R hb_b = has ? ld<R>(hA + soa(ib, N, n)) : R(0);
+                const R qq = (R)fmaxf(q, 0.5f);
+                const R v_lin = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
+                const R v_far = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+                v = (q <= 0.5f && !thin) ? v_lin : v_far;
+            }
+            hd[ib] = has ? v : hd[ib];
+        }
+    } else if (mask) {
         const R Tref = par<R>(p.Tref, p.pf.Tref);
 #pragma unroll
         for (int ib = 0; ib < QH; ++ib) {
@@ -389,6 +436,38 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     }
 }
 
+// With many wall nodes the plain 16-bit step runs as two launches: every
+// node but the wall nodes, then the wall nodes alone, one thread per entry of
+// the wall table, with branch-free link bodies.  A warp that holds wall nodes
+// runs the link bodies of the union of its lanes' link directions, each with
+// a load round trip behind its branch; packed into warps of their own (the
+// porous bed: 11k full warps instead of 94k mixed ones) they cost less, though
+// their pulls no longer coalesce.  Measured on the 512x256x256 porous bed
+// (D3Q7 h): FP16 22.3k -> 23.6k MLUPS; FP32 20.2k -> 20.1k, so FP32 and FP64
+// keep one launch.  Results are those of the single launch bit for bit.
+// Threshold: a wall node per LBM_WALL_SPLIT_NODES nodes or more.
+#ifndef LBM_WALL_SPLIT_NODES
+#define LBM_WALL_SPLIT_NODES 400
+#endif
+template <typename S, int QH, bool CUM, bool EQ, bool TRT>
+void launch_plain_step(const Buffers& b, const DevParams& p, cudaStream_t s) {
+    using R = typename Acc<S>::R;
+    const int grid = (p.N + kBlock - 1) / kBlock;
+#define LBM_PLAIN_ARGS                                                                                           \
+    (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, b.seg_base, \
+        b.wmask, b.woff, b.lq, b.lwall, b.Twall, nullptr, nullptr, nullptr, b.wnode, p
+    if constexpr (sizeof(S) == 2) {
+        if (p.nwall > 0 && (int64_t)p.nwall * LBM_WALL_SPLIT_NODES >= (int64_t)p.N) {
+            k_step<S, QH, true, false, CUM, EQ, false, TRT, 1><<<grid, kBlock, 0, s>>>(LBM_PLAIN_ARGS);
+            k_step<S, QH, true, false, CUM, EQ, false, TRT, 2>
+                <<<(p.nwall + kBlock - 1) / kBlock, kBlock, 0, s>>>(LBM_PLAIN_ARGS);
+            return;
+        }
+    }
+    k_step<S, QH, true, false, CUM, EQ, false, TRT, 0><<<grid, kBlock, 0, s>>>(LBM_PLAIN_ARGS);
+#undef LBM_PLAIN_ARGS
+}
+
 template <typename S, int QH>
 cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bool advance_h) {
     using R = typename Acc<S>::R;
@@ -396,7 +475,7 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
     R* urec = (R*)b.urec;
 #define LBM_STEP_ARGS                                                                                            \
     (const S*)b.fA, (S*)b.fB, (const S*)b.hA, (S*)b.hB, b.flags, b.theta, (const R*)b.inlet_post, b.seg_base, \
-        b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, b.frec, b.hrec, p
+        b.wmask, b.woff, b.lq, b.lwall, b.Twall, urec, b.frec, b.hrec, b.wnode, p
     const bool cum = p.hkind == 3, eq = p.wall_bc == 1;
     if (b.frec) {  // pre-collision records for the coupled adjoint (R-typed storage only)
         if constexpr (sizeof(S) == sizeof(R)) {
@@ -416,14 +495,12 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
         const int v = (urec ? 4 : 0) | (cum ? 2 : 0) | (eq ? 1 : 0);
         switch (v) {
             case 0:
-                if (p.hkind == 0)
-                    k_step<S, QH, true, false, false, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
-                else
-                    k_step<S, QH, true, false, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+                if (p.hkind == 0) launch_plain_step<S, QH, false, false, true>(b, p, s);
+                else launch_plain_step<S, QH, false, false, false>(b, p, s);
                 break;
-            case 1: k_step<S, QH, true, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
-            case 2: k_step<S, QH, true, false, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
-            case 3: k_step<S, QH, true, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+            case 1: launch_plain_step<S, QH, false, true, false>(b, p, s); break;
+            case 2: launch_plain_step<S, QH, true, false, false>(b, p, s); break;
+            case 3: launch_plain_step<S, QH, true, true, false>(b, p, s); break;
             case 4: k_step<S, QH, true, true, false, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
             case 5: k_step<S, QH, true, true, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
             case 6: k_step<S, QH, true, true, true, false><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
