@@ -142,6 +142,29 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, int64_t n_links,
                             const float* link_q, const int32_t* link_wall, int n_walls,
                             int is_device);
 
+/* Geometry of a channel with spherical obstacles, built on the device and
+ * installed as by lbm_set_geometry (Sec. 3; the workloads of Sec. 4 are
+ * spheres and cylinders in channels).  centres: host double[3*n_spheres]
+ * (x, y, z), radii: host double[n_spheres], wall_ids: host int32[n_spheres]
+ * in [0, n_walls) or NULL (all 0).  A node is solid when it lies in a closed
+ * ball |x - c|^2 <= R^2, periodic images in y and z included (not in x);
+ * with periodic_x = 0 the planes x = 0 and x = nx-1 are inlet and outlet.  A
+ * fluid node's link a is a wall link when its target x + e_a (inside
+ * 0 <= x < nx) lies in a ball; q is the smallest t in (0, 1] with
+ * |x + t e_a - c| = R, from the node's coordinates in the image frame of
+ * that ball, computed in FP64 with one rounding per operation in the order
+ * d = x - c, e.d = (d_x e_x + d_y e_y) + d_z e_z, d.d likewise,
+ * disc = max((e.d)^2 - |e|^2 (d.d - R^2), 0), t = (-e.d - sqrt(disc)) / |e|^2,
+ * clipped to [smallest positive double, 1] and rounded to float (a float 0
+ * becomes the smallest normal float).  Spheres must not touch one another and
+ * must satisfy lbm_set_geometry's rules.  flags_out: host uint8[N] receiving
+ * the flags (0 fluid, 1 solid, 2 inlet, 3 outlet), or NULL; the links can be
+ * read with lbm_get_links.  Errors: LBM_ERR_INVALID (radius not in
+ * (0, min(ny, nz)/2), wall id out of range, or a rule of lbm_set_geometry),
+ * NOMEM, CUDA. */
+lbm_status lbm_build_spheres(lbm_ctx* ctx, int n_spheres, const double* centres, const double* radii,
+                             const int32_t* wall_ids, int n_walls, uint8_t* flags_out);
+
 /* Dirichlet temperature of wall `wall_id` for Eq. IABB (h^eq_i(x_w) = w_i T_w,
  * wall velocity zero).  Takes effect at the next step. */
 lbm_status lbm_set_bc(lbm_ctx* ctx, int wall_id, double T_wall);

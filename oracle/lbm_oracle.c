@@ -1649,3 +1649,81 @@ int orc_adjoint_flow(orc_sim* s, const double* f_post, const double* h_post, int
     free(muf); free(muh); free(lamf); free(lamh); free(gF); free(frec); free(hrec);
     return 0;
 }
+
+/* ---- geometry of spheres in a channel (Sec. 3: q along the link) ---------
+ * The definition, node by node: a node is solid when it lies in a closed
+ * ball |x - c|^2 <= R^2, periodic images in y and z included (shifts of -1,
+ * 0, +1 periods, enough for 2R below ny and nz), not in x; with periodic_x =
+ * 0 the planes x = 0 and x = nx-1 are inlet (2) and outlet (3).  A fluid
+ * node's link a (target inside 0 <= x < nx, y and z wrapped) is a wall link
+ * when the target lies in a ball; q is the smaller root t of
+ * |d + t e_a|^2 = R^2 with d the node's offset from that ball's centre in the
+ * same image frame, clipped to (0, 1] and rounded to float.  Links come out
+ * sorted by (node, direction).  Returns the number of links; writes at most
+ * cap of them. */
+static int ball_image(double x, double y, double z, int ns, const double* c, const double* r, int ny, int nz,
+                      int* ky, int* kz) {
+    for (int i = 0; i < ns; ++i) {
+        const double RR = r[i] * r[i];
+        for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b) {
+                const double dx = x - c[3 * i], dy = (y + a * ny) - c[3 * i + 1], dz = (z + b * nz) - c[3 * i + 2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 <= RR) {
+                    *ky = a;
+                    *kz = b;
+                    return i;
+                }
+            }
+    }
+    return -1;
+}
+
+int64_t orc_build_spheres(int nx, int ny, int nz, int periodic_x, int ns, const double* centres,
+                          const double* radii, const int* wall_ids, uint8_t* flags, int64_t cap, int* lnode,
+                          int* ldir, float* lq, int* lwall) {
+    const lattice_t* L = lattice(27);
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t n = 0; n < N; ++n) {
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((int64_t)nx * ny));
+        int ky, kz;
+        uint8_t f = 0;
+        if (!periodic_x) f = (x == 0) ? 2 : (x == nx - 1 ? 3 : 0);
+        if (ball_image(x, y, z, ns, centres, radii, ny, nz, &ky, &kz) >= 0) f = 1;
+        flags[n] = f;
+    }
+    int64_t k = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        if (flags[n] != 0) continue;
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((int64_t)nx * ny));
+        for (int a = 1; a < 27; ++a) {
+            const int ex = L->e[a][0], ey = L->e[a][1], ez = L->e[a][2];
+            if (x + ex < 0 || x + ex >= nx) continue;
+            int ky, kz;
+            const int i = ball_image(x + ex, y + ey, z + ez, ns, centres, radii, ny, nz, &ky, &kz);
+            if (i < 0) continue;
+            if (k < cap) {
+                const double dx = x - centres[3 * i];
+                const double dy = (double)(y + ky * ny) - centres[3 * i + 1];
+                const double dz = (double)(z + kz * nz) - centres[3 * i + 2];
+                const double ee = (double)(ex * ex + ey * ey + ez * ez);
+                const double de = dx * ex + dy * ey + dz * ez;
+                const double dd = dx * dx + dy * dy + dz * dz;
+                double disc = de * de - ee * (dd - radii[i] * radii[i]);
+                if (disc < 0.0) disc = 0.0;
+                double t = (-de - sqrt(disc)) / ee;
+                const double tmin = nextafter(0.0, 1.0);
+                if (t < tmin) t = tmin;
+                if (t > 1.0) t = 1.0;
+                float q = (float)t;
+                if (q <= 0.0f) q = 1.17549435e-38f; /* FLT_MIN */
+                lnode[k] = (int)n;
+                ldir[k] = a;
+                lq[k] = q;
+                lwall[k] = wall_ids ? wall_ids[i] : 0;
+            }
+            ++k;
+        }
+    }
+    return k;
+}

@@ -118,7 +118,31 @@ def lib():
                                        C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_wall_force.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_build_spheres.restype = C.c_int64
+        L.orc_build_spheres.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
     return _lib
+
+
+# ---- geometry --------------------------------------------------------------
+def build_spheres(nx, ny, nz, centres, radii, wall_ids=None, periodic_x=False):
+    """Flags and wall links of closed balls in an nx x ny x nz channel
+    (orc_build_spheres: Sec. 3's q along each link, FP64, node by node).
+    Returns (flags uint8[N], links dict of node, dir, q, wall)."""
+    c = np.ascontiguousarray(np.asarray(centres, np.float64).reshape(-1, 3))
+    r = np.ascontiguousarray(np.asarray(radii, np.float64).reshape(-1))
+    w = None if wall_ids is None else np.ascontiguousarray(np.asarray(wall_ids, np.int32).reshape(-1))
+    N = nx * ny * nz
+    flags = np.empty(N, np.uint8)
+    args = (nx, ny, nz, 1 if periodic_x else 0, int(r.size), c.ctypes.data, r.ctypes.data,
+            w.ctypes.data if w is not None else None, flags.ctypes.data)
+    n = lib().orc_build_spheres(*args, 0, None, None, None, None)
+    node = np.empty(n, np.int32); dr = np.empty(n, np.int32)
+    q = np.empty(n, np.float32); wall = np.empty(n, np.int32)
+    m = lib().orc_build_spheres(*args, n, node.ctypes.data, dr.ctypes.data, q.ctypes.data, wall.ctypes.data)
+    assert m == n
+    return flags, {"node": node, "dir": dr, "q": q, "wall": wall}
 
 
 # ---- single-node helpers -------------------------------------------------

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
-SOURCES = (["lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = (["lbm_api.cu", "lbm_noalloc.cu", "lbm_geometry.cu"]
            + [f"lbm_step_{s}_q{q}.cu" for s in ("f32", "f64", "f16", "bf16") for q in (27, 7)]
            + [f"lbm_adjoint_{s}_q{q}.cu" for s in ("f32", "f64") for q in (27, 7)])
 HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh"]

@@ -664,6 +664,79 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, int64_t n_links, c
     return LBM_OK;
 }
 
+lbm_status lbm_build_spheres(lbm_ctx* c, int n_spheres, const double* centres, const double* radii,
+                             const int32_t* wall_ids, int n_walls, uint8_t* flags_out) {
+    if (!c) return LBM_ERR_INVALID;
+    if (n_spheres < 0 || (n_spheres > 0 && (!centres || !radii)))
+        return fail(c, LBM_ERR_INVALID, "bad sphere list");
+    if (n_walls < 1) return fail(c, LBM_ERR_INVALID, "n_walls must be >= 1");
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    std::vector<lbmd::GeoSphere> sp(n_spheres);
+    for (int i = 0; i < n_spheres; ++i) {
+        const double R = radii[i];
+        if (!(R > 0.0) || !(2.0 * R < ny) || !(2.0 * R < nz))
+            return fail(c, LBM_ERR_INVALID, "sphere radius must be positive and below ny/2 and nz/2");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(centres[3 * i + d])) return fail(c, LBM_ERR_INVALID, "sphere centre not finite");
+        const int w = wall_ids ? wall_ids[i] : 0;
+        if (w < 0 || w >= n_walls) return fail(c, LBM_ERR_INVALID, "sphere wall id out of range");
+        sp[i] = {centres[3 * i], centres[3 * i + 1], centres[3 * i + 2], R, w};
+    }
+    DeviceGuard g(c->device);
+    const int64_t N = c->N;
+    const int nb = (int)((N + lbmd::kGeoBlock - 1) / lbmd::kGeoBlock);
+    lbmd::GeoSphere* d_sp = nullptr;
+    uint8_t* d_fl = nullptr;
+    uint32_t* d_mask = nullptr;
+    int* d_bsum = nullptr;
+    int64_t* d_boff = nullptr;
+    int32_t *d_node = nullptr, *d_dir = nullptr, *d_wall = nullptr;
+    float* d_q = nullptr;
+    auto release = [&]() {
+        cudaFree(d_sp); cudaFree(d_fl); cudaFree(d_mask); cudaFree(d_bsum); cudaFree(d_boff);
+        cudaFree(d_node); cudaFree(d_dir); cudaFree(d_q); cudaFree(d_wall);
+    };
+    lbm_status st = LBM_OK;
+    int64_t total = 0;
+    if (dev_alloc(c, &d_sp, std::max<size_t>(1, sp.size()) * sizeof(lbmd::GeoSphere)) != cudaSuccess ||
+        dev_alloc(c, &d_fl, (size_t)N) != cudaSuccess || dev_alloc(c, &d_mask, (size_t)N * 4) != cudaSuccess ||
+        dev_alloc(c, &d_bsum, (size_t)nb * 4) != cudaSuccess ||
+        dev_alloc(c, &d_boff, (size_t)(nb + 1) * 8) != cudaSuccess) {
+        release();
+        return fail(c, LBM_ERR_NOMEM, "sphere geometry: out of device memory");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!sp.empty())
+        e = cudaMemcpyAsync(d_sp, sp.data(), sp.size() * sizeof(lbmd::GeoSphere), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = lbmd::launch_sphere_flags(d_fl, d_mask, nx, ny, nz, c->p.periodic_x, d_sp, n_spheres, d_bsum, d_boff,
+                                      c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_boff + nb, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(c, e, "sphere geometry");
+    }
+    const size_t nl = (size_t)std::max<int64_t>(total, 1);
+    if (dev_alloc(c, &d_node, nl * 4) != cudaSuccess || dev_alloc(c, &d_dir, nl * 4) != cudaSuccess ||
+        dev_alloc(c, &d_q, nl * 4) != cudaSuccess || dev_alloc(c, &d_wall, nl * 4) != cudaSuccess) {
+        release();
+        return fail(c, LBM_ERR_NOMEM, "sphere geometry links: out of device memory");
+    }
+    e = lbmd::launch_sphere_links(d_mask, nx, ny, nz, d_sp, n_spheres, d_boff, d_node, d_dir, d_q, d_wall,
+                                  c->stream);
+    if (e == cudaSuccess && flags_out)
+        e = cudaMemcpyAsync(flags_out, d_fl, (size_t)N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(c, e, "sphere geometry links");
+    }
+    st = lbm_set_geometry(c, d_fl, total, d_node, d_dir, d_q, d_wall, n_walls, 1);
+    release();
+    return st;
+}
+
 lbm_status lbm_set_bc(lbm_ctx* c, int wall_id, double T_wall) {
     if (!c) return LBM_ERR_INVALID;
     DeviceGuard g(c->device);

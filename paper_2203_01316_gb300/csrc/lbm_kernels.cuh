@@ -104,6 +104,22 @@ cudaError_t launch_wall_force(const Buffers& b, const DevParams& p, int wall, do
                               cudaStream_t s);
 cudaError_t launch_stream_map(const Buffers& b, const DevParams& p, int qh, int32_t* src, cudaStream_t s);
 
+// ---- geometry of spheres built on the device (lbm_geometry.cu) ----
+struct GeoSphere {
+    double cx, cy, cz, R;
+    int wall;
+};
+constexpr int kGeoBlock = 256;
+// flags[N] (0 fluid, 1 solid, 2 inlet, 3 outlet), the link masks of the fluid
+// nodes, per-block link counts bsum[nb] and their exclusive sums boff[nb + 1]
+// (boff[nb] = total), nb = ceil(N / kGeoBlock)
+cudaError_t launch_sphere_flags(uint8_t* flags, uint32_t* mask, int nx, int ny, int nz, int periodic_x,
+                                const GeoSphere* sp, int ns, int* bsum, int64_t* boff, cudaStream_t s);
+// the links, sorted by (node, direction), into arrays of boff[nb] entries
+cudaError_t launch_sphere_links(const uint32_t* mask, int nx, int ny, int nz, const GeoSphere* sp, int ns,
+                                const int64_t* boff, int32_t* lnode, int32_t* ldir, float* lq, int32_t* lwall,
+                                cudaStream_t s);
+
 #ifdef LBM_KERNEL_TU
 
 // ---- pull addressing -------------------------------------------------------

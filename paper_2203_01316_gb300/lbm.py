@@ -27,7 +27,7 @@ SYMBOLS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_set_bc", "lbm_s
            "lbm_stream_map", "lbm_get_links", "lbm_sync", "lbm_last_error", "lbm_balances_noalloc",
            "lbm_section_flux", "lbm_objective_accumulate", "lbm_step_record", "lbm_adjoint_step",
            "lbm_adjoint_wall_gradient", "lbm_step_record_h", "lbm_adjoint_step_h", "lbm_step_record_pre",
-           "lbm_flow_record_size", "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient", "lbm_wall_force"]
+           "lbm_flow_record_size", "lbm_build_spheres", "lbm_adjoint_flow_step", "lbm_adjoint_flow_gradient", "lbm_wall_force"]
 OBJ_SURFACE, OBJ_SECTION, OBJ_FORCE = 0, 1, 2
 
 
@@ -96,6 +96,7 @@ def lib():
         "lbm_step_record_h": [vp, i32, vp, vp],
         "lbm_step_record_pre": [vp, i32, vp, vp],
         "lbm_flow_record_size": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "lbm_build_spheres": [vp, i32, vp, vp, vp, i32, vp],
         "lbm_adjoint_flow_step": [vp, vp, vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
         "lbm_adjoint_flow_gradient": [vp, C.POINTER(dbl), C.POINTER(dbl), i32],
         "lbm_adjoint_step_h": [vp, vp, vp, vp, vp, C.POINTER(Objective), vp],
@@ -207,6 +208,19 @@ class Solver:
         if len({fdev, n_dev, d_dev, q_dev, w_dev}) != 1:
             raise ValueError("flags and links must all be host arrays or all device tensors")
         self._check(self.L.lbm_set_geometry(self._h, fp, len(links["node"]), n_p, d_p, q_p, w_p, int(n_walls), fdev))
+
+    def build_spheres(self, centres, radii, wall_ids=None, n_walls=1):
+        """Geometry of closed balls (centres [n, 3], radii [n]) built on the
+        device and installed; returns the flags (uint8[N])."""
+        c = np.ascontiguousarray(np.asarray(centres, np.float64).reshape(-1, 3))
+        r = np.ascontiguousarray(np.asarray(radii, np.float64).reshape(-1))
+        w = None if wall_ids is None else np.ascontiguousarray(np.asarray(wall_ids, np.int32).reshape(-1))
+        flags = np.empty(self.N, np.uint8)
+        self._check(self.L.lbm_build_spheres(self._h, int(r.size), c.ctypes.data if r.size else None,
+                                             r.ctypes.data if r.size else None,
+                                             w.ctypes.data if w is not None else None, int(n_walls),
+                                             flags.ctypes.data))
+        return flags
 
     def set_bc(self, wall, T):
         self._check(self.L.lbm_set_bc(self._h, int(wall), float(T)))
