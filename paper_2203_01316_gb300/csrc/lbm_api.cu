@@ -95,6 +95,20 @@ template <typename T> cudaError_t dev_alloc(lbm_ctx* c, T** p, size_t bytes) {
     return cudaMalloc((void**)p, bytes);
 }
 
+// multiplier and shift of node_xyz's division by d (see DevParams::mx)
+static void fast_divisor(int d, uint32_t& m, int& s) {
+    if (d <= 1) {
+        m = 0;
+        s = 0;
+        return;
+    }
+    int l = 1;
+    while ((int64_t(1) << l) < d) ++l;
+    const uint64_t num = uint64_t(1) << (31 + l);
+    m = (uint32_t)((num + (uint64_t)d - 1) / (uint64_t)d);
+    s = l - 1;
+}
+
 template <typename S_, int Q_> struct Tag {
     using S = S_;
     static constexpr int Q = Q_;
@@ -367,6 +381,8 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     d.wall_bc = p.wall_bc;
     d.zou_he = (p.inlet_bc == LBM_INLET_ZOU_HE && !p.periodic_x) ? 1 : 0;
     d.nwall = 0;
+    fast_divisor(p.nx, d.mx, d.sx);
+    fast_divisor(p.ny, d.my, d.sy);
     d.step = 0;
     for (int i = 0; i < 3; ++i) d.F[i] = d.uin[i] = 0.0;
     d.Tin = 0.0;

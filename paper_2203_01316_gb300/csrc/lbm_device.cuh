@@ -317,6 +317,11 @@ struct DevParams {
     int mirror_lo, mirror_hi;  // rows y = 0 / y = ny-1 are symmetry rows
     int zou_he;                // inlet plane: 0 fixed equilibria, 1 Zou-He (k_inlet after the step)
     int nwall;                 // wall nodes (entries of the wall table)
+    // n / nx and r / ny for 0 <= n, r < 2^31 as umulhi(n, m) >> s (the
+    // round-up method for 31-bit dividends: m = ceil(2^(31+l) / d),
+    // l = ceil(log2 d) >= 1, s = l - 1); m = 0 for a divisor of 1
+    uint32_t mx, my;
+    int sx, sy;
     uint32_t step;       // time level being written (seeds the stochastic rounding)
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6

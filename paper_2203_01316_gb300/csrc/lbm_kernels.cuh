@@ -130,10 +130,11 @@ struct Nbr {
 };
 
 __device__ __forceinline__ void node_xyz(int n, const DevParams& p, int& x, int& y, int& z) {
-    x = n % p.nx;
-    const int r = n / p.nx;
-    y = r % p.ny;
-    z = r / p.ny;
+    const uint32_t r = p.mx ? __umulhi((uint32_t)n, p.mx) >> p.sx : (uint32_t)n;  // n / nx
+    const uint32_t q = p.my ? __umulhi(r, p.my) >> p.sy : r;                      // r / ny
+    x = n - (int)r * p.nx;
+    y = (int)r - (int)q * p.ny;
+    z = (int)q;
 }
 
 __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const DevParams& p) {
@@ -177,7 +178,8 @@ __device__ __forceinline__ uint32_t soa(int i, int N, int node) {
 // low value, bits 16-28 the high one; BF16: bits 0-15 and 16-31): the value
 // rounds up in magnitude with probability equal to the discarded fraction,
 // so rounding errors have zero mean.  The 32 bits are one draw of the node's
-// stream.
+// stream, which starts at a hash of (node, time level) and serves the f stores
+// and then the h stores.
 template <bool SR> __device__ __forceinline__ uint32_t cvt_pair(__half*, float hi, float lo, uint32_t r) {
     uint32_t d;
     if constexpr (SR) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
@@ -192,9 +194,7 @@ template <bool SR> __device__ __forceinline__ uint32_t cvt_pair(__nv_bfloat16*, 
 }
 // v[0..Q) of node n into X[i * N + n] (16-bit storage)
 template <bool SR, typename S, int Q>
-__device__ __forceinline__ void store16(S* __restrict__ X, const float* v, int n, int N, uint32_t key,
-                                        uint32_t step) {
-    SrStream rs{sr_bits(key, step)};
+__device__ __forceinline__ void store16(S* __restrict__ X, const float* v, int n, int N, SrStream& rs) {
 #pragma unroll
     for (int i = 0; i < Q; i += 2) {
         const float hi = (i + 1 < Q) ? v[i + 1] : 0.0f;
@@ -207,13 +207,13 @@ __device__ __forceinline__ void store16(S* __restrict__ X, const float* v, int n
 template <typename S, int QH>
 __device__ __forceinline__ void collide_store_f(typename Acc<S>::R* fd, S* __restrict__ fB, int n,
                                                 const DevParams& p, typename Acc<S>::R& ux,
-                                                typename Acc<S>::R& uy, typename Acc<S>::R& uz) {
+                                                typename Acc<S>::R& uy, typename Acc<S>::R& uz, SrStream& rs) {
     using R = typename Acc<S>::R;
     R rho;
     collide_f<R>(fd, p, ux, uy, uz, rho);
     if constexpr (sizeof(S) == 2) {
-        if (p.stochastic) store16<true, S, 27>(fB, fd, n, p.N, (uint32_t)n << 1, p.step);
-        else store16<false, S, 27>(fB, fd, n, p.N, 0u, 0u);
+        if (p.stochastic) store16<true, S, 27>(fB, fd, n, p.N, rs);
+        else store16<false, S, 27>(fB, fd, n, p.N, rs);
     } else {
 #pragma unroll
         for (int a = 0; a < 27; ++a) st(fB + soa(a, p.N, n), fd[a]);
@@ -224,7 +224,7 @@ template <typename S, int QH, bool CUM = false, bool TRT = false>
 __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __restrict__ hB, int n,
                                                 const DevParams& p, typename Acc<S>::R ux,
                                                 typename Acc<S>::R uy, typename Acc<S>::R uz,
-                                                typename Acc<S>::R Q) {
+                                                typename Acc<S>::R Q, SrStream& rs) {
     using R = typename Acc<S>::R;
     if constexpr (sizeof(R) == 4) {
         // FP32 arithmetic: the transforms' roundings bias the zeroth moment of
@@ -241,8 +241,8 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
         collide_h<R, QH, CUM, TRT>(hd, ux, uy, uz, Q, p);
     }
     if constexpr (sizeof(S) == 2) {
-        if (p.stochastic) store16<true, S, QH>(hB, hd, n, p.N, ((uint32_t)n << 1) | 1u, p.step);
-        else store16<false, S, QH>(hB, hd, n, p.N, 0u, 0u);
+        if (p.stochastic) store16<true, S, QH>(hB, hd, n, p.N, rs);
+        else store16<false, S, QH>(hB, hd, n, p.N, rs);
     } else {
 #pragma unroll
         for (int i = 0; i < QH; ++i) st(hB + soa(i, p.N, n), hd[i]);
@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     int x, y, z;
     node_xyz(n, p, x, y, z);
     const Nbr nb = make_nbr(x, y, z, p);
+    SrStream rs{sr_bits((uint32_t)n, p.step)};  // 16-bit stochastic rounding: f stores, then h
     R fd[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + soa(a, N, src_of(nb, a)));
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
 #pragma unroll
         for (int k = 0; k < 10; ++k) ((R*)frec)[soa(k, N, n)] = m[k];
     }
-    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
+    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz, rs);
     if (REC) {
         urec[n] = ux;
         urec[N + n] = uy;
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
 #pragma unroll
         for (int i = 0; i < QH; ++i) ((R*)hrec)[soa(i, N, n)] = hd[i];
     }
-    collide_store_h<S, QH, CUM, TRT>(hd, hB, n, p, ux, uy, uz, Q);
+    collide_store_h<S, QH, CUM, TRT>(hd, hB, n, p, ux, uy, uz, Q, rs);
     }
 }
 
@@ -562,8 +563,9 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restri
     R hd[QH];
     heq_dev<R, QH>(hd, (R)(rho[n] * T[n] - p.Tref) - R(0.5) * Q, vx, vy, vz, p);
     R ux, uy, uz;
-    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz);
-    collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q);
+    SrStream rs{sr_bits((uint32_t)n, p.step)};
+    collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz, rs);
+    collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q, rs);
 }
 
 template <typename S, int QH>
@@ -1342,7 +1344,8 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
         for (int a = 0; a < 27; ++a) inl[(size_t)a * p.ny * p.nz + i] = fd[a];
     }
     R vx, vy, vz;
-    collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz);
+    SrStream rs{sr_bits((uint32_t)n, p.step)};
+    collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz, rs);
     if (urec) {
         urec[n] = vx;
         urec[N + n] = vy;
@@ -1361,7 +1364,7 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
             for (int k = 0; k < QH; ++k) ((R*)hrec)[k * N + n] = hd[k];
         }
         const R Q = theta ? (R)__ldg(theta + n) : R(0);
-        collide_store_h<S, QH, CUM>(hd, hB, n, p, vx, vy, vz, Q);
+        collide_store_h<S, QH, CUM>(hd, hB, n, p, vx, vy, vz, Q, rs);
     }
 }
 
