@@ -249,6 +249,15 @@ __device__ __forceinline__ void collide_store_h(typename Acc<S>::R* hd, S* __res
     }
 }
 
+// the division of the q > 1/2 link rule: the denominator 2q lies in [1, 2],
+// where the fast FP32 division is within 2 ulp and needs no range checks
+// (porous bed: +2% with the wall nodes' warps serialised on these bodies);
+// FP64 keeps the correctly rounded division
+template <typename R> __device__ __forceinline__ R wdiv(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fdividef(a, b);
+    else return a / b;
+}
+
 // ---- the step: pull streaming, Eq. IBB / Eq. IABB on wall links, planes,
 // collision of f and h; one thread per node --------------------------------
 // Wall nodes find their entry in the wall table without a search: the nodes
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
             const R fb_b = has ? ld<R>(fA + soa(b, N, n)) : R(0);
             const R qq = (R)fmaxf(q, 0.5f);
             const R v_lin = R(2) * (R)q * fa_b + (R(1) - R(2) * (R)q) * fd[a];
-            const R v_far = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
+            const R v_far = wdiv<R>(fa_b + (R(2) * qq - R(1)) * fb_b, R(2) * qq);
             const R v = (q <= 0.5f && !thin) ? v_lin : v_far;
             fd[b] = has ? v : fd[b];
         }
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
             } else {
                 const R qq = (R)fmaxf(q, 0.5f);
                 const R fb_b = ld<R>(fA + soa(b, N, n));
-                fd[b] = (fa_b + (R(2) * qq - R(1)) * fb_b) / (R(2) * qq);
+                fd[b] = wdiv<R>(fa_b + (R(2) * qq - R(1)) * fb_b, R(2) * qq);
             }
         }
     }
@@ -413,7 +422,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
                 const R hb_b = has ? ld<R>(hA + soa(ib, N, n)) : R(0);
                 const R qq = (R)fmaxf(q, 0.5f);
                 const R v_lin = -(R(2) * (R)q * ha_b + (R(1) - R(2) * (R)q) * hd[ia]) + heq2;
-                const R v_far = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+                const R v_far = wdiv<R>(-ha_b + (R(2) * qq - R(1)) * hb_b + heq2, R(2) * qq);
                 v = (q <= 0.5f && !thin) ? v_lin : v_far;
             }
             hd[ib] = has ? v : hd[ib];
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
             } else {
                 const R qq = (R)fmaxf(q, 0.5f);
                 const R hb_b = ld<R>(hA + soa(ib, N, n));
-                hd[ib] = (-ha_b + (R(2) * qq - R(1)) * hb_b + heq2) / (R(2) * qq);
+                hd[ib] = wdiv<R>(-ha_b + (R(2) * qq - R(1)) * hb_b + heq2, R(2) * qq);
             }
         }
     }
