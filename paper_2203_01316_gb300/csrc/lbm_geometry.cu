@@ -30,6 +30,9 @@ __device__ __forceinline__ double dist2(double x, double y, double z, const Sphe
 // plus a step; -1 if none
 __device__ int ball_of(int x, int y, int z, const Sphere* sp, int ns, int ny, int nz, int& ky, int& kz) {
     for (int i = 0; i < ns; ++i) {
+        // x has no images: a point more than R + 1 away along x is outside by a
+        // margin no rounding can close, so the exact test below is skipped
+        if (fabs((double)x - sp[i].cx) > sp[i].R + 1.0) continue;
         const double RR = __dmul_rn(sp[i].R, sp[i].R);
         for (int a = -1; a <= 1; ++a)
             for (int b = -1; b <= 1; ++b) {
