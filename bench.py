@@ -947,6 +947,8 @@ def run_ours(args):
     line["e2e"] = e2e
     line["storage_variants"] = variants
     line["adjoint"] = measure_adjoint(w, stream, ms, steps=args.adjoint_steps)
+    if args.flow_adjoint_steps > 0:  # the coupled f + h adjoint (gradients for F and u_in too)
+        line["flow_adjoint"] = measure_flow_adjoint(w, stream, ms, steps=args.flow_adjoint_steps)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
@@ -972,6 +974,8 @@ def main():
                     help="scale the workload grid (profiling of a smaller case)")
     ap.add_argument("--storage", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--flow-adjoint-steps", type=int, default=100,
+                    help="levels of the coupled-adjoint leg of the bench line (0: skip it)")
     ap.add_argument("--flow-adjoint", action="store_true",
                     help="time the coupled f + h adjoint (gradients for F and u_in) on the workload")
     ap.add_argument("--storages", default="", help="validation hill, nusselt study: comma-separated storages")
