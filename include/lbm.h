@@ -105,11 +105,12 @@ typedef enum { LBM_WALL_IBB_IABB = 0, LBM_WALL_BB_EQ = 1, LBM_WALL_BB_ABB = 2 } 
  * kernel (f and h of a node in one thread; the fastest measured on GB300).
  * LBM_STEP_AUTO replays a CUDA graph of two steps for calls of 4 or more
  * steps (captured on the context's stream at first use and again whenever
- * the buffers or parameters it captured change; not for stochastically
- * rounded 16-bit storage, whose rounding follows the step count), which
- * removes the launch gaps that dominate small grids; results are
- * bit-identical to LBM_STEP_CLASSIC, which launches every step.  While the
- * caller is capturing the context's stream, lbm_step launches every step. */
+ * the buffers or parameters it captured change; with 16-bit storage the
+ * graph advances a device copy of the time level that seeds the stochastic
+ * rounding), which removes the launch gaps that dominate small grids;
+ * results are bit-identical to LBM_STEP_CLASSIC, which launches every step.
+ * While the caller is capturing the context's stream, lbm_step launches
+ * every step. */
 typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_CLASSIC = 1 } lbm_step_kernel;
 
 /* Create a context and allocate its device state.  The populations are zero

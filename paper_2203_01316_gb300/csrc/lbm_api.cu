@@ -45,6 +45,7 @@ struct lbm_ctx {
     double* d_flowacc = nullptr;    // coupled adjoint: per node (dJ/dF, dJ/du_in) accumulators, [N][6]
     void* d_din = nullptr;          // coupled adjoint: d(inlet state)/du_in, R[3][27 + qh]
     void* d_wflow = nullptr;        // coupled adjoint: velocity derivative of the h step, R[3][N]
+    uint32_t* d_stepctr = nullptr;  // 16-bit storage: the time level replayed step graphs read
     std::vector<double> h_din;      // the uploaded copy of d_din
     int n_walls = 1;
     float* d_Twall = nullptr;
@@ -354,6 +355,8 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
         dev_alloc(c, &c->d_scratch, (3 * lbmd::kRedBlocks + 4) * sizeof(double)) != cudaSuccess ||
         dev_alloc(c, &c->d_Twall, sizeof(float)) != cudaSuccess)
         return bail(fail(c, LBM_ERR_NOMEM, "context buffers: out of device memory"));
+    if (c->ssize == 2 && dev_alloc(c, &c->d_stepctr, sizeof(uint32_t)) != cudaSuccess)
+        return bail(fail(c, LBM_ERR_NOMEM, "step counter: out of device memory"));
 
     cudaMemsetAsync(c->d_flags, 0, N, c->stream);
     cudaMemsetAsync(c->d_Twall, 0, sizeof(float), c->stream);
@@ -381,6 +384,7 @@ lbm_status lbm_create(const lbm_params* params, lbm_ctx** out) {
     d.wall_bc = p.wall_bc;
     d.zou_he = (p.inlet_bc == LBM_INLET_ZOU_HE && !p.periodic_x) ? 1 : 0;
     d.nwall = 0;
+    d.step_ctr = nullptr;
     fast_divisor(p.nx, d.mx, d.sx);
     fast_divisor(p.ny, d.my, d.sy);
     d.step = 0;
@@ -413,6 +417,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_flowacc);
     cudaFree(c->d_din);
     cudaFree(c->d_wflow);
+    cudaFree(c->d_stepctr);
     for (auto& gr : c->graphs)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -864,11 +869,26 @@ static cudaError_t fill_mirror(lbm_ctx* c, const Buffers& b, const DevParams& p)
 }
 
 // the launches of one plain step (symmetry rows, the step, the Zou-He inlet)
-static lbm_status step_once(lbm_ctx* c) {
+// the time-level counter of replayed 16-bit step graphs: set before a run
+// of replays, advanced inside each captured step
+__global__ void k_step_counter(uint32_t* ctr, uint32_t value, int advance) {
+    if (advance) *ctr += 1u;
+    else *ctr = value;
+}
+
+// one plain step; in_graph: the step is being captured for replay, so with
+// stochastically rounded 16-bit storage its kernels read the time level from
+// the device counter, which the step advances first
+static lbm_status step_once(lbm_ctx* c, bool in_graph = false) {
     const Buffers b = buffers(c);
     c->dp.step += 1;
-    const DevParams p = c->dp;
+    DevParams p = c->dp;
     cudaError_t e;
+    if (in_graph && c->d_stepctr) {
+        k_step_counter<<<1, 1, 0, c->stream>>>(c->d_stepctr, 0u, 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "step counter launch");
+        p.step_ctr = c->d_stepctr;
+    }
     if ((e = fill_mirror(c, b, p)) != cudaSuccess) return cuda_fail(c, e, "symmetry rows launch");
     e = dispatch(c, [&](auto tag) {
         using Tg = decltype(tag);
@@ -885,9 +905,9 @@ static lbm_status step_once(lbm_ctx* c) {
 // (captured on first use, cached in two slots), or nullptr when none can be
 // had (the stream is being captured by the caller, or capture failed).  Two
 // steps bring the A/B buffers back to the same roles, so the graph replays
-// as long as the signature matches; the step counter is not part of it, so
-// graphs serve only storage whose kernels ignore that counter (everything
-// but stochastically rounded 16-bit storage).
+// as long as the signature matches; the step counter is not part of it (the
+// stochastic rounding of 16-bit storage reads the time level from a device
+// counter that the graph advances).
 static lbm_ctx::StepGraph* step_graph(lbm_ctx* c) {
     lbm_ctx::StepGraph key;
     key.b = buffers(c);
@@ -908,8 +928,8 @@ static lbm_ctx::StepGraph* step_graph(lbm_ctx* c) {
     lbm_status st = LBM_OK;
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = step_once(c);
-        if (st == LBM_OK) st = step_once(c);
+        st = step_once(c, true);
+        if (st == LBM_OK) st = step_once(c, true);
         e = cudaStreamEndCapture(c->stream, &graph);
     }
     // the captured launches did not run: undo their bookkeeping
@@ -939,12 +959,17 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "initialise the fields first");
     DeviceGuard g(c->device);
     // launch-bound stretches replay graphs of two steps (LBM_STEP_AUTO)
-    const bool graphs = c->p.step_kernel == LBM_STEP_AUTO && !c->graph_broken && n >= 4 &&
-                        !(c->ssize == 2 && c->dp.stochastic);
+    const bool graphs = c->p.step_kernel == LBM_STEP_AUTO && !c->graph_broken && n >= 4;
     if (graphs) {
+        bool counter_set = false;
         while (n >= 2) {
             lbm_ctx::StepGraph* gr = step_graph(c);
             if (!gr) break;
+            if (c->d_stepctr && !counter_set) {  // the graph's steps continue from dp.step
+                k_step_counter<<<1, 1, 0, c->stream>>>(c->d_stepctr, c->dp.step, 0);
+                CK(cudaGetLastError(), "step counter launch");
+                counter_set = true;
+            }
             CK(cudaGraphLaunch(gr->exec, c->stream), "step graph launch");
             c->dp.step += 2;
             n -= 2;

@@ -323,6 +323,9 @@ struct DevParams {
     uint32_t mx, my;
     int sx, sy;
     uint32_t step;       // time level being written (seeds the stochastic rounding)
+    // in replayed CUDA graphs the time level is read from this device counter,
+    // which the graph advances before each step (nullptr: use step)
+    const uint32_t* step_ctr;
     double omega1, omega_bulk;  // f: shear and bulk rates
     double sh[7];               // h: rate of central moments of each order 0..6
     double rho0, Tref;

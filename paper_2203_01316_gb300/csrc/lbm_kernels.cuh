@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kBlock, step_min_blocks<S, QH>()) k_step(const
     int x, y, z;
     node_xyz(n, p, x, y, z);
     const Nbr nb = make_nbr(x, y, z, p);
-    SrStream rs{sr_bits((uint32_t)n, p.step)};  // 16-bit stochastic rounding: f stores, then h
+    SrStream rs{sr_bits((uint32_t)n, p.step_ctr ? *p.step_ctr : p.step)};  // 16-bit stochastic rounding: f stores, then h
     R fd[27];
 #pragma unroll
     for (int a = 0; a < 27; ++a) fd[a] = ld<R>(fA + soa(a, N, src_of(nb, a)));
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kBlock) k_init(S* __restrict__ fB, S* __restri
     R hd[QH];
     heq_dev<R, QH>(hd, (R)(rho[n] * T[n] - p.Tref) - R(0.5) * Q, vx, vy, vz, p);
     R ux, uy, uz;
-    SrStream rs{sr_bits((uint32_t)n, p.step)};
+    SrStream rs{sr_bits((uint32_t)n, p.step_ctr ? *p.step_ctr : p.step)};
     collide_store_f<S, QH>(fd, fB, n, p, ux, uy, uz, rs);
     collide_store_h<S, QH, CUM>(hd, hB, n, p, ux, uy, uz, Q, rs);
 }
@@ -1353,7 +1353,7 @@ __global__ void __launch_bounds__(kBlock) k_inlet(const S* __restrict__ fA, S* _
         for (int a = 0; a < 27; ++a) inl[(size_t)a * p.ny * p.nz + i] = fd[a];
     }
     R vx, vy, vz;
-    SrStream rs{sr_bits((uint32_t)n, p.step)};
+    SrStream rs{sr_bits((uint32_t)n, p.step_ctr ? *p.step_ctr : p.step)};
     collide_store_f<S, QH>(fd, fB, n, p, vx, vy, vz, rs);
     if (urec) {
         urec[n] = vx;

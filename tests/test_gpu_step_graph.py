@@ -2,8 +2,9 @@
 the same bits as LBM_STEP_CLASSIC, which launches every step: over an odd
 number of steps (graph replays plus a plain step), across parameter changes
 between calls (the graph is captured again), with the three launches of a
-step with symmetry rows and the Zou-He inlet, in FP32 and FP64, and with
-stochastically rounded FP16 storage (which keeps plain launches)."""
+step with symmetry rows and the Zou-He inlet, in FP32, FP64 and with
+stochastically rounded FP16 and BF16 storage (whose graphs advance a device
+copy of the time level that seeds the rounding)."""
 import numpy as np
 import pytest
 
@@ -25,7 +26,7 @@ def _same(a, b):
     assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
 def test_graph_steps_equal_plain_steps(storage):
     w = I.heated_sphere(38, 19, 11, D=7.0, cx=12.0, seed=7, u_in=0.03, T_in=0.2)
     a, b = _both(lambda k: make_pair(w, nu=0.03, k=2e-3, storage=storage, wall_T=(0.8,), T_ref=0.2,
