@@ -13,8 +13,16 @@ checkpoint, recomputes the velocity of every level of the segment, then runs
 the adjoint kernel level by level.  For the central-moment kinds the h step
 is affine and its adjoint needs only u, so the recomputation advances f only;
 the Cumulants-1st collision is nonlinear in h, so there the recomputation
-advances h as well and keeps each level's post-collision h for the adjoint.  All arithmetic runs in the CUDA library; this module only
-orders the calls and owns the device buffers (torch tensors).
+advances h as well and keeps each level's post-collision h for the adjoint.
+
+Two-level checkpointing (every2 < every): the backward first re-runs each
+segment from its checkpoint keeping a second-level checkpoint every `every2`
+steps, then treats each sub-segment as above.  Memory: nsteps/every + every/
+every2 states plus every2 levels of records instead of nsteps/every states
+plus every levels of records, for one more forward pass; the recomputed
+states and records are the same bits, so the gradients are too.  All
+arithmetic runs in the CUDA library; this module only orders the calls and
+owns the device buffers (torch tensors).
 """
 from __future__ import annotations
 
@@ -25,9 +33,10 @@ from .lbm import Solver
 
 class ThermalObjective(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, T_wall, solver: Solver, state0, nsteps: int, window, objective, every: int):
-        if every < 1:
-            raise ValueError("checkpoint interval must be >= 1")
+    def forward(ctx, theta, T_wall, solver: Solver, state0, nsteps: int, window, objective, every: int,
+                every2=None):
+        if every < 1 or (every2 is not None and every2 < 1):
+            raise ValueError("checkpoint intervals must be >= 1")
         dev = state0.device
         # the solver runs on its own stream: order it after torch's work on
         # the inputs, and torch's later work after the solver's
@@ -49,6 +58,7 @@ class ThermalObjective(torch.autograd.Function):
         solver.sync()
         ctx.solver, ctx.ckpts, ctx.nsteps, ctx.window = solver, ckpts, nsteps, window
         ctx.objective, ctx.every, ctx.n_walls = objective, every, T_wall.numel()
+        ctx.every2 = every2
         ctx.theta_dtype, ctx.Tw_dtype = theta.dtype, T_wall.dtype
         ctx.theta_device, ctx.Tw_device = theta.device, T_wall.device
         return J[0]
@@ -66,20 +76,33 @@ class ThermalObjective(torch.autograd.Function):
         s.adjoint_wall_gradient(ctx.n_walls, reset=True)
         lo, hi = ctx.window
         starts = sorted(ctx.ckpts)
+        every2 = ctx.every2 if ctx.every2 is not None else ctx.every
         for seg_start in reversed(starts):
             seg_end = min(seg_start + ctx.every, ctx.nsteps)
-            L = seg_end - seg_start
             s.load_state(ctx.ckpts[seg_start])
-            urec = torch.empty(L * 3 * N, dtype=rdt, device=dev)
-            hrec = torch.empty(L * qh * N, dtype=rdt, device=dev) if s.cumulant_h else None
-            s.step_record(L, urec, advance_h=False, h_rec=hrec)
-            for k in range(seg_end, seg_start, -1):
-                obj = ctx.objective if lo <= k <= hi else None
-                j = k - seg_start - 1
-                u_k = urec[j * 3 * N:(j + 1) * 3 * N]
-                h_k = hrec[j * qh * N:(j + 1) * qh * N] if hrec is not None else None
-                s.adjoint_step(u_k, mu_next, mu_out, obj, dtheta, h_level=h_k)
-                mu_next, mu_out = mu_out, mu_next
+            if every2 < seg_end - seg_start:  # second level: states every every2 steps of the segment
+                inner = {}
+                for k in range(seg_start, seg_end):
+                    if (k - seg_start) % every2 == 0:
+                        inner[k] = s.save_state(torch.empty_like(ctx.ckpts[seg_start]))
+                    s.step(1)
+            else:
+                inner = {seg_start: None}
+            for sub_start in sorted(inner, reverse=True):
+                sub_end = min(sub_start + every2, seg_end)
+                L = sub_end - sub_start
+                if inner[sub_start] is not None:
+                    s.load_state(inner[sub_start])
+                urec = torch.empty(L * 3 * N, dtype=rdt, device=dev)
+                hrec = torch.empty(L * qh * N, dtype=rdt, device=dev) if s.cumulant_h else None
+                s.step_record(L, urec, advance_h=False, h_rec=hrec)
+                for k in range(sub_end, sub_start, -1):
+                    obj = ctx.objective if lo <= k <= hi else None
+                    j = k - sub_start - 1
+                    u_k = urec[j * 3 * N:(j + 1) * 3 * N]
+                    h_k = hrec[j * qh * N:(j + 1) * qh * N] if hrec is not None else None
+                    s.adjoint_step(u_k, mu_next, mu_out, obj, dtheta, h_level=h_k)
+                    mu_next, mu_out = mu_out, mu_next
         # level 0: the initial state is given; only its objective and wall terms remain
         obj0 = ctx.objective if lo <= 0 <= hi else None
         s.adjoint_step(None, mu_next, mu_out, obj0, None)
@@ -87,13 +110,14 @@ class ThermalObjective(torch.autograd.Function):
         gJ = gJ.to(torch.float64)
         g_theta = (gJ.to(dtheta.device) * dtheta).to(device=ctx.theta_device, dtype=ctx.theta_dtype)
         g_Tw = (gJ.cpu() * torch.from_numpy(dTw)).to(device=ctx.Tw_device, dtype=ctx.Tw_dtype)
-        return g_theta, g_Tw, None, None, None, None, None, None
+        return g_theta, g_Tw, None, None, None, None, None, None, None
 
 
-def thermal_objective(theta, T_wall, solver, state0, nsteps, window, objective, every=50):
+def thermal_objective(theta, T_wall, solver, state0, nsteps, window, objective, every=50, every2=None):
     """J(theta, T_wall) with gradients by the adjoint (see module docstring).
-    state0: CUDA uint8 tensor from solver.save_state(out=...)."""
-    return ThermalObjective.apply(theta, T_wall, solver, state0, nsteps, window, objective, every)
+    state0: CUDA uint8 tensor from solver.save_state(out=...); every2 (optional,
+    below every) turns on the second checkpoint level."""
+    return ThermalObjective.apply(theta, T_wall, solver, state0, nsteps, window, objective, every, every2)
 
 
 class FlowObjective(torch.autograd.Function):

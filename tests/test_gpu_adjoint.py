@@ -211,3 +211,31 @@ def test_config4_adjoint_vs_fp64_finite_differences():
         for st in ("f32", "f64"):
             assert abs(grads[st][2][wall] - fd) <= 1e-4 * abs(fd), (st, wall, grads[st][2][wall], fd)
     assert math.isfinite(J0)
+
+
+@pytest.mark.parametrize("kind", ["trt", "cum1st"])
+def test_two_level_checkpoints_give_the_same_gradients(kind):
+    """every2 < every re-runs each segment keeping second-level states; the
+    recomputed states and records are the same bits, so J and both gradients
+    are identical to the one-level run."""
+    torch = _torch()
+    from paper_2203_01316_gb300.autograd import thermal_objective
+    w = _plate()
+    N = len(w["rho"])
+    theta = I.uniform(23, N, 0.0, 1e-3)
+    theta[np.asarray(w["flags"]) == I.SOLID] = 0.0
+    s = _solver(w, "f32", 27, kind, 0.05, 0.01, (1e-5, 0.0, 0.0), [1.0, 0.1], theta)
+    obj = s.objective("surface", 1, 1.0)
+    state0 = s.save_state(torch.empty(s.state_size(), dtype=torch.uint8, device="cuda"))
+    out = []
+    for every, every2 in ((12, None), (12, 5), (12, 1)):
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+        tw = torch.tensor([1.0, 0.1], dtype=torch.float64, requires_grad=True)
+        J = thermal_objective(th, tw, s, state0, 31, (20, 31), obj, every=every, every2=every2)
+        J.backward()
+        out.append((float(J.item()), th.grad.cpu().numpy(), tw.grad.numpy()))
+    for J, g, gw in out[1:]:
+        assert J == out[0][0]
+        assert np.array_equal(g, out[0][1]) and np.array_equal(gw, out[0][2])
+    assert np.abs(out[0][1]).max() > 0
+    s.close()
