@@ -130,9 +130,10 @@ class FlowObjective(torch.autograd.Function):
     runs the coupled adjoint level by level.  FP32 or FP64 storage."""
 
     @staticmethod
-    def forward(ctx, theta, T_wall, F, u_in, solver: Solver, state0, nsteps: int, window, objective, every: int):
-        if every < 1:
-            raise ValueError("checkpoint interval must be >= 1")
+    def forward(ctx, theta, T_wall, F, u_in, solver: Solver, state0, nsteps: int, window, objective, every: int,
+                every2=None):
+        if every < 1 or (every2 is not None and every2 < 1):
+            raise ValueError("checkpoint intervals must be >= 1")
         dev = state0.device
         torch.cuda.synchronize(dev)
         solver.set_source(theta.detach().to(device=dev, dtype=torch.float32))
@@ -155,6 +156,7 @@ class FlowObjective(torch.autograd.Function):
         solver.sync()
         ctx.solver, ctx.ckpts, ctx.nsteps, ctx.window = solver, ckpts, nsteps, window
         ctx.objective, ctx.every, ctx.n_walls = objective, every, T_wall.numel()
+        ctx.every2 = every2
         ctx.meta = [(t.dtype, t.device) for t in (theta, T_wall, F, u_in)]
         return J[0]
 
@@ -173,19 +175,32 @@ class FlowObjective(torch.autograd.Function):
         lo, hi = ctx.window
         cur = 0
         FR, HR = s.flow_record_size()
+        every2 = ctx.every2 if ctx.every2 is not None else ctx.every
         for seg_start in sorted(ctx.ckpts, reverse=True):
             seg_end = min(seg_start + ctx.every, ctx.nsteps)
-            L = seg_end - seg_start
             s.load_state(ctx.ckpts[seg_start])
-            frec = torch.empty(L * FR, dtype=rdt, device=dev)
-            hrec = torch.empty(L * HR, dtype=rdt, device=dev)
-            s.step_record_pre(L, frec, hrec)
-            for k in range(seg_end, seg_start, -1):
-                obj = ctx.objective if lo <= k <= hi else None
-                j = k - seg_start - 1
-                s.adjoint_flow_step(frec[j * FR:(j + 1) * FR], hrec[j * HR:(j + 1) * HR],
-                                    muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj, dtheta)
-                cur = 1 - cur
+            if every2 < seg_end - seg_start:  # second level, as in ThermalObjective
+                inner = {}
+                for k in range(seg_start, seg_end):
+                    if (k - seg_start) % every2 == 0:
+                        inner[k] = s.save_state(torch.empty_like(ctx.ckpts[seg_start]))
+                    s.step(1)
+            else:
+                inner = {seg_start: None}
+            for sub_start in sorted(inner, reverse=True):
+                sub_end = min(sub_start + every2, seg_end)
+                L = sub_end - sub_start
+                if inner[sub_start] is not None:
+                    s.load_state(inner[sub_start])
+                frec = torch.empty(L * FR, dtype=rdt, device=dev)
+                hrec = torch.empty(L * HR, dtype=rdt, device=dev)
+                s.step_record_pre(L, frec, hrec)
+                for k in range(sub_end, sub_start, -1):
+                    obj = ctx.objective if lo <= k <= hi else None
+                    j = k - sub_start - 1
+                    s.adjoint_flow_step(frec[j * FR:(j + 1) * FR], hrec[j * HR:(j + 1) * HR],
+                                        muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj, dtheta)
+                    cur = 1 - cur
         obj0 = ctx.objective if lo <= 0 <= hi else None
         s.adjoint_flow_step(None, None, muf[cur], muh[cur], muf[1 - cur], muh[1 - cur], obj0, None)
         dTw = s.adjoint_wall_gradient(ctx.n_walls, reset=True)
@@ -193,9 +208,9 @@ class FlowObjective(torch.autograd.Function):
         gJ = gJ.detach().to(torch.float64).cpu()
         grads = [dtheta.cpu(), torch.from_numpy(dTw), torch.from_numpy(dF), torch.from_numpy(duin)]
         out = [(gJ * g).to(dtype=dt, device=dv) for g, (dt, dv) in zip(grads, ctx.meta)]
-        return out[0], out[1], out[2], out[3], None, None, None, None, None, None
+        return out[0], out[1], out[2], out[3], None, None, None, None, None, None, None
 
 
-def flow_objective(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every=50):
+def flow_objective(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every=50, every2=None):
     """J(theta, T_wall, F, u_in) with gradients by the coupled adjoint."""
-    return FlowObjective.apply(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every)
+    return FlowObjective.apply(theta, T_wall, F, u_in, solver, state0, nsteps, window, objective, every, every2)

@@ -507,7 +507,13 @@ cudaError_t launch_step(const Buffers& b, const DevParams& p, cudaStream_t s, bo
         if constexpr (sizeof(S) == sizeof(R)) {
             const int v = (cum ? 2 : 0) | (eq ? 1 : 0);
             switch (v) {
-                case 0: k_step<S, QH, true, false, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
+                case 0:  // CM-TRT: the same compile-time-rate collision as the plain step, so
+                         // recorded levels and plain steps give the same bits
+                    if (p.hkind == 0)
+                        k_step<S, QH, true, false, false, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+                    else
+                        k_step<S, QH, true, false, false, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS);
+                    break;
                 case 1: k_step<S, QH, true, false, false, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
                 case 2: k_step<S, QH, true, false, true, false, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;
                 default: k_step<S, QH, true, false, true, true, true><<<grid, kBlock, 0, s>>>(LBM_STEP_ARGS); break;

@@ -22,7 +22,7 @@ from test_gpu_adjoint import _channel, _plate, _solver
 pytestmark = pytest.mark.gpu
 
 
-def _gpu(s, theta, Tw, F, uin, nsteps, window, obj_spec, every):
+def _gpu(s, theta, Tw, F, uin, nsteps, window, obj_spec, every, every2=None):
     import torch
     from paper_2203_01316_gb300.autograd import flow_objective
     kind, idx, weight = obj_spec[:3]
@@ -32,7 +32,7 @@ def _gpu(s, theta, Tw, F, uin, nsteps, window, obj_spec, every):
     tw = torch.tensor(Tw, dtype=torch.float64, requires_grad=True)
     tF = torch.tensor(F, dtype=torch.float64, requires_grad=True)
     tu = torch.tensor(uin, dtype=torch.float64, requires_grad=True)
-    J = flow_objective(th, tw, tF, tu, s, state0, nsteps, window, obj, every=every)
+    J = flow_objective(th, tw, tF, tu, s, state0, nsteps, window, obj, every=every, every2=every2)
     J.backward()
     return (float(J.item()), th.grad.cpu().numpy(), tw.grad.numpy(), tF.grad.numpy(), tu.grad.numpy())
 
@@ -97,3 +97,33 @@ def test_flow_adjoint_refuses_16_bit_storage():
     h = torch.empty(27 * N, dtype=torch.float32, device="cuda")
     with pytest.raises(LBMError):
         s.step_record_pre(1, f, h)
+
+
+def test_flow_adjoint_two_level_checkpoints_give_the_same_gradients():
+    """every2 < every: the same recomputed bits, so the same J and gradients
+    (theta, T_w, F, u_in) as one checkpoint level, from the same saved state."""
+    import torch
+    from paper_2203_01316_gb300.autograd import flow_objective
+    w = _channel()
+    Tw = [1.0]
+    F = (1e-5, 0.0, 0.0)
+    uin = tuple(w["u_in"])
+    theta = w["theta"].astype(np.float32).astype(np.float64)
+    s = _solver(w, "f32", 27, "trt", 0.05, 0.01, F, Tw, theta)
+    obj = s.objective("surface", 0, 1.0)
+    state0 = s.save_state(torch.empty(s.state_size(), dtype=torch.uint8, device="cuda"))
+    out = []
+    for every2 in (None, 4, 1):
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+        tw = torch.tensor(Tw, dtype=torch.float64, requires_grad=True)
+        tF = torch.tensor(F, dtype=torch.float64, requires_grad=True)
+        tu = torch.tensor(uin, dtype=torch.float64, requires_grad=True)
+        J = flow_objective(th, tw, tF, tu, s, state0, 13, (5, 13), obj, every=6, every2=every2)
+        J.backward()
+        out.append([float(J.item()), th.grad.cpu().numpy(), tw.grad.numpy(), tF.grad.numpy(), tu.grad.numpy()])
+    for r in out[1:]:
+        assert r[0] == out[0][0]
+        for a, b in zip(r[1:], out[0][1:]):
+            assert np.array_equal(a, b)
+    assert np.abs(out[0][3]).max() > 0
+    s.close()
